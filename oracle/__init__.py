@@ -1,0 +1,207 @@
+"""FP64 CPU oracle of the ensemble-averaged bubble-dynamics source update.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product path
+(``paper_2511_21031_gb300``) never does, and this package never imports it.
+
+This module only marshals numpy arrays into the plain C oracle
+(``pab_oracle.c``), which holds all of the arithmetic; see that file for the
+paper passages each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pab_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+FLAG_STEP_LIMIT = 1
+FLAG_NONFINITE = 2
+FLAG_SUPERSONIC = 4
+FLAG_NONPOS = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("c", ctypes.c_double), ("mu", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("p0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("pv", ctypes.c_double), ("gas_mode", ctypes.c_int32),
+                ("max_attempts", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("v_floor", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class Params:
+    """Liquid, gas and stepper constants (SI units). Defaults: water, Sec. 5."""
+    rho: float = 1000.0
+    c: float = 1500.0
+    mu: float = 1e-3
+    sigma: float = 0.072
+    p0: float = 101325.0
+    gamma: float = 1.4
+    pv: float = 0.0
+    gas_mode: int = 0
+    max_attempts: int = 100000
+    tol: float = 1e-4
+    v_floor: float = -1.0  # < 0: 1e-3 * sqrt(p0 / rho)
+
+    def as_c(self) -> _Params:
+        vf = self.v_floor if self.v_floor >= 0 else 1e-3 * math.sqrt(self.p0 / self.rho)
+        return _Params(self.rho, self.c, self.mu, self.sigma, self.p0, self.gamma, self.pv,
+                       int(self.gas_mode), int(self.max_attempts), self.tol, vf)
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_ldp = ctypes.POINTER(ctypes.c_longdouble)
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(_Params)
+            lib.orc_bins.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _dp, _dp]
+            lib.orc_bins.restype = ctypes.c_int
+            lib.orc_rhs.argtypes = [P, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            lib.orc_rhs.restype = None
+            lib.orc_step.argtypes = [P, ctypes.c_int64, ctypes.c_int32, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_int32, _dp, _dp, _fp, _u32p, _i32p]
+            lib.orc_step.restype = None
+            lib.orc_moments.argtypes = [P, ctypes.c_int64, ctypes.c_int32, _dp, _dp, _dp, _dp,
+                                        _dp, _dp, _ldp]
+            lib.orc_moments.restype = None
+            lib.orc_error_norm.argtypes = [_dp, _dp, ctypes.c_double]
+            lib.orc_error_norm.restype = ctypes.c_double
+            lib.orc_step_factor.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_step_factor.restype = ctypes.c_double
+            lib.orc_linear_trial.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp]
+            lib.orc_linear_trial.restype = None
+            lib.orc_linear_advance.argtypes = [_dp, _dp, _fp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int32, _i32p]
+            lib.orc_linear_advance.restype = ctypes.c_uint32
+            _LIB = lib
+    return _LIB
+
+
+def _ptr(a, typ):
+    return a.ctypes.data_as(typ)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def bins(n_bins: int, R0ref: float = 10e-6, s: float = 0.3, K: float = 5.0):
+    """Lognormal bin table (R0_i, w_i) with Simpson weights normalised to one."""
+    R0 = np.zeros(n_bins)
+    w = np.zeros(n_bins)
+    rc = _lib().orc_bins(int(n_bins), R0ref, s, K, _ptr(R0, _dp), _ptr(w, _dp))
+    if rc != 0:
+        raise ValueError(f"invalid bin request: n_bins={n_bins} s={s} K={K}")
+    return R0, w
+
+
+def rhs(params: Params, R0: float, p_inf: float, R: float, Rdot: float):
+    """Keller-Miksis right-hand side: returns (Rdot, Rddot, p_bw)."""
+    y = np.array([R, Rdot], dtype=np.float64)
+    f = np.zeros(2)
+    pbw = np.zeros(1)
+    cp = params.as_c()
+    _lib().orc_rhs(ctypes.byref(cp), R0, p_inf, _ptr(y, _dp), _ptr(f, _dp), _ptr(pbw, _dp))
+    return float(f[0]), float(f[1]), float(pbw[0])
+
+
+def step(params: Params, R0, p_inf, dt, R, Rdot, h, n_fixed: int = 0):
+    """Advance [B][C] state in place over one flow step; returns (flags, attempts)."""
+    R0 = _f64(R0)
+    p_inf = _f64(p_inf)
+    B = R0.shape[0]
+    C = p_inf.shape[0]
+    for a, dt_ in ((R, np.float64), (Rdot, np.float64), (h, np.float32)):
+        if a.dtype != dt_ or not a.flags.c_contiguous or a.size != B * C:
+            raise ValueError("state arrays must be contiguous [B][C] (R, Rdot f64; h f32)")
+    flags = np.zeros((B, C), dtype=np.uint32)
+    attempts = np.zeros((B, C), dtype=np.int32)
+    cp = params.as_c()
+    _lib().orc_step(ctypes.byref(cp), C, B, _ptr(R0, _dp), _ptr(p_inf, _dp), float(dt),
+                    int(n_fixed), _ptr(R, _dp), _ptr(Rdot, _dp), _ptr(h, _fp),
+                    _ptr(flags, _u32p), _ptr(attempts, _i32p))
+    return flags, attempts
+
+
+def moments(params: Params, R0, w, n_b, R, Rdot, with_long_double: bool = False):
+    """[7][C] moments (n_b, alpha, <R^3>, <R^2 Rdot>, S_alpha, <R^3 p_bw>/<R^3>, <R^3 Rdot^2>/<R^3>)."""
+    R0 = _f64(R0)
+    w = _f64(w)
+    n_b = _f64(n_b)
+    R = _f64(R)
+    Rdot = _f64(Rdot)
+    B = R0.shape[0]
+    C = n_b.shape[0]
+    out = np.zeros((7, C))
+    ald = np.zeros(C, dtype=np.longdouble) if with_long_double else None
+    cp = params.as_c()
+    _lib().orc_moments(ctypes.byref(cp), C, B, _ptr(R0, _dp), _ptr(w, _dp), _ptr(n_b, _dp),
+                       _ptr(R, _dp), _ptr(Rdot, _dp), _ptr(out, _dp),
+                       _ptr(ald, _ldp) if ald is not None else None)
+    if with_long_double:
+        return out, ald
+    return out
+
+
+def error_norm(y3, z, v_floor):
+    y3 = _f64(y3)
+    z = _f64(z)
+    return float(_lib().orc_error_norm(_ptr(y3, _dp), _ptr(z, _dp), v_floor))
+
+
+def step_factor(err, tol):
+    return float(_lib().orc_step_factor(err, tol))
+
+
+def linear_trial(A, y, h):
+    A = _f64(A).reshape(4)
+    y = _f64(y)
+    y3 = np.zeros(2)
+    z = np.zeros(2)
+    _lib().orc_linear_trial(_ptr(A, _dp), _ptr(y, _dp), h, _ptr(y3, _dp), _ptr(z, _dp))
+    return y3, z
+
+
+def linear_advance(A, y, h, dt, tol, v_floor, max_attempts=100000):
+    """Adaptive driver on y' = A y; y (2,) f64 and h (1,) f32 updated in place."""
+    A = _f64(A).reshape(4)
+    na = np.zeros(1, dtype=np.int32)
+    fl = _lib().orc_linear_advance(_ptr(A, _dp), _ptr(y, _dp), _ptr(h, _fp), dt, tol, v_floor,
+                                   int(max_attempts), _ptr(na, _i32p))
+    return int(fl), int(na[0])
+
+
+def equilibrium_nb(alpha0: float, R0, w) -> float:
+    """n_b from the initial void fraction at the equilibrium state (Eq. e:ndf)."""
+    return alpha0 / (4.0 / 3.0 * math.pi * float(np.dot(_f64(w), _f64(R0) ** 3)))
