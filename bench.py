@@ -1,0 +1,346 @@
+"""Throughput of the bubble source update on GB300: bin-steps/s.
+
+One step = one flow step of the whole hot path over the workload: every
+(cell, bin) advanced with adaptive SSP-RK3(2) sub-steps under its cell's
+pressure, and the 7 quadrature moments of every cell written (one fused
+kernel per step).  bin-steps = cells x bins x flow steps (sub-steps are not
+counted).
+
+Default workload: 128^3 cells x Nb = 31 lognormal bins (s = 0.5), water,
+plane acoustic wave of 1.2 p0 at 100 kHz with 5 % seeded phase jitter,
+dt = 5e-9 s, adaptive FP64 (tol 1e-4).  The state (1.3 GB) is larger than
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload grid128|grid256_mixed|small] [--precision fp64|mixed]
+
+Under torchrun every rank advances its own 128^3 block (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2511_21031_gb300 import workloads  # noqa: E402
+
+METRIC = "bin-steps/s (cells x bins x flow steps)"
+NOMINAL_FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 1.25 TFLOP/s / (152 SMs x 2.07 GHz), see the design doc
+NOMINAL_FP32_FLOPS_PER_CLK_PER_SM = 256.0  # 128 FP32 lanes x 2 (FMA)
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 kernel executes per trial
+# (sub-step attempt) and per bin-step outside the trial loop, counted with ncu
+# (sm__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64-cell
+# workload; profiles/step_kernel_fp64_grid128.md gives the capture.
+FP64_FLOPS_PER_TRIAL = 420.0
+FP64_FLOPS_PER_BINSTEP = 60.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name, rank, edge=0):
+    if name == "grid128":
+        return workloads.config_grid128(seed=2 + 1000 * rank, edge=edge or 128)
+    if name == "grid256_mixed":
+        return workloads.config_grid256_mixed(seed=3 + 1000 * rank)
+    if name == "small":
+        return workloads.config_small(seed=1 + 1000 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, seconds=12.0, sample_cells=16384):
+    """The oracle as it stands on the host cores, on a seeded sample of the workload's cells."""
+    import oracle
+    cells = np.sort(np.random.default_rng(11).choice(wl.n_cells, min(sample_cells, wl.n_cells),
+                                                      replace=False))
+    sub = wl.subset(cells)
+    P = oracle.Params(**sub.fluid)
+    R0, _ = oracle.bins(sub.n_bins, sub.R0ref, sub.s, sub.span_K)
+    R = np.repeat(R0[:, None], sub.n_cells, axis=1).copy()
+    V = np.zeros_like(R)
+    h = np.zeros(R.shape, dtype=np.float32)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.step(P, R0, sub.pressure_step(steps), sub.dt, R, V, h)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds or steps >= wl.n_steps:
+            break
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": sub.n_cells * sub.n_bins * steps / el, "unit": "bin-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {steps} flow steps of {wl.name}"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = make_workload(args.workload, 0)
+    import oracle
+    cells = np.sort(np.random.default_rng(11).choice(wl.n_cells, min(16384, wl.n_cells), replace=False))
+    sub = wl.subset(cells)
+    P = oracle.Params(**sub.fluid)
+    R0, _ = oracle.bins(sub.n_bins, sub.R0ref, sub.s, sub.span_K)
+    R = np.repeat(R0[:, None], sub.n_cells, axis=1).copy()
+    V = np.zeros_like(R)
+    h = np.zeros(R.shape, dtype=np.float32)
+    for n in range(args.warmup):
+        oracle.step(P, R0, sub.pressure_step(n), sub.dt, R, V, h)
+    t0 = time.perf_counter()
+    for n in range(args.warmup, args.warmup + args.steps):
+        oracle.step(P, R0, sub.pressure_step(n), sub.dt, R, V, h)
+    el = time.perf_counter() - t0
+    value = sub.n_cells * sub.n_bins * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bin-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.n_cells, "bins": wl.n_bins, "dt": wl.dt,
+                       "sample_cells": sub.n_cells},
+            "cpu_baseline": {"value": value, "unit": "bin-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins per step"},
+            "e2e": {"value": value, "unit": "bin-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2511_21031_gb300 import pab
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = make_workload(args.workload, rank, args.edge)
+    precision = args.precision or wl.precision
+
+    # cpu baseline first, on rank 0 only, before any heavy GPU work
+    cpu = cpu_baseline(wl, seconds=args.cpu_seconds) if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        solver = pab.Solver(wl.n_cells, wl.n_bins, precision=precision, s_lognormal=wl.s,
+                            R0ref=wl.R0ref, span_K=wl.span_K, alpha0=wl.alpha0)
+        if args.block_warps:
+            solver.set_block_warps(args.block_warps)
+        total = args.warmup + args.steps
+        ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
+        mom = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64, device=dev)
+        for n in range(args.warmup):
+            solver.step(ps[n], wl.dt, moments=mom)
+        solver.moments(out=mom)  # one reduce-only launch (profiled for its per-bin cost)
+        solver.status()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            solver.step(ps[args.warmup + k], wl.dt, moments=mom)
+            ev[k][1].record(stream)
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    st = solver.status(stream=stream)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    # end to end through the host-buffer C-ABI entry point (pinned host memory)
+    n_e2e = max(1, min(args.steps, 10))
+    ph = [torch.as_tensor(wl.pressure_step(args.warmup + k)).pin_memory() for k in range(n_e2e)]
+    mh = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64).pin_memory()
+    solver.step_host(ph[0], wl.dt, moments_host=mh, stream=stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        solver.step_host(ph[k], wl.dt, moments_host=mh, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    solver.status(stream=stream)
+
+    bin_steps = wl.n_cells * wl.n_bins * args.steps
+    value = bin_steps * ws / (ms_total * 1e-3)
+    trials_per_binstep = st["n_attempts"] / bin_steps
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    sm_mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    if precision == "fp64":
+        flops_per_launch = wl.n_cells * wl.n_bins * (trials_per_binstep * FP64_FLOPS_PER_TRIAL
+                                                     + FP64_FLOPS_PER_BINSTEP)
+        peak = NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * SM_MAX_MHZ * 1e6
+        roof = {"bound": "alu", "achieved": flops_per_launch / avg_launch_s / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": flops_per_launch / avg_launch_s / peak, "traffic": None,
+                "pipe": "fp64", "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz",
+                "frac_at_measured_clock": flops_per_launch / avg_launch_s
+                / (NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * sm_mhz * 1e6)}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "pipe": "fp64+fp32"}
+
+    fma = None
+    if args.peak_probe:
+        sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
+        ms, n = pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 2000, sink.data_ptr(), int(stream.cuda_stream))
+        ms, n = pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 2000, sink.data_ptr(), int(stream.cuda_stream))
+        ms32, n32 = pab.pab_peak_fma(pab.PAB_MIXED, N_SM * 16, 256, 20000, sink.data_ptr(),
+                                     int(stream.cuda_stream))
+        fma = {"fp64_tflops": 2 * n / (ms * 1e-3) / 1e12, "fp32_tflops": 2 * n32 / (ms32 * 1e-3) / 1e12}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "bin-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.n_cells, "bins": wl.n_bins, "s": wl.s,
+                       "dt": wl.dt, "forcing": f"{wl.amp} p0 at {wl.freq:g} Hz", "precision": precision,
+                       "stepper": "adaptive SSP-RK3(2) tol 1e-4",
+                       "l2": "state 20 B/bin x 65M bins > L2, no flush needed",
+                       "parallelism": f"{ws} independent blocks (weak)", "seed": wl.seed},
+            "gpu_launches": args.steps,
+            "latency_ms": {"p50": float(np.percentile(launch_ms, 50)),
+                           "p99": float(np.percentile(launch_ms, 99))},
+            "trials_per_bin_step": trials_per_binstep,
+            "status_flags": st["flags"],
+            "roofline": roof,
+            "e2e": {"value": wl.n_cells * wl.n_bins * n_e2e * ws / e2e_s, "unit": "bin-steps/s",
+                    "h2d_bytes_per_step": wl.n_cells * 8, "d2h_bytes_per_step": 7 * wl.n_cells * 8},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        if fma:
+            line["fma_probe"] = fma
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="grid128")
+    ap.add_argument("--precision", default=None, choices=(None, "fp64", "mixed"))
+    ap.add_argument("--block-warps", type=int, default=0)
+    ap.add_argument("--edge", type=int, default=0, help="grid edge override (profiling runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--peak-probe", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

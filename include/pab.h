@@ -1,0 +1,185 @@
+/*
+ * pab.h - C ABI of the phase-averaged bubble-dynamics library (sm_103a).
+ *
+ * The library advances the ensemble-averaged (Euler-Euler) bubble state of
+ * "Hardware-Accelerated Phase-Averaging for Cavitating Bubbly Flows"
+ * (arXiv 2511.21031) over one flow step and reduces it into the source terms
+ * of the carrier equations:
+ *   - every grid cell carries Nb equilibrium-radius bins R0_i drawn from a
+ *     lognormal distribution with Simpson quadrature weights w_i (Sec. 2.2);
+ *   - each bin's radius obeys the Keller-Miksis equation, Eq. (keller_miksis),
+ *     with a polytropic gas (Ando's pressure ODE without transfer terms),
+ *     surface tension, viscosity and liquid compressibility (Sec. 2);
+ *   - the bins of a cell advance under that cell's pressure p_inf with
+ *     adaptive third-order TVD Runge-Kutta sub-steps, accepted when the
+ *     relative error against the embedded second-order member stays below a
+ *     tolerance (1e-4 in the paper, Sec. 3);
+ *   - the bins are reduced by the quadrature weights into n_b, the void
+ *     fraction alpha = 4/3 pi n_b <R^3> (Eq. e:ndf), the alpha source
+ *     3 alpha <R^2 Rdot>/<R^3> (Eq. e:alpha) and the pressure moments
+ *     <R^3 p_bw>/<R^3>, <R^3 Rdot^2>/<R^3> (Eq. e:pressure).
+ *
+ * Conventions (all entry points):
+ *   - Device pointers are caller-owned, contiguous, resident on the device
+ *     that was current at pab_create, and must stay valid until the stream
+ *     work that uses them has completed.  The handle owns only its state and
+ *     its small scratch (status counters, staging for the host entry point).
+ *   - State layout is bin-major structure-of-arrays: element (bin i, cell c)
+ *     is at index i * n_cells + c.  Moments are [7][n_cells], row k at k * n_cells.
+ *   - Calls are stream-ordered and asynchronous unless stated.  `stream` is a
+ *     cudaStream_t (NULL = legacy default stream).  Device-side problems are
+ *     recorded in the handle's status word and per-bin flags, never by trapping;
+ *     pab_status_flags reads them.
+ *   - No exceptions cross the ABI.  A handle is not thread-safe; separate
+ *     handles are.  Every call returns PAB_EINVAL for a NULL handle.
+ *   - On a non-OK return, pab_last_error(handle) describes the failure.
+ */
+#ifndef PAB_H
+#define PAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pab_s pab_t;
+
+typedef enum {
+    PAB_OK = 0,
+    PAB_EINVAL = 1,        /* invalid argument or configuration; nothing launched */
+    PAB_ENOMEM = 2,        /* device or host allocation failed */
+    PAB_ECUDA = 3,         /* a CUDA runtime call failed */
+    PAB_ESTEP_LIMIT = 4,   /* some bin exhausted max_attempts (pab_status_flags) */
+    PAB_ENONFINITE = 5,    /* non-finite input or state met (pab_status_flags) */
+    PAB_ESTATE = 6         /* call not valid in the handle's state */
+} pab_status;
+
+/* precision */
+enum { PAB_FP64 = 0, PAB_MIXED = 1 };
+/* stepper */
+enum { PAB_ADAPTIVE = 0, PAB_FIXED = 1 };
+/* gas_mode */
+enum { PAB_GAS_POLYTROPIC = 0, PAB_GAS_EMPTY = 1 };
+
+/* Per-bin status bits (OR-ed into the handle's status word). */
+#define PAB_FLAG_STEP_LIMIT 1u   /* attempts exhausted; the bin keeps its last accepted state */
+#define PAB_FLAG_NONFINITE 2u    /* non-finite pressure or state; the bin is left unchanged */
+#define PAB_FLAG_SUPERSONIC 4u   /* |Rdot| >= c after the step */
+#define PAB_FLAG_NONPOS 8u       /* R <= 0 after the step */
+
+#define PAB_MAX_BINS 63
+
+/*
+ * Configuration of one handle.  pab_config_default fills water (Sec. 5):
+ * rho 1000, c 1500, mu 1e-3, sigma 0.072, p0 101325, gamma 1.4, pv 0; bins
+ * R0ref 10e-6, s 0.3, span 5 s; adaptive FP64, tol 1e-4 (Sec. 3),
+ * v_floor 1e-3 sqrt(p0/rho), max_attempts 100000; alpha0 4e-5; equilibrium start.
+ */
+typedef struct {
+    int64_t n_cells;        /* C >= 1 */
+    int32_t n_bins;         /* Nb: 1, or odd 3..PAB_MAX_BINS (Simpson needs odd Nb) */
+    int32_t gas_mode;       /* PAB_GAS_POLYTROPIC: p_b = pv + p_g0 (R0/R)^(3 gamma),
+                               p_g0 = p0 + 2 sigma/R0 - pv; PAB_GAS_EMPTY: p_b = pv */
+    double rho, c, mu, sigma, p0, gamma, pv;   /* c = INFINITY: incompressible (RP) limit */
+    double R0ref;           /* median equilibrium radius of the lognormal */
+    double s_lognormal;     /* shape s of the lognormal (> 0 when Nb > 1) */
+    double span_K;          /* bins cover ln(R0/R0ref) in [-K s, K s] */
+    const double *R0_host;  /* optional explicit table [n_bins] (host, copied at create); */
+    const double *w_host;   /*   both non-NULL overrides the lognormal table */
+    int32_t precision;      /* PAB_FP64 or PAB_MIXED */
+    int32_t stepper;        /* PAB_ADAPTIVE or PAB_FIXED */
+    int32_t n_fixed_sub;    /* sub-steps per call in PAB_FIXED mode (>= 1) */
+    int32_t max_attempts;   /* bound on trials per bin per call (>= 1) */
+    double tol;             /* acceptance tolerance of the embedded error */
+    double v_floor;         /* floor of the Rdot scale in the error norm; < 0: default */
+    double alpha0;          /* default n_b = alpha0 / (4/3 pi sum_i w_i R0_i^3) */
+    double Rdot0_ref;       /* initial Rdot_i = Rdot0_ref * R0_i / R0ref (0: rest) */
+    int32_t record_attempts;/* non-zero: keep per-bin trial counts of the last call */
+    int32_t block_warps;    /* warps per CTA (0: default); cells per CTA is 32 */
+} pab_config;
+
+/* Fill *cfg with the defaults above (n_cells = 1, n_bins = 21). */
+void pab_config_default(pab_config *cfg);
+
+/*
+ * Create a handle: validates cfg, builds the bin table (R0_i, w_i) in FP64 on
+ * the host (Sec. 2.2; lognormal nodes equally spaced in ln R0 over +-K s,
+ * composite Simpson coefficients times the normal density, normalised to sum
+ * one), allocates the state R, Rdot (FP64 [Nb][C]) and the carried sub-step
+ * h (FP32 [Nb][C]) on the current device, and initialises R = R0_i,
+ * Rdot = Rdot0_ref R0_i/R0ref, h = 0 (first call uses dt) on `stream`.
+ * Errors: PAB_EINVAL (bad cfg, even Nb, NULL out), PAB_ENOMEM, PAB_ECUDA.
+ */
+pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out);
+
+/*
+ * Advance every (cell, bin) over one flow step dt (Sec. 3; the bubble half
+ * of the Strang split: p_inf is held constant over the call), then, if
+ * moments_dev is not NULL, reduce the new state into moments_dev [7][C]:
+ *   0 n_b, 1 alpha, 2 <R^3>, 3 <R^2 Rdot>, 4 3 alpha <R^2 Rdot>/<R^3>,
+ *   5 <R^3 p_bw>/<R^3>, 6 <R^3 Rdot^2>/<R^3>.
+ * p_inf_dev: [C] FP64 cell pressure (device).  nb_dev: [C] FP64 number
+ * density (device) or NULL for the handle's default n_b.
+ * Errors: PAB_EINVAL (NULL p_inf_dev, dt <= 0 or non-finite), PAB_ECUDA.
+ * Non-finite p_inf in a cell is not an error return: its bins are left
+ * unchanged and flagged PAB_FLAG_NONFINITE.
+ */
+pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_dev,
+                           double dt, double *moments_dev, void *stream);
+
+/* Reduce the current state into moments_dev [7][C] (same rows as above)
+ * without advancing it.  nb_dev as in pab_bubble_step. */
+pab_status pab_moments(pab_t *h, const double *nb_dev, double *moments_dev, void *stream);
+
+/*
+ * End-to-end form for host buffers: copies p_inf_host [C] (and nb_host [C]
+ * when not NULL) to the device, runs pab_bubble_step, copies the moments to
+ * moments_host [7][C] (when not NULL) and synchronises `stream`.  Pinned host
+ * memory makes the copies asynchronous DMA.  Staging buffers are allocated on
+ * first use and owned by the handle.
+ */
+pab_status pab_bubble_step_host(pab_t *h, const double *p_inf_host, const double *nb_host,
+                                double dt, double *moments_host, void *stream);
+
+/*
+ * Synchronise `stream`, return the status accumulated since the last call
+ * and reset it: *flags = OR of per-bin PAB_FLAG_* bits, *n_flagged = number
+ * of bin-steps that set any bit, *n_attempts = total trials, *n_fp64 = trials
+ * taken on the FP64 path in PAB_MIXED mode.  Any output pointer may be NULL.
+ * Returns PAB_ENONFINITE or PAB_ESTEP_LIMIT when those bits are set, else PAB_OK.
+ */
+pab_status pab_status_flags(pab_t *h, uint32_t *flags, int64_t *n_flagged, int64_t *n_attempts,
+                            int64_t *n_fp64, void *stream);
+
+/* Checkpoint / resume: copy the state out of / into the handle (device
+ * buffers [Nb][C]; h_dev may be NULL to leave h untouched on set). */
+pab_status pab_get_state(pab_t *h, double *R_dev, double *Rdot_dev, float *h_dev, void *stream);
+pab_status pab_set_state(pab_t *h, const double *R_dev, const double *Rdot_dev, const float *h_dev,
+                         void *stream);
+
+/* Per-bin trial counts of the last pab_bubble_step (int32 [Nb][C], device);
+ * PAB_ESTATE unless the handle was created with record_attempts. */
+pab_status pab_get_attempts(pab_t *h, int32_t *attempts_dev, void *stream);
+
+/* Copy the bin table (host arrays of n_bins) and the default n_b. */
+pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double *nb_default);
+
+/* Launch shape: warps per CTA (1..32; each warp covers 32 cells and strides
+ * over the bins).  Used by the autotuner. */
+pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
+
+/* Release the state on the creation stream.  NULL-safe. */
+void pab_destroy(pab_t *h);
+
+/* Description of the last failure on this handle ("" if none). */
+const char *pab_last_error(const pab_t *h);
+
+/* Static name of a status code. */
+const char *pab_status_string(pab_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAB_H */

@@ -1,0 +1,504 @@
+// Host side of the C ABI declared in include/pab.h: configuration checks,
+// the lognormal bin table, device state ownership and the stream-ordered
+// entry points.  No compute happens here; every step of the path runs in the
+// kernels of pab_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pab.h"
+#include "pab_internal.h"
+
+struct pab_s {
+    pab_config cfg;
+    pab::StepConst K;
+    int device = 0;
+    cudaStream_t create_stream = nullptr;
+    double *R = nullptr;
+    double *V = nullptr;
+    float *h = nullptr;
+    int32_t *attempts = nullptr;
+    pab::Counters *counters = nullptr;
+    pab::Counters *counters_host = nullptr;  // pinned
+    double *stage_p = nullptr;                // host entry point staging [C]
+    double *stage_nb = nullptr;               // [C]
+    double *stage_out = nullptr;              // [7][C]
+    int block_warps = 8;
+    char err[512] = {0};
+};
+
+namespace {
+
+pab_status fail(pab_t *h, pab_status s, const char *fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+pab_status cuda_fail(pab_t *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? PAB_ENOMEM : PAB_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+size_t n_state(const pab_t *h) { return (size_t)h->cfg.n_bins * (size_t)h->cfg.n_cells; }
+
+// Lognormal bins with composite Simpson weights (Sec. 2.2): nodes equally
+// spaced in phi = ln(R0/R0ref) over [-K s, K s]; coefficient 1,4,2,...,4,1
+// times the normal density N(phi; 0, s^2); normalised to sum one.
+bool lognormal_table(int B, double R0ref, double s, double K, double *R0, double *w)
+{
+    if (B == 1) {
+        R0[0] = R0ref;
+        w[0] = 1.0;
+        return true;
+    }
+    if (B < 3 || B % 2 == 0 || !(s > 0.0) || !(K > 0.0))
+        return false;
+    const double step = 2.0 * K * s / (double)(B - 1);
+    double sum = 0.0;
+    for (int i = 0; i < B; ++i) {
+        const double phi = -K * s + step * (double)i;
+        const int coef = (i == 0 || i == B - 1) ? 1 : ((i & 1) ? 4 : 2);
+        const double g = std::exp(-phi * phi / (2.0 * s * s));
+        R0[i] = R0ref * std::exp(phi);
+        w[i] = (double)coef * g;  // dphi/3 and the density's constant cancel
+        sum += w[i];
+    }
+    for (int i = 0; i < B; ++i)
+        w[i] /= sum;
+    return true;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+pab_status validate(const pab_config *c, char *msg, size_t n)
+{
+#define BAD(...)                        \
+    do {                                \
+        snprintf(msg, n, __VA_ARGS__);  \
+        return PAB_EINVAL;              \
+    } while (0)
+    if (c->n_cells < 1)
+        BAD("n_cells must be >= 1 (got %lld)", (long long)c->n_cells);
+    if (c->n_bins < 1 || c->n_bins > PAB_MAX_BINS || (c->n_bins > 1 && c->n_bins % 2 == 0))
+        BAD("n_bins must be 1 or odd in 3..%d (got %d)", PAB_MAX_BINS, c->n_bins);
+    if (!finite_pos(c->rho) || !(c->c > 0.0) || !(c->mu >= 0.0) || !(c->sigma >= 0.0) ||
+        !finite_pos(c->p0) || !finite_pos(c->gamma) || !(c->pv >= 0.0) || !std::isfinite(c->pv))
+        BAD("fluid constants out of range");
+    if (c->gas_mode != PAB_GAS_POLYTROPIC && c->gas_mode != PAB_GAS_EMPTY)
+        BAD("gas_mode must be 0 or 1");
+    if (c->precision != PAB_FP64 && c->precision != PAB_MIXED)
+        BAD("precision must be PAB_FP64 or PAB_MIXED");
+    if (c->stepper != PAB_ADAPTIVE && c->stepper != PAB_FIXED)
+        BAD("stepper must be PAB_ADAPTIVE or PAB_FIXED");
+    if (c->stepper == PAB_FIXED && c->n_fixed_sub < 1)
+        BAD("n_fixed_sub must be >= 1 in fixed mode");
+    if (c->max_attempts < 1)
+        BAD("max_attempts must be >= 1");
+    if (!finite_pos(c->tol))
+        BAD("tol must be positive");
+    if ((c->R0_host == nullptr) != (c->w_host == nullptr))
+        BAD("R0_host and w_host must be given together");
+    if (c->R0_host) {
+        for (int i = 0; i < c->n_bins; ++i)
+            if (!finite_pos(c->R0_host[i]) || !(c->w_host[i] >= 0.0) || !std::isfinite(c->w_host[i]))
+                BAD("explicit bin table entry %d out of range", i);
+    } else {
+        if (!finite_pos(c->R0ref))
+            BAD("R0ref must be positive");
+        if (c->n_bins > 1 && (!finite_pos(c->s_lognormal) || !finite_pos(c->span_K)))
+            BAD("s_lognormal and span_K must be positive when n_bins > 1");
+    }
+    if (!std::isfinite(c->Rdot0_ref) || !(c->alpha0 >= 0.0) || !std::isfinite(c->alpha0))
+        BAD("Rdot0_ref / alpha0 out of range");
+    if (c->block_warps < 0 || c->block_warps > 16)
+        BAD("block_warps must be 0..16");
+    return PAB_OK;
+#undef BAD
+}
+
+void build_const(const pab_config *c, const double *R0, const double *w, pab::StepConst *K)
+{
+    std::memset(K, 0, sizeof(*K));
+    K->C = c->n_cells;
+    K->B = c->n_bins;
+    K->gas_mode = c->gas_mode;
+    K->max_attempts = c->max_attempts;
+    K->n_fixed = c->stepper == PAB_FIXED ? c->n_fixed_sub : 0;
+    K->rho = c->rho;
+    K->inv_rho = 1.0 / c->rho;
+    K->c = c->c;
+    K->inv_c = 1.0 / c->c;
+    K->mu = c->mu;
+    K->sigma = c->sigma;
+    K->gamma = c->gamma;
+    K->pv = c->pv;
+    K->p0 = c->p0;
+    K->three_gamma = 3.0 * c->gamma;
+    K->four_mu = 4.0 * c->mu;
+    K->two_sigma = 2.0 * c->sigma;
+    K->ic_rho = K->inv_c / c->rho;
+    K->fmu_ic_rho = 4.0 * c->mu * K->inv_c / c->rho;
+    K->tol = c->tol;
+    K->cbrt_tol = std::cbrt(c->tol);
+    K->v_floor = c->v_floor >= 0.0 ? c->v_floor : 1e-3 * std::sqrt(c->p0 / c->rho);
+    K->v_collapse = c->c / 20.0;
+    K->r_collapse = 0.2;
+    K->inv_rhof = (float)K->inv_rho;
+    K->inv_cf = (float)K->inv_c;
+    K->four_muf = (float)K->four_mu;
+    K->two_sigmaf = (float)K->two_sigma;
+    K->three_gammaf = (float)K->three_gamma;
+    K->ic_rhof = (float)K->ic_rho;
+    K->fmu_ic_rhof = (float)K->fmu_ic_rho;
+    K->v_floorf = (float)K->v_floor;
+    double m3 = 0.0;
+    for (int i = 0; i < c->n_bins; ++i) {
+        pab::BinConst &b = K->bins[i];
+        b.R0 = R0[i];
+        b.w = w[i];
+        b.pg0 = c->gas_mode == PAB_GAS_POLYTROPIC ? c->p0 + 2.0 * c->sigma / R0[i] - c->pv : 0.0;
+        b.peq = c->pv + b.pg0 - 2.0 * c->sigma / R0[i];
+        b.R0f = (float)R0[i];
+        b.invR0f = (float)(1.0 / R0[i]);
+        b.pg0f = (float)b.pg0;
+        b.lnR0f = (float)std::log(R0[i]);
+        m3 += w[i] * R0[i] * R0[i] * R0[i];
+    }
+    K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pab_config_default(pab_config *c)
+{
+    if (!c)
+        return;
+    std::memset(c, 0, sizeof(*c));
+    c->n_cells = 1;
+    c->n_bins = 21;
+    c->gas_mode = PAB_GAS_POLYTROPIC;
+    c->rho = 1000.0;
+    c->c = 1500.0;
+    c->mu = 1e-3;
+    c->sigma = 0.072;
+    c->p0 = 101325.0;
+    c->gamma = 1.4;
+    c->pv = 0.0;
+    c->R0ref = 10e-6;
+    c->s_lognormal = 0.3;
+    c->span_K = 5.0;
+    c->precision = PAB_FP64;
+    c->stepper = PAB_ADAPTIVE;
+    c->n_fixed_sub = 1;
+    c->max_attempts = 100000;
+    c->tol = 1e-4;
+    c->v_floor = -1.0;
+    c->alpha0 = 4e-5;
+    c->Rdot0_ref = 0.0;
+    c->record_attempts = 0;
+    c->block_warps = 0;
+}
+
+const char *pab_status_string(pab_status s)
+{
+    switch (s) {
+    case PAB_OK: return "PAB_OK";
+    case PAB_EINVAL: return "PAB_EINVAL";
+    case PAB_ENOMEM: return "PAB_ENOMEM";
+    case PAB_ECUDA: return "PAB_ECUDA";
+    case PAB_ESTEP_LIMIT: return "PAB_ESTEP_LIMIT";
+    case PAB_ENONFINITE: return "PAB_ENONFINITE";
+    case PAB_ESTATE: return "PAB_ESTATE";
+    }
+    return "PAB_UNKNOWN";
+}
+
+const char *pab_last_error(const pab_t *h) { return h ? h->err : "NULL handle"; }
+
+pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
+{
+    if (!out)
+        return PAB_EINVAL;
+    *out = nullptr;
+    if (!cfg)
+        return PAB_EINVAL;
+    char msg[256];
+    if (validate(cfg, msg, sizeof(msg)) != PAB_OK) {
+        fprintf(stderr, "pab_create: %s\n", msg);
+        return PAB_EINVAL;
+    }
+    double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
+    if (cfg->R0_host) {
+        double sum = 0.0;
+        for (int i = 0; i < cfg->n_bins; ++i) {
+            R0[i] = cfg->R0_host[i];
+            w[i] = cfg->w_host[i];
+            sum += w[i];
+        }
+        if (!(sum > 0.0)) {
+            fprintf(stderr, "pab_create: explicit weights sum to zero\n");
+            return PAB_EINVAL;
+        }
+    } else if (!lognormal_table(cfg->n_bins, cfg->R0ref, cfg->s_lognormal, cfg->span_K, R0, w)) {
+        fprintf(stderr, "pab_create: invalid bin table request\n");
+        return PAB_EINVAL;
+    }
+    pab_t *h = new (std::nothrow) pab_t();
+    if (!h)
+        return PAB_ENOMEM;
+    h->cfg = *cfg;
+    h->cfg.R0_host = nullptr;
+    h->cfg.w_host = nullptr;
+    h->create_stream = (cudaStream_t)stream;
+    h->block_warps = cfg->block_warps > 0 ? cfg->block_warps : 8;
+    build_const(cfg, R0, w, &h->K);
+    cudaError_t e = cudaGetDevice(&h->device);
+    const size_t n = n_state(h);
+    cudaStream_t s = h->create_stream;
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void **)&h->R, n * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void **)&h->V, n * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void **)&h->h, n * sizeof(float), s);
+    if (e == cudaSuccess && cfg->record_attempts)
+        e = cudaMallocAsync((void **)&h->attempts, n * sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void **)&h->counters, sizeof(pab::Counters), s);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h->counters_host, sizeof(pab::Counters));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->counters, 0, sizeof(pab::Counters), s);
+    if (e == cudaSuccess && h->attempts)
+        e = cudaMemsetAsync(h->attempts, 0, n * sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = pab::launch_init(h->K, cfg->Rdot0_ref, cfg->R0ref, h->R, h->V, h->h, s);
+    if (e != cudaSuccess) {
+        pab_status st = e == cudaErrorMemoryAllocation ? PAB_ENOMEM : PAB_ECUDA;
+        fprintf(stderr, "pab_create: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        pab_destroy(h);
+        return st;
+    }
+    *out = h;
+    return PAB_OK;
+}
+
+void pab_destroy(pab_t *h)
+{
+    if (!h)
+        return;
+    cudaStream_t s = h->create_stream;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device)
+        cudaSetDevice(h->device);
+    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->counters, h->stage_p, h->stage_nb,
+                    h->stage_out};
+    for (void *b : bufs)
+        if (b)
+            cudaFreeAsync(b, s);
+    cudaStreamSynchronize(s);
+    if (h->counters_host)
+        cudaFreeHost(h->counters_host);
+    if (cur != h->device)
+        cudaSetDevice(cur);
+    delete h;
+}
+
+pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_dev, double dt,
+                           double *moments_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!p_inf_dev)
+        return fail(h, PAB_EINVAL, "pab_bubble_step: p_inf_dev is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(h, PAB_EINVAL, "pab_bubble_step: dt must be positive and finite (got %g)", dt);
+    pab::StepArgs a;
+    a.p_inf = p_inf_dev;
+    a.nb = nb_dev;
+    a.dt = dt;
+    a.R = h->R;
+    a.V = h->V;
+    a.h = h->h;
+    a.attempts = h->attempts;
+    a.out = moments_dev;
+    a.counters = h->counters;
+    cudaError_t e = pab::launch_step(h->K, h->cfg.precision, a, h->block_warps, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step launch");
+    return PAB_OK;
+}
+
+pab_status pab_moments(pab_t *h, const double *nb_dev, double *moments_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!moments_dev)
+        return fail(h, PAB_EINVAL, "pab_moments: moments_dev is NULL");
+    cudaError_t e = pab::launch_moments(h->K, h->cfg.precision, nb_dev, h->R, h->V, moments_dev,
+                                        h->block_warps, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_moments launch");
+    return PAB_OK;
+}
+
+pab_status pab_bubble_step_host(pab_t *h, const double *p_inf_host, const double *nb_host, double dt,
+                                double *moments_host, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!p_inf_host)
+        return fail(h, PAB_EINVAL, "pab_bubble_step_host: p_inf_host is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(h, PAB_EINVAL, "pab_bubble_step_host: dt must be positive and finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t C = (size_t)h->cfg.n_cells;
+    cudaError_t e = cudaSuccess;
+    if (!h->stage_p)
+        e = cudaMallocAsync((void **)&h->stage_p, C * sizeof(double), s);
+    if (e == cudaSuccess && nb_host && !h->stage_nb)
+        e = cudaMallocAsync((void **)&h->stage_nb, C * sizeof(double), s);
+    if (e == cudaSuccess && moments_host && !h->stage_out)
+        e = cudaMallocAsync((void **)&h->stage_out, 7 * C * sizeof(double), s);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host staging");
+    e = cudaMemcpyAsync(h->stage_p, p_inf_host, C * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nb_host)
+        e = cudaMemcpyAsync(h->stage_nb, nb_host, C * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host H2D");
+    pab_status st = pab_bubble_step(h, h->stage_p, nb_host ? h->stage_nb : nullptr, dt,
+                                    moments_host ? h->stage_out : nullptr, stream);
+    if (st != PAB_OK)
+        return st;
+    if (moments_host) {
+        e = cudaMemcpyAsync(moments_host, h->stage_out, 7 * C * sizeof(double),
+                            cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, "pab_bubble_step_host D2H");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host sync");
+    return PAB_OK;
+}
+
+pab_status pab_status_flags(pab_t *h, uint32_t *flags, int64_t *n_flagged, int64_t *n_attempts,
+                            int64_t *n_fp64, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->counters_host, h->counters, sizeof(pab::Counters),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->counters, 0, sizeof(pab::Counters), s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_status_flags");
+    const pab::Counters c = *h->counters_host;
+    if (flags)
+        *flags = c.flags_or;
+    if (n_flagged)
+        *n_flagged = (int64_t)c.n_flagged;
+    if (n_attempts)
+        *n_attempts = (int64_t)c.n_attempts;
+    if (n_fp64)
+        *n_fp64 = (int64_t)c.n_fp64;
+    if (c.flags_or & PAB_FLAG_NONFINITE)
+        return fail(h, PAB_ENONFINITE, "non-finite pressure or state in %llu bin-steps",
+                    (unsigned long long)c.n_flagged);
+    if (c.flags_or & PAB_FLAG_STEP_LIMIT)
+        return fail(h, PAB_ESTEP_LIMIT, "max_attempts exhausted (%llu flagged bin-steps)",
+                    (unsigned long long)c.n_flagged);
+    return PAB_OK;
+}
+
+pab_status pab_get_state(pab_t *h, double *R_dev, double *Rdot_dev, float *h_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = n_state(h);
+    cudaError_t e = cudaSuccess;
+    if (R_dev)
+        e = cudaMemcpyAsync(R_dev, h->R, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && Rdot_dev)
+        e = cudaMemcpyAsync(Rdot_dev, h->V, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && h_dev)
+        e = cudaMemcpyAsync(h_dev, h->h, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_get_state");
+}
+
+pab_status pab_set_state(pab_t *h, const double *R_dev, const double *Rdot_dev, const float *h_dev,
+                         void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!R_dev || !Rdot_dev)
+        return fail(h, PAB_EINVAL, "pab_set_state: R_dev and Rdot_dev are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = n_state(h);
+    cudaError_t e = cudaMemcpyAsync(h->R, R_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->V, Rdot_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && h_dev)
+        e = cudaMemcpyAsync(h->h, h_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_set_state");
+}
+
+pab_status pab_get_attempts(pab_t *h, int32_t *attempts_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!h->attempts)
+        return fail(h, PAB_ESTATE, "handle was created without record_attempts");
+    if (!attempts_dev)
+        return fail(h, PAB_EINVAL, "pab_get_attempts: NULL destination");
+    cudaError_t e = cudaMemcpyAsync(attempts_dev, h->attempts, n_state(h) * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_get_attempts");
+}
+
+pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double *nb_default)
+{
+    if (!h)
+        return PAB_EINVAL;
+    for (int i = 0; i < h->K.B; ++i) {
+        if (R0_host)
+            R0_host[i] = h->K.bins[i].R0;
+        if (w_host)
+            w_host[i] = h->K.bins[i].w;
+    }
+    if (nb_default)
+        *nb_default = h->K.nb_default;
+    return PAB_OK;
+}
+
+pab_status pab_set_block_warps(pab_t *h, int32_t block_warps)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (block_warps < 1 || block_warps > 16)
+        return fail(h, PAB_EINVAL, "block_warps must be 1..16");
+    h->block_warps = block_warps;
+    return PAB_OK;
+}
+
+}  // extern "C"

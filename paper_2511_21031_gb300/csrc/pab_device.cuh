@@ -1,0 +1,251 @@
+// Device arithmetic of the bubble source update: Keller-Miksis acceleration
+// in FP64 and in an FP32 deviation form, one SSP-RK3/RK2 trial, the error
+// norm, the step-size controller and the adaptive advance of one bin.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "pab_internal.h"
+
+namespace pab {
+
+struct Trial {
+    double R, V;    // third-order result y3
+    double eR, eV;  // |y3 - y2| per component (embedded second-order difference)
+    bool ok;        // every stage radius positive and y3 finite
+};
+
+// ---------------------------------------------------------------------------
+// Keller-Miksis acceleration, Eq. (keller_miksis), FP64.
+//   p_b = pv + p_g0 (R0/R)^(3 gamma)       (Ando's ODE without transfer terms)
+//   p_bw = p_b - (4 mu Rdot + 2 sigma)/R
+//   d/dt p_bw = -3 gamma (p_b - pv) Rdot/R + (4 mu Rdot + 2 sigma) Rdot/R^2 - 4 mu Rddot/R
+// The Rddot inside d/dt p_bw moves to the left-hand side, whose coefficient
+// becomes R (1 - Rdot/c) + 4 mu/(rho c).  1/c = 0 gives Rayleigh-Plesset.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double p_inf,
+                                          double R, double V)
+{
+    const double iR = 1.0 / R;
+    const double VR = V * iR;
+    double pg = 0.0;
+    if (K.gas_mode == PAB_GAS_POLYTROPIC)
+        pg = bc.pg0 * pow(bc.R0 * iR, K.three_gamma);
+    const double s = fma(K.four_mu, V, K.two_sigma);
+    const double pbw = (K.pv + pg) - s * iR;
+    const double dpbw = (s * iR - K.three_gamma * pg) * VR;
+    const double icV = V * K.inv_c;
+    const double num = (pbw - p_inf) * K.inv_rho * (1.0 + icV) + R * K.ic_rho * dpbw
+                     - 1.5 * V * V * (1.0 - icV * (1.0 / 3.0));
+    const double den = fma(R, 1.0 - icV, K.fmu_ic_rho);
+    return num / den;
+}
+
+// Wall pressure p_bw at (R, Rdot) in FP64 (for the <R^3 p_bw> moment).
+__device__ __forceinline__ double wall_pressure64(const StepConst &K, const BinConst &bc, double R,
+                                                  double V)
+{
+    const double iR = 1.0 / R;
+    double pg = 0.0;
+    if (K.gas_mode == PAB_GAS_POLYTROPIC)
+        pg = bc.pg0 * pow(bc.R0 * iR, K.three_gamma);
+    return (K.pv + pg) - fma(K.four_mu, V, K.two_sigma) * iR;
+}
+
+// ---------------------------------------------------------------------------
+// The same acceleration in FP32, written in deviations from equilibrium so
+// that nothing cancels: with xi = R - R0, u = xi/R0,
+//   p_b - pv - p_g0          = p_g0 expm1(-3 gamma log1p(u))
+//   p_bw - p_inf             = A + (p_b - pv - p_g0) + (2 sigma u - 4 mu Rdot)/R
+// where A = pv + p_g0 - 2 sigma/R0 - p_inf is formed in FP64 once per bin-step
+// (for the polytropic gas A = p0 - p_inf).  Each term is then accurate
+// relative to itself rather than to p0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gas_dev32(const StepConst &K, const BinConst &bc, float u)
+{
+    return bc.pg0f * expm1f(-K.three_gammaf * log1pf(u));
+}
+
+__device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc, float A, float xi,
+                                         float V)
+{
+    const float R = bc.R0f + xi;
+    const float iR = 1.0f / R;
+    const float u = xi * bc.invR0f;
+    float pgdev = 0.0f, pg = 0.0f;
+    if (K.gas_mode == PAB_GAS_POLYTROPIC) {
+        pgdev = gas_dev32(K, bc, u);
+        pg = bc.pg0f + pgdev;
+    }
+    const float VR = V * iR;
+    const float s = fmaf(K.four_muf, V, K.two_sigmaf);
+    const float dp = A + pgdev + (K.two_sigmaf * u - K.four_muf * V) * iR;
+    const float dpbw = (s * iR - K.three_gammaf * pg) * VR;
+    const float icV = V * K.inv_cf;
+    const float num = dp * K.inv_rhof * (1.0f + icV) + R * K.ic_rhof * dpbw
+                    - 1.5f * V * V * (1.0f - icV * (1.0f / 3.0f));
+    const float den = fmaf(R, 1.0f - icV, K.fmu_ic_rhof);
+    return num / den;
+}
+
+// ---------------------------------------------------------------------------
+// One trial of the Shu-Osher SSP-RK3 scheme with the embedded SSP-RK2 (Heun)
+// member sharing its first two evaluations (Sec. 3):
+//   y1 = y + h f(y);  u = y1 + h f(y1)
+//   y2 = 3/4 y + 1/4 u;  z = 1/2 (y + u)      (z: second order)
+//   y3 = 1/3 y + 2/3 (y2 + h f(y2))           (third order, the one kept)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double p_inf,
+                                         double R, double V, double h)
+{
+    const double a1 = accel64(K, bc, p_inf, R, V);
+    const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
+    const double a2 = accel64(K, bc, p_inf, y1R, y1V);
+    const double uR = fma(h, y1V, y1R), uV = fma(h, a2, y1V);
+    const double zR = 0.5 * (R + uR), zV = 0.5 * (V + uV);
+    const double y2R = fma(0.75, R, 0.25 * uR), y2V = fma(0.75, V, 0.25 * uV);
+    const double a3 = accel64(K, bc, p_inf, y2R, y2V);
+    const double wR = fma(h, y2V, y2R), wV = fma(h, a3, y2V);
+    Trial t;
+    t.R = fma(2.0 / 3.0, wR, R * (1.0 / 3.0));
+    t.V = fma(2.0 / 3.0, wV, V * (1.0 / 3.0));
+    t.eR = fabs(t.R - zR);
+    t.eV = fabs(t.V - zV);
+    t.ok = (y1R > 0.0) && (y2R > 0.0) && (t.R > 0.0) && (fabs(t.V) <= DBL_MAX);
+    return t;
+}
+
+// The same trial with the three right-hand sides in FP32 on increments from
+// y: k_j = h f(stage j).  y3 - y = (k1 + k2)/6 + 2/3 k3 and the embedded
+// difference y3 - z = (2 k3 - k1 - k2)/3 is formed in FP64 from the k's, so
+// the error estimate suffers no FP32 cancellation.  The new state is y plus
+// the FP32 increment, added in FP64.
+__device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc, float A, double R,
+                                         double V, double h)
+{
+    const float xi0 = (float)(R - bc.R0);
+    const float v0 = (float)V;
+    const float hf = (float)h;
+    const float a1 = accel32(K, bc, A, xi0, v0);
+    const float k1R = hf * v0, k1V = hf * a1;
+    const float v1 = v0 + k1V;
+    const float a2 = accel32(K, bc, A, xi0 + k1R, v1);
+    const float k2R = hf * v1, k2V = hf * a2;
+    const float e2R = 0.25f * (k1R + k2R), e2V = 0.25f * (k1V + k2V);
+    const float v2 = v0 + e2V;
+    const float a3 = accel32(K, bc, A, xi0 + e2R, v2);
+    const float k3R = hf * v2, k3V = hf * a3;
+    const float d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
+    const float d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
+    Trial t;
+    t.R = R + (double)d3R;
+    t.V = V + (double)d3V;
+    t.eR = fabs(2.0 * (double)k3R - ((double)k1R + (double)k2R)) * (1.0 / 3.0);
+    t.eV = fabs(2.0 * (double)k3V - ((double)k1V + (double)k2V)) * (1.0 / 3.0);
+    const float r1 = bc.R0f + (xi0 + k1R), r2 = bc.R0f + (xi0 + e2R);
+    t.ok = (r1 > 0.0f) && (r2 > 0.0f) && (t.R > 0.0) && (fabs(t.V) <= DBL_MAX)
+        && isfinite(a1 + a2 + a3);
+    return t;
+}
+
+// Relative error of a trial: max(|dR|/|R3|, |dRdot|/max(|Rdot3|, v_floor)).
+__device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
+{
+    const double aR = fabs(t.R);
+    const double vs = fmax(fabs(t.V), K.v_floor);
+    return fmax(t.eR * vs, t.eV * aR) / (aR * vs);
+}
+
+// Step-size factor clamp(0.9 (tol/err)^(1/3), 0.2, 5); 0.2 after a failed trial.
+__device__ __forceinline__ double step_factor(const StepConst &K, double err, bool ok)
+{
+    if (!ok || !(err <= DBL_MAX))
+        return 0.2;
+    if (err == 0.0)
+        return 5.0;
+    return fmin(fmax(0.9 * K.cbrt_tol * rcbrt(err), 0.2), 5.0);
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive advance of one bin over dt with the carried proposal hc:
+//   h = min(hc, dt) (dt when hc is not a positive number); the trial size is
+//   min(h, dt - t) and the trial that reaches dt is marked last, so the call
+//   ends exactly at dt; accepted: t += h_try, proposal h_try * fac (on the
+//   last trial the unclipped h is kept when it was clipped and fac >= 1);
+//   rejected: h = h_try * fac; at most max_attempts trials.
+// MIXED selects the FP64 trial only where R < r_collapse R0 or
+// |Rdot| > v_collapse, else the FP32 trial.
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
+                                                     double p_inf, float A, double dt, double &R,
+                                                     double &V, float &hc, int &n_att, int &n64)
+{
+    double h = (double)hc;
+    if (!(h > 0.0) || h > dt)
+        h = dt;
+    double t = 0.0;
+    uint32_t flags = 0;
+    int n = 0;
+    for (;;) {
+        if (n >= K.max_attempts) {
+            flags |= PAB_FLAG_STEP_LIMIT;
+            break;
+        }
+        const double rem = dt - t;
+        const bool last = h >= rem;
+        const double ht = last ? rem : h;
+        Trial tr;
+        if (MIXED) {
+            const bool stiff = (R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse);
+            if (stiff) {
+                tr = trial64(K, bc, p_inf, R, V, ht);
+                ++n64;
+            } else {
+                tr = trial32(K, bc, A, R, V, ht);
+            }
+        } else {
+            tr = trial64(K, bc, p_inf, R, V, ht);
+        }
+        ++n;
+        const double err = error_norm(K, tr);
+        const double fac = step_factor(K, err, tr.ok);
+        if (tr.ok && err <= K.tol) {
+            R = tr.R;
+            V = tr.V;
+            if (last) {
+                const bool clipped = rem < h;
+                h = (clipped && fac >= 1.0) ? h : ht * fac;
+                break;
+            }
+            t += ht;
+            h = ht * fac;
+        } else {
+            h = ht * fac;
+        }
+    }
+    hc = (float)h;
+    n_att = n;
+    return flags;
+}
+
+// Fixed mode: n equal trials of dt/n, no error estimate (MIXED: FP64 trials
+// only for bins near collapse, as in the adaptive mode).
+template <bool MIXED>
+__device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst &bc, double p_inf,
+                                              float A, double dt, double &R, double &V)
+{
+    const double h = dt / (double)K.n_fixed;
+    for (int i = 0; i < K.n_fixed; ++i) {
+        Trial tr;
+        if (MIXED && !((R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse)))
+            tr = trial32(K, bc, A, R, V, h);
+        else
+            tr = trial64(K, bc, p_inf, R, V, h);
+        R = tr.R;
+        V = tr.V;
+    }
+}
+
+}  // namespace pab

@@ -1,0 +1,76 @@
+// Internal declarations shared by the host API and the kernels of libpab.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pab.h"
+
+namespace pab {
+
+// Per-bin constants, computed once in FP64 on the host at create time.
+struct BinConst {
+    double R0;     // equilibrium radius R0_i
+    double w;      // quadrature weight w_i (sums to one over the bins)
+    double pg0;    // gas pressure at equilibrium: p0 + 2 sigma/R0 - pv (0 for an empty cavity)
+    double peq;    // pv + pg0 - 2 sigma/R0: the wall pressure at R = R0, Rdot = 0
+    float R0f;     // R0 in FP32 (mixed path)
+    float invR0f;  // 1/R0 in FP32
+    float pg0f;    // pg0 in FP32
+    float lnR0f;   // unused padding kept for 16-byte alignment
+};
+
+// Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
+// so warp-uniform reads come from the constant bank.
+struct StepConst {
+    int64_t C;            // cells
+    int32_t B;            // bins
+    int32_t gas_mode;
+    int32_t max_attempts;
+    int32_t n_fixed;      // > 0: fixed mode with n_fixed sub-steps
+    double rho, inv_rho, c, inv_c, mu, sigma, gamma, pv, p0;
+    double three_gamma;   // 3 gamma
+    double four_mu;       // 4 mu
+    double two_sigma;     // 2 sigma
+    double ic_rho;        // (1/c)/rho
+    double fmu_ic_rho;    // 4 mu (1/c)/rho
+    double tol;
+    double cbrt_tol;      // tol^(1/3)
+    double v_floor;
+    double v_collapse;    // mixed: |Rdot| above this takes the FP64 path (c/20)
+    double r_collapse;    // mixed: R/R0 below this takes the FP64 path (0.2)
+    double nb_default;    // n_b when the caller passes no n_b field
+    float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
+    BinConst bins[PAB_MAX_BINS];
+};
+
+// Device-side status accumulated over calls until pab_status_flags reads it.
+struct Counters {
+    unsigned int flags_or;
+    unsigned int pad;
+    unsigned long long n_flagged;
+    unsigned long long n_attempts;
+    unsigned long long n_fp64;
+};
+
+struct StepArgs {
+    const double *p_inf;   // [C]
+    const double *nb;      // [C] or nullptr
+    double dt;
+    double *R;             // [B][C]
+    double *V;             // [B][C]
+    float *h;              // [B][C]
+    int32_t *attempts;     // [B][C] or nullptr
+    double *out;           // [7][C] or nullptr
+    Counters *counters;
+};
+
+// Launchers (pab_kernels.cu).  Return the launch error.
+cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,
+                        cudaStream_t s);
+cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, const double *R,
+                           const double *V, double *out, int block_warps, cudaStream_t s);
+cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
+                        float *h, cudaStream_t s);
+
+}  // namespace pab

@@ -1,0 +1,300 @@
+// Kernels of the bubble source update on sm_103a.
+//
+// Work decomposition: a CTA owns a tile of 32 consecutive cells (one per
+// lane) and all Nb bins of those cells; its warps stride over the bins.  All
+// lanes of a warp therefore advance the same bin of 32 neighbouring cells:
+// loads and stores of the bin-major state are 256-byte coalesced, the bin
+// constants are warp-uniform constant-bank reads, and neighbouring cells
+// (similar pressure) need similar sub-step counts, which keeps the adaptive
+// loop's divergence low.  Each lane keeps running quadrature sums for its
+// cell over the bins its warp visits; the warps' partial sums are combined in
+// shared memory and one warp writes the 7 moments of the 32 cells.  No
+// atomics touch the state: every (bin, cell) has one owner (Sec. 4).
+#include <cuda_runtime.h>
+
+#include "pab_device.cuh"
+#include "pab_internal.h"
+
+namespace pab {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kMaxWarps = 16;
+
+// Running quadrature sums of one lane (one cell).  In MIXED mode the alpha
+// sum sum w R^3 is compensated (Neumaier).
+template <bool MIXED>
+struct MomAcc {
+    double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
+
+    __device__ __forceinline__ void add_m3(double x)
+    {
+        if (MIXED) {
+            const double t = m3 + x;
+            if (fabs(m3) >= fabs(x))
+                m3c += (m3 - t) + x;
+            else
+                m3c += (x - t) + m3;
+            m3 = t;
+        } else {
+            m3 += x;
+        }
+    }
+};
+
+template <bool MIXED>
+__device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &bc, double R,
+                                           double V, MomAcc<MIXED> &acc)
+{
+    const double wr2 = bc.w * R * R;
+    const double wr3 = wr2 * R;
+    double pbw;
+    if (MIXED) {
+        // deviation of p_bw from its equilibrium value peq, in FP32
+        const float xi = (float)(R - bc.R0);
+        const float Rf = (float)R;
+        const float Vf = (float)V;
+        const float u = xi * bc.invR0f;
+        const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
+        const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * Vf) / Rf;
+        pbw = bc.peq + (double)dev;
+    } else {
+        pbw = wall_pressure64(K, bc, R, V);
+    }
+    acc.add_m3(wr3);
+    acc.m2v += wr2 * V;
+    acc.m3p += wr3 * pbw;
+    acc.m3v2 += wr3 * V * V;
+}
+
+// Combine the warps' partial sums of one tile and write the moments.
+template <bool MIXED>
+__device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAcc<MIXED> &acc,
+                                                 double nb, int64_t c, bool valid, double *out)
+{
+    __shared__ double red[5][kMaxWarps][kTile];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    red[0][warp][lane] = acc.m3;
+    red[1][warp][lane] = acc.m3c;
+    red[2][warp][lane] = acc.m2v;
+    red[3][warp][lane] = acc.m3p;
+    red[4][warp][lane] = acc.m3v2;
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double m3 = red[0][0][lane], m3c = red[1][0][lane];
+        double m2v = red[2][0][lane], m3p = red[3][0][lane], m3v2 = red[4][0][lane];
+        for (int w = 1; w < nw; ++w) {
+            const double x = red[0][w][lane];
+            if (MIXED) {
+                const double t = m3 + x;
+                if (fabs(m3) >= fabs(x))
+                    m3c += (m3 - t) + x;
+                else
+                    m3c += (x - t) + m3;
+                m3 = t;
+                m3c += red[1][w][lane];
+            } else {
+                m3 += x;
+            }
+            m2v += red[2][w][lane];
+            m3p += red[3][w][lane];
+            m3v2 += red[4][w][lane];
+        }
+        if (MIXED)
+            m3 += m3c;
+        const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
+        const double inv_m3 = 1.0 / m3;
+        const int64_t C = K.C;
+        out[0 * C + c] = nb;
+        out[1 * C + c] = alpha;
+        out[2 * C + c] = m3;
+        out[3 * C + c] = m2v;
+        out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
+        out[5 * C + c] = m3p * inv_m3;
+        out[6 * C + c] = m3v2 * inv_m3;
+    }
+}
+
+// Block-wide sums of the status counters, one atomic per CTA and counter.
+__device__ __forceinline__ void flush_counters(uint32_t fl_or, uint32_t n_flag, uint32_t n_att,
+                                               uint32_t n64, Counters *cnt)
+{
+    __shared__ uint32_t sc[4][kMaxWarps];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    fl_or = __reduce_or_sync(0xffffffffu, fl_or);
+    n_flag = __reduce_add_sync(0xffffffffu, n_flag);
+    n_att = __reduce_add_sync(0xffffffffu, n_att);
+    n64 = __reduce_add_sync(0xffffffffu, n64);
+    if (lane == 0) {
+        sc[0][warp] = fl_or;
+        sc[1][warp] = n_flag;
+        sc[2][warp] = n_att;
+        sc[3][warp] = n64;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t f = 0;
+        unsigned long long a = 0, b = 0, d = 0;
+        for (int w = 0; w < nw; ++w) {
+            f |= sc[0][w];
+            a += sc[1][w];
+            b += sc[2][w];
+            d += sc[3][w];
+        }
+        if (f)
+            atomicOr(&cnt->flags_or, f);
+        if (a)
+            atomicAdd(&cnt->n_flagged, a);
+        if (b)
+            atomicAdd(&cnt->n_attempts, b);
+        if (d)
+            atomicAdd(&cnt->n_fp64, d);
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
+    const bool valid = c < K.C;
+    const double p_inf = valid ? a.p_inf[c] : K.p0;
+    const bool p_ok = isfinite(p_inf);
+    const double nb = valid ? (a.nb ? a.nb[c] : K.nb_default) : 0.0;
+
+    MomAcc<MIXED> acc;
+    uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
+    for (int b = warp; b < K.B; b += nw) {
+        if (!valid)
+            continue;
+        const BinConst &bc = K.bins[b];
+        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
+        double R = a.R[k];
+        double V = a.V[k];
+        uint32_t fl = 0;
+        int na = 0;
+        if (!p_ok || !isfinite(R) || !isfinite(V)) {
+            fl = PAB_FLAG_NONFINITE;
+        } else {
+            const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
+            if (K.n_fixed > 0) {
+                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt, R, V);
+                na = K.n_fixed;
+            } else {
+                float hc = a.h[k];
+                int nd = 0;
+                fl = advance_adaptive<MIXED>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
+                a.h[k] = hc;
+                n64 += nd;
+            }
+            if (!isfinite(R) || !isfinite(V))
+                fl |= PAB_FLAG_NONFINITE;
+            else if (!(R > 0.0))
+                fl |= PAB_FLAG_NONPOS;
+            if (fabs(V) >= K.c)
+                fl |= PAB_FLAG_SUPERSONIC;
+            a.R[k] = R;
+            a.V[k] = V;
+        }
+        if (a.attempts)
+            a.attempts[k] = na;
+        fl_or |= fl;
+        n_flag += (fl != 0);
+        n_att += na;
+        if (a.out)
+            accumulate<MIXED>(K, bc, R, V, acc);
+    }
+    if (a.out)
+        reduce_and_store<MIXED>(K, acc, nb, c, valid, a.out);
+    flush_counters(fl_or, n_flag, n_att, n64, a.counters);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
+                   const double *__restrict__ Rp, const double *__restrict__ Vp,
+                   double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
+    const bool valid = c < K.C;
+    const double nb = valid ? (nbp ? nbp[c] : K.nb_default) : 0.0;
+    MomAcc<MIXED> acc;
+    for (int b = warp; b < K.B; b += nw) {
+        if (!valid)
+            continue;
+        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
+        accumulate<MIXED>(K, K.bins[b], Rp[k], Vp[k], acc);
+    }
+    reduce_and_store<MIXED>(K, acc, nb, c, valid, out);
+}
+
+__global__ void init_kernel(const __grid_constant__ StepConst K, double rdot_scale, double *R,
+                            double *V, float *h)
+{
+    const size_t n = (size_t)K.B * (size_t)K.C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / (size_t)K.C);
+        const double R0 = K.bins[b].R0;
+        R[i] = R0;
+        V[i] = rdot_scale * R0;
+        h[i] = 0.0f;
+    }
+}
+
+int clamp_warps(int w, int B)
+{
+    if (w <= 0)
+        w = 8;
+    if (w > kMaxWarps)
+        w = kMaxWarps;
+    if (w > B)
+        w = B;
+    return w < 1 ? 1 : w;
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,
+                        cudaStream_t s)
+{
+    const int nw = clamp_warps(block_warps, K.B);
+    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
+    if (precision == PAB_MIXED)
+        step_kernel<true><<<grid, nw * 32, 0, s>>>(K, a);
+    else
+        step_kernel<false><<<grid, nw * 32, 0, s>>>(K, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, const double *R,
+                           const double *V, double *out, int block_warps, cudaStream_t s)
+{
+    const int nw = clamp_warps(block_warps, K.B);
+    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
+    if (precision == PAB_MIXED)
+        moments_kernel<true><<<grid, nw * 32, 0, s>>>(K, nb, R, V, out);
+    else
+        moments_kernel<false><<<grid, nw * 32, 0, s>>>(K, nb, R, V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
+                        float *h, cudaStream_t s)
+{
+    const double scale = (R0ref > 0.0) ? Rdot0_ref / R0ref : 0.0;
+    init_kernel<<<152 * 8, 256, 0, s>>>(K, scale, R, V, h);
+    return cudaGetLastError();
+}
+
+}  // namespace pab

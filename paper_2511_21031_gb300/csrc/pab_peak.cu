@@ -1,0 +1,57 @@
+// FMA throughput microbenchmark (measurement aid for the roofline).
+#include <cuda_runtime.h>
+
+#include "pab_measure.h"
+
+namespace {
+
+template <typename T>
+__global__ void fma_streams(int iters, double *sink)
+{
+    T a0 = (T)threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+    const T m = (T)0.999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
+            a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+        }
+    }
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] =
+        (double)(a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7);
+}
+
+}  // namespace
+
+extern "C" pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int32_t iters,
+                                   double *sink_dev, float *ms_out, double *fma_out, void *stream)
+{
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !sink_dev || !ms_out || !fma_out)
+        return PAB_EINVAL;
+    if (precision != PAB_FP64 && precision != PAB_MIXED)
+        return PAB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return PAB_ECUDA;
+    cudaEventRecord(e0, s);
+    if (precision == PAB_FP64)
+        fma_streams<double><<<blocks, threads, 0, s>>>(iters, sink_dev);
+    else
+        fma_streams<float><<<blocks, threads, 0, s>>>(iters, sink_dev);
+    cudaError_t e = cudaGetLastError();
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess)
+        e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess)
+        return PAB_ECUDA;
+    *ms_out = ms;
+    *fma_out = (double)blocks * threads * (double)iters * 32.0;
+    return PAB_OK;
+}

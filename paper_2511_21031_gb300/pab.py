@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libpab (include/pab.h).
+
+The module-level functions carry the C names and only marshal arguments
+(integers for device pointers and streams).  ``Solver`` wraps one handle for
+torch tensors: it checks dtype, device and contiguity and passes
+``data_ptr()`` and the current CUDA stream.  Every step of the path runs in
+the library's kernels; if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from . import _build
+
+PAB_OK, PAB_EINVAL, PAB_ENOMEM, PAB_ECUDA, PAB_ESTEP_LIMIT, PAB_ENONFINITE, PAB_ESTATE = range(7)
+PAB_FP64, PAB_MIXED = 0, 1
+PAB_ADAPTIVE, PAB_FIXED = 0, 1
+PAB_GAS_POLYTROPIC, PAB_GAS_EMPTY = 0, 1
+FLAG_STEP_LIMIT, FLAG_NONFINITE, FLAG_SUPERSONIC, FLAG_NONPOS = 1, 2, 4, 8
+MAX_BINS = 63
+N_MOMENTS = 7
+MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3Rdot2_over_R3")
+
+EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
+           "pab_bubble_step_host", "pab_status_flags", "pab_get_state", "pab_set_state",
+           "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
+           "pab_last_error", "pab_status_string", "pab_peak_fma")
+
+
+class PabError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class pab_config(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_bins", ctypes.c_int32), ("gas_mode", ctypes.c_int32),
+                ("rho", ctypes.c_double), ("c", ctypes.c_double), ("mu", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("p0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("pv", ctypes.c_double), ("R0ref", ctypes.c_double), ("s_lognormal", ctypes.c_double),
+                ("span_K", ctypes.c_double), ("R0_host", ctypes.POINTER(ctypes.c_double)),
+                ("w_host", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int32),
+                ("stepper", ctypes.c_int32), ("n_fixed_sub", ctypes.c_int32),
+                ("max_attempts", ctypes.c_int32), ("tol", ctypes.c_double), ("v_floor", ctypes.c_double),
+                ("alpha0", ctypes.c_double), ("Rdot0_ref", ctypes.c_double),
+                ("record_attempts", ctypes.c_int32), ("block_warps", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libpab.so (building it first if allowed); raises if it is unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libpab.so missing or stale at {path}; run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    cfgp = ctypes.POINTER(pab_config)
+    sig = {
+        "pab_config_default": (None, [cfgp]),
+        "pab_create": (i32, [cfgp, vp, ctypes.POINTER(vp)]),
+        "pab_bubble_step": (i32, [vp, vp, vp, dbl, vp, vp]),
+        "pab_moments": (i32, [vp, vp, vp, vp]),
+        "pab_bubble_step_host": (i32, [vp, vp, vp, dbl, vp, vp]),
+        "pab_status_flags": (i32, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64), ctypes.POINTER(i64), vp]),
+        "pab_get_state": (i32, [vp, vp, vp, vp, vp]),
+        "pab_set_state": (i32, [vp, vp, vp, vp, vp]),
+        "pab_get_attempts": (i32, [vp, vp, vp]),
+        "pab_get_bins": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pab_set_block_warps": (i32, [vp, i32]),
+        "pab_destroy": (None, [vp]),
+        "pab_last_error": (ctypes.c_char_p, [vp]),
+        "pab_status_string": (ctypes.c_char_p, [i32]),
+        "pab_peak_fma": (i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(dbl), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+# --------------------------------------------------------------------------
+# C names, argument marshalling only
+# --------------------------------------------------------------------------
+def status_string(s: int) -> str:
+    try:
+        return load().pab_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def pab_config_default(**overrides) -> pab_config:
+    cfg = pab_config()
+    load().pab_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(f"pab_config has no field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _check(h, st, what):
+    if st != PAB_OK:
+        msg = load().pab_last_error(h).decode() if h else ""
+        raise PabError(st, f"{what}: {msg}")
+
+
+def pab_create(cfg: pab_config, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    st = load().pab_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(out))
+    if st != PAB_OK:
+        raise PabError(st, "pab_create rejected the configuration (details on stderr)")
+    return out.value
+
+
+def pab_bubble_step(h: int, p_inf_ptr: int, nb_ptr: int, dt: float, moments_ptr: int, stream: int = 0):
+    _check(h, load().pab_bubble_step(h, p_inf_ptr or None, nb_ptr or None, float(dt),
+                                     moments_ptr or None, stream or None), "pab_bubble_step")
+
+
+def pab_moments(h: int, nb_ptr: int, moments_ptr: int, stream: int = 0):
+    _check(h, load().pab_moments(h, nb_ptr or None, moments_ptr or None, stream or None), "pab_moments")
+
+
+def pab_bubble_step_host(h: int, p_inf_host: int, nb_host: int, dt: float, moments_host: int,
+                         stream: int = 0):
+    _check(h, load().pab_bubble_step_host(h, p_inf_host or None, nb_host or None, float(dt),
+                                          moments_host or None, stream or None), "pab_bubble_step_host")
+
+
+def pab_status_flags(h: int, stream: int = 0, raise_on_error: bool = False):
+    fl = ctypes.c_uint32()
+    nf, na, n64 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = load().pab_status_flags(h, ctypes.byref(fl), ctypes.byref(nf), ctypes.byref(na),
+                                 ctypes.byref(n64), stream or None)
+    if st in (PAB_EINVAL, PAB_ECUDA) or (raise_on_error and st != PAB_OK):
+        _check(h, st, "pab_status_flags")
+    return dict(status=st, flags=fl.value, n_flagged=nf.value, n_attempts=na.value, n_fp64=n64.value)
+
+
+def pab_get_state(h, R_ptr, Rdot_ptr, h_ptr, stream=0):
+    _check(h, load().pab_get_state(h, R_ptr or None, Rdot_ptr or None, h_ptr or None, stream or None),
+           "pab_get_state")
+
+
+def pab_set_state(h, R_ptr, Rdot_ptr, h_ptr, stream=0):
+    _check(h, load().pab_set_state(h, R_ptr or None, Rdot_ptr or None, h_ptr or None, stream or None),
+           "pab_set_state")
+
+
+def pab_get_attempts(h, att_ptr, stream=0):
+    _check(h, load().pab_get_attempts(h, att_ptr or None, stream or None), "pab_get_attempts")
+
+
+def pab_get_bins(h, n_bins: int):
+    R0 = (ctypes.c_double * n_bins)()
+    w = (ctypes.c_double * n_bins)()
+    nb = ctypes.c_double()
+    _check(h, load().pab_get_bins(h, R0, w, ctypes.byref(nb)), "pab_get_bins")
+    return list(R0), list(w), nb.value
+
+
+def pab_set_block_warps(h, w):
+    _check(h, load().pab_set_block_warps(h, int(w)), "pab_set_block_warps")
+
+
+def pab_peak_fma(precision: int, blocks: int, threads: int, iters: int, sink_ptr: int, stream: int = 0):
+    """Returns (kernel ms, FMA count) of the FMA-throughput microbenchmark."""
+    ms = ctypes.c_float()
+    n = ctypes.c_double()
+    st = load().pab_peak_fma(int(precision), int(blocks), int(threads), int(iters), sink_ptr,
+                             ctypes.byref(ms), ctypes.byref(n), stream or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_peak_fma")
+    return ms.value, n.value
+
+
+def pab_destroy(h):
+    if h:
+        load().pab_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# torch convenience wrapper around one handle
+# --------------------------------------------------------------------------
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Solver:
+    """One resident ensemble: n_cells x n_bins bubble state on the current GPU."""
+
+    def __init__(self, n_cells: int, n_bins: int = 21, *, precision: str = "fp64",
+                 fixed_substeps: int = 0, stream=None, **cfg_overrides):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device; there is no CPU fallback")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        prec = {"fp64": PAB_FP64, "mixed": PAB_MIXED}[precision]
+        kw = dict(n_cells=int(n_cells), n_bins=int(n_bins), precision=prec)
+        if fixed_substeps:
+            kw.update(stepper=PAB_FIXED, n_fixed_sub=int(fixed_substeps))
+        kw.update(cfg_overrides)
+        self._keep = []
+        for key in ("R0_host", "w_host"):
+            if key in kw and kw[key] is not None and not isinstance(kw[key], ctypes.POINTER(ctypes.c_double)):
+                arr = (ctypes.c_double * len(kw[key]))(*[float(x) for x in kw[key]])
+                self._keep.append(arr)
+                kw[key] = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        self.cfg = pab_config_default(**kw)
+        self.n_cells = int(n_cells)
+        self.n_bins = int(n_bins)
+        self.precision = precision
+        self.handle = pab_create(self.cfg, _stream_handle(stream))
+        self.R0, self.w, self.nb_default = pab_get_bins(self.handle, self.n_bins)
+
+    # ---- checks -----------------------------------------------------------
+    def _dev(self, t, shape, dtype, name):
+        import torch
+        if t is None:
+            return 0
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype \
+                or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)} "
+                             f"on {self.device}")
+        return t.data_ptr()
+
+    # ---- entry points -----------------------------------------------------
+    def step(self, p_inf, dt: float, moments=None, nb=None, stream=None):
+        import torch
+        pab_bubble_step(self.handle, self._dev(p_inf, (self.n_cells,), torch.float64, "p_inf"),
+                        self._dev(nb, (self.n_cells,), torch.float64, "nb"), dt,
+                        self._dev(moments, (N_MOMENTS, self.n_cells), torch.float64, "moments"),
+                        _stream_handle(stream))
+        return moments
+
+    def moments(self, out=None, nb=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((N_MOMENTS, self.n_cells), dtype=torch.float64, device=self.device)
+        pab_moments(self.handle, self._dev(nb, (self.n_cells,), torch.float64, "nb"),
+                    self._dev(out, (N_MOMENTS, self.n_cells), torch.float64, "moments"),
+                    _stream_handle(stream))
+        return out
+
+    def step_host(self, p_inf_host, dt: float, moments_host=None, nb_host=None, stream=None):
+        """End-to-end form with host (CPU, ideally pinned) float64 tensors."""
+        import torch
+
+        def hp(t, shape, name):
+            if t is None:
+                return 0
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() \
+                    or tuple(t.shape) != tuple(shape):
+                raise ValueError(f"{name} must be a contiguous float64 CPU tensor of shape {shape}")
+            return t.data_ptr()
+        pab_bubble_step_host(self.handle, hp(p_inf_host, (self.n_cells,), "p_inf_host"),
+                             hp(nb_host, (self.n_cells,), "nb_host"), dt,
+                             hp(moments_host, (N_MOMENTS, self.n_cells), "moments_host"),
+                             _stream_handle(stream))
+        return moments_host
+
+    def status(self, stream=None, raise_on_error=False):
+        return pab_status_flags(self.handle, _stream_handle(stream), raise_on_error)
+
+    def get_state(self, stream=None):
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        R = torch.empty(shp, dtype=torch.float64, device=self.device)
+        V = torch.empty_like(R)
+        h = torch.empty(shp, dtype=torch.float32, device=self.device)
+        pab_get_state(self.handle, R.data_ptr(), V.data_ptr(), h.data_ptr(), _stream_handle(stream))
+        return R, V, h
+
+    def set_state(self, R, V, h=None, stream=None):
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        pab_set_state(self.handle, self._dev(R, shp, torch.float64, "R"),
+                      self._dev(V, shp, torch.float64, "Rdot"),
+                      self._dev(h, shp, torch.float32, "h"), _stream_handle(stream))
+
+    def attempts(self, stream=None):
+        import torch
+        a = torch.empty((self.n_bins, self.n_cells), dtype=torch.int32, device=self.device)
+        pab_get_attempts(self.handle, a.data_ptr(), _stream_handle(stream))
+        return a
+
+    def set_block_warps(self, w: int):
+        pab_set_block_warps(self.handle, w)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pab_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

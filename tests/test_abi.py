@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point
+include/pab.h declares, the ctypes config matches the C layout, and invalid
+calls are refused before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2511_21031_gb300 import pab
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h")]
+
+
+def _declared():
+    text = "".join(open(h).read() for h in HEADERS)
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pab_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = pab.load()
+    declared = _declared()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(pab.EXPORTS)
+
+
+def test_config_layout_matches_c():
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "pab.h"
+int main(void) {
+  printf("%zu", sizeof(pab_config));
+#define O(f) printf(" %s=%zu", #f, offsetof(pab_config, f));
+  O(n_cells) O(n_bins) O(gas_mode) O(rho) O(c) O(mu) O(sigma) O(p0) O(gamma) O(pv) O(R0ref)
+  O(s_lognormal) O(span_K) O(R0_host) O(w_host) O(precision) O(stepper) O(n_fixed_sub)
+  O(max_attempts) O(tol) O(v_floor) O(alpha0) O(Rdot0_ref) O(record_attempts) O(block_warps)
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(pab.pab_config)
+    for item in out[1:]:
+        k, v = item.split("=")
+        assert getattr(pab.pab_config, k).offset == int(v), k
+
+
+def test_config_defaults_are_water_and_paper_tolerance():
+    c = pab.pab_config_default()
+    assert (c.rho, c.c, c.mu, c.sigma, c.p0, c.gamma, c.pv) == (1000.0, 1500.0, 1e-3, 0.072, 101325.0, 1.4, 0.0)
+    assert c.tol == 1e-4 and c.n_bins == 21 and c.R0ref == 10e-6 and c.alpha0 == 4e-5
+
+
+@pytest.mark.parametrize("bad", [dict(n_bins=20), dict(n_bins=2), dict(n_bins=65), dict(n_cells=0),
+                                 dict(rho=-1.0), dict(tol=0.0), dict(stepper=1, n_fixed_sub=0),
+                                 dict(precision=7), dict(gas_mode=3), dict(max_attempts=0),
+                                 dict(n_bins=21, s_lognormal=0.0), dict(block_warps=17)])
+def test_invalid_configs_are_refused_without_device_work(bad):
+    cfg = pab.pab_config_default(**{"n_cells": 8, **bad})
+    out = ctypes.c_void_p()
+    st = pab.load().pab_create(ctypes.byref(cfg), None, ctypes.byref(out))
+    assert st == pab.PAB_EINVAL
+    assert out.value is None
+
+
+def test_null_handle_calls_return_einval():
+    lib = pab.load()
+    assert lib.pab_bubble_step(None, None, None, 1e-8, None, None) == pab.PAB_EINVAL
+    assert lib.pab_moments(None, None, None, None) == pab.PAB_EINVAL
+    assert lib.pab_status_flags(None, None, None, None, None, None) == pab.PAB_EINVAL
+    assert lib.pab_get_state(None, None, None, None, None) == pab.PAB_EINVAL
+    assert lib.pab_set_state(None, None, None, None, None) == pab.PAB_EINVAL
+    assert lib.pab_set_block_warps(None, 4) == pab.PAB_EINVAL
+    lib.pab_destroy(None)
+    assert lib.pab_last_error(None) == b"NULL handle"
+    assert pab.status_string(pab.PAB_ESTEP_LIMIT) == "PAB_ESTEP_LIMIT"
