@@ -42,12 +42,18 @@ NOMINAL_FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 1.25 TFLOP/s / (152 SMs x 2.07 GHz),
 NOMINAL_FP32_FLOPS_PER_CLK_PER_SM = 256.0  # 128 FP32 lanes x 2 (FMA)
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-# FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 kernel executes per trial
-# (sub-step attempt) and per bin-step outside the trial loop, counted with ncu
-# (sm__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64-cell
-# workload; profiles/step_kernel_fp64_grid128.md gives the capture.
-FP64_FLOPS_PER_TRIAL = 420.0
-FP64_FLOPS_PER_BINSTEP = 60.0
+# FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel executes per trial
+# (one sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination,
+# error norm, controller) and per bin-step outside the trial loop (wall
+# pressure and quadrature sums), counted with ncu
+# (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64^3 x 31
+# grid; profiles/step_kernel_fp64_grid128.md gives the capture and arithmetic.
+FP64_FLOPS_PER_TRIAL = 601.5
+FP64_FLOPS_PER_BINSTEP = 151.4
+# DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
+# on the 64^3 x 31 grid, 281.4 MB / 8.13M bin-steps); scaled by bin-steps.
+FP64_DRAM_BYTES_PER_BINSTEP = 34.6
+FP64_PIPE_ACTIVE_NCU = 0.86
 
 
 def _dist():
@@ -274,7 +280,9 @@ def run_ours(args):
         peak = NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * SM_MAX_MHZ * 1e6
         roof = {"bound": "alu", "achieved": flops_per_launch / avg_launch_s / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": flops_per_launch / avg_launch_s / peak, "traffic": None,
+                "frac": flops_per_launch / avg_launch_s / peak,
+                "traffic": FP64_DRAM_BYTES_PER_BINSTEP * wl.n_cells * wl.n_bins,
+                "fp64_pipe_active_ncu": FP64_PIPE_ACTIVE_NCU,
                 "pipe": "fp64", "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz",
                 "frac_at_measured_clock": flops_per_launch / avg_launch_s
                 / (NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * sm_mhz * 1e6)}
