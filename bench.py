@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 from paper_2511_21031_gb300 import workloads  # noqa: E402
 
 METRIC = "bin-steps/s (cells x bins x flow steps)"
-NOMINAL_FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 1.25 TFLOP/s / (152 SMs x 2.07 GHz), see the design doc
+NOMINAL_FP64_FLOPS_PER_CLK_PER_SM = 4.0   # nominal 1.25 TFLOP/s / (152 SMs x 2.07 GHz)
 NOMINAL_FP32_FLOPS_PER_CLK_PER_SM = 256.0  # 128 FP32 lanes x 2 (FMA)
 N_SM = 152
 SM_MAX_MHZ = 2070.0
@@ -47,7 +47,7 @@ SM_MAX_MHZ = 2070.0
 # error norm, controller) and per bin-step outside the trial loop (wall
 # pressure and quadrature sums), counted with ncu
 # (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64^3 x 31
-# grid; profiles/step_kernel_fp64_grid128.md gives the capture and arithmetic.
+# grid (three timed launches, 1.3267 trials per bin-step, plus one reduce-only launch).
 FP64_FLOPS_PER_TRIAL = 601.5
 FP64_FLOPS_PER_BINSTEP = 151.4
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
