@@ -169,6 +169,48 @@ pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double 
  * over the bins).  Used by the autotuner. */
 pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
 
+/*
+ * Allocation-free form of pab_bubble_step.  The paper has no counterpart of
+ * this entry point; it exists for callers that may not allocate device memory
+ * themselves or have a library allocate behind their back: a flow solver that
+ * owns every byte of the GPU through its own pre-sized pools (its memory
+ * budget is fixed, and a cudaMalloc from a library would break it or fail on a
+ * full device), or a plugin that receives device pointers from a host
+ * framework's allocator and must return them untouched in count and size.
+ *
+ * There is no handle: the caller passes the configuration and owns the whole
+ * state.  cfg is validated exactly as in pab_create (record_attempts and
+ * block_warps = 0 are ignored; 8 warps per CTA then).  The bin table is the one
+ * pab_create builds from cfg (R0_i = R0ref exp(-K s + i 2 K s/(Nb-1)) for Nb > 1).
+ * R_dev, Rdot_dev: FP64 [Nb][C] state, advanced in place (device).
+ * h_dev: FP32 [Nb][C] carried sub-step, in place (device; 0 before the first
+ *   call; may be NULL in PAB_FIXED mode only).
+ * p_inf_dev, nb_dev, dt, moments_dev: as in pab_bubble_step.
+ * status_dev: NULL, or 4 int64 on the device receiving, stream-ordered,
+ *   {flags, n_flagged, n_attempts, n_fp64} of this call (see pab_status_flags).
+ *
+ * The only scratch is one status block kept in a static device array of
+ * PAB_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  The block does not grow with the problem, so the
+ * only sizes refused (PAB_EINVAL, nothing launched) are those the kernel
+ * cannot take: n_bins outside 1..PAB_MAX_BINS (odd), n_cells < 1.  The call
+ * clears the block, launches the step kernel and copies the block out; it
+ * calls no cudaMalloc, cudaFree or allocating library routine.  Every call
+ * shares the block, so calls that overlap on the GPU (other streams, other
+ * threads) race on it and may report each other's counts; the state and the
+ * moments, which live in caller buffers, are not affected.
+ * The first call on a device looks up the block's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.
+ * Errors: PAB_EINVAL (bad cfg, NULL pointers, dt <= 0 or non-finite),
+ * PAB_ECUDA (symbol lookup or launch failure).
+ */
+#define PAB_NOALLOC_SCRATCH_BYTES 256
+pab_status pab_bubble_step_noalloc(const pab_config *cfg, const double *p_inf_dev,
+                                   const double *nb_dev, double dt, double *R_dev,
+                                   double *Rdot_dev, float *h_dev, double *moments_dev,
+                                   int64_t *status_dev, void *stream);
+
 /* Release the state on the creation stream.  NULL-safe. */
 void pab_destroy(pab_t *h);
 

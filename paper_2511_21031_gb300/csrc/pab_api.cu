@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "pab.h"
@@ -502,3 +503,97 @@ pab_status pab_set_block_warps(pab_t *h, int32_t block_warps)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.  Its only scratch, the status block of the
+// step kernel, lives in this static device array instead of a handle's
+// cudaMalloc'ed memory.  Host code cannot use the array's name as a device
+// address, so each device's address is looked up once, with that device
+// current, and cached.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PAB_NOALLOC_SCRATCH_BYTES];
+static_assert(sizeof(pab::Counters) <= PAB_NOALLOC_SCRATCH_BYTES, "status block exceeds the scratch");
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+cudaError_t noalloc_scratch(pab::Counters **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (pab::Counters *)g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const double *p_inf_dev,
+                                              const double *nb_dev, double dt, double *R_dev,
+                                              double *Rdot_dev, float *h_dev, double *moments_dev,
+                                              int64_t *status_dev, void *stream)
+{
+    if (!cfg || !p_inf_dev || !R_dev || !Rdot_dev)
+        return PAB_EINVAL;
+    if (!h_dev && cfg->stepper != PAB_FIXED)
+        return PAB_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return PAB_EINVAL;
+    char msg[256];
+    if (validate(cfg, msg, sizeof(msg)) != PAB_OK) {
+        fprintf(stderr, "pab_bubble_step_noalloc: %s\n", msg);
+        return PAB_EINVAL;
+    }
+    double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
+    if (cfg->R0_host) {
+        for (int i = 0; i < cfg->n_bins; ++i) {
+            R0[i] = cfg->R0_host[i];
+            w[i] = cfg->w_host[i];
+        }
+    } else if (!lognormal_table(cfg->n_bins, cfg->R0ref, cfg->s_lognormal, cfg->span_K, R0, w)) {
+        return PAB_EINVAL;
+    }
+    pab::StepConst K;
+    build_const(cfg, R0, w, &K);
+    pab::Counters *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "pab_bubble_step_noalloc: scratch lookup: %s\n", cudaGetErrorString(e));
+        return PAB_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(scratch, 0, sizeof(pab::Counters), s);
+    pab::StepArgs a;
+    a.p_inf = p_inf_dev;
+    a.nb = nb_dev;
+    a.dt = dt;
+    a.R = R_dev;
+    a.V = Rdot_dev;
+    a.h = h_dev;
+    a.attempts = nullptr;
+    a.out = moments_dev;
+    a.counters = scratch;
+    if (e == cudaSuccess)
+        e = pab::launch_step(K, cfg->precision, a, cfg->block_warps > 0 ? cfg->block_warps : 8, s);
+    if (e == cudaSuccess && status_dev)
+        e = cudaMemcpyAsync(status_dev, scratch, sizeof(pab::Counters), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "pab_bubble_step_noalloc: %s\n", cudaGetErrorString(e));
+        return PAB_ECUDA;
+    }
+    return PAB_OK;
+}

@@ -26,7 +26,8 @@ MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3R
 EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_bubble_step_host", "pab_status_flags", "pab_get_state", "pab_set_state",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
-           "pab_last_error", "pab_status_string", "pab_peak_fma")
+           "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc")
+NOALLOC_SCRATCH_BYTES = 256
 
 
 class PabError(RuntimeError):
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_status_string": (ctypes.c_char_p, [i32]),
         "pab_peak_fma": (i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(dbl), vp]),
+        "pab_bubble_step_noalloc": (i32, [cfgp, vp, vp, dbl, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +191,16 @@ def pab_peak_fma(precision: int, blocks: int, threads: int, iters: int, sink_ptr
     if st != PAB_OK:
         raise PabError(st, "pab_peak_fma")
     return ms.value, n.value
+
+
+def pab_bubble_step_noalloc(cfg: pab_config, p_inf_ptr: int, nb_ptr: int, dt: float, R_ptr: int,
+                            Rdot_ptr: int, h_ptr: int, moments_ptr: int, status_ptr: int, stream: int = 0):
+    """Allocation-free step on caller-owned state (no handle); see include/pab.h."""
+    st = load().pab_bubble_step_noalloc(ctypes.byref(cfg), p_inf_ptr or None, nb_ptr or None, float(dt),
+                                        R_ptr or None, Rdot_ptr or None, h_ptr or None,
+                                        moments_ptr or None, status_ptr or None, stream or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_bubble_step_noalloc (details on stderr)")
 
 
 def pab_destroy(h):
