@@ -189,6 +189,83 @@ def run_reference(args):
     return 0
 
 
+def _time_steps(solver, wl, ps, args, stream, clocks=None):
+    """Warm up, then time args.steps flow steps (one fused launch each) with CUDA events."""
+    import torch
+
+    from paper_2511_21031_gb300 import pab
+    ws, _, _ = _dist()
+    mom = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64, device=ps[0].device)
+    with torch.cuda.stream(stream):
+        for n in range(args.warmup):
+            solver.step(ps[n], wl.dt, moments=mom)
+    solver.status(stream=stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            solver.step(ps[args.warmup + k], wl.dt, moments=mom)
+            ev[k][1].record(stream)
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    st = solver.status(stream=stream)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=ps[0].device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return dict(ms_total=ms_total, launch_ms=launch_ms, status=st, clocks=clk, moments=mom)
+
+
+def _mixed_error_sample(wl, n_steps, n_cells=256):
+    """Error of the mixed path against the FP64 oracle on a seeded sample of cells
+    (outside any timed region)."""
+    import torch
+
+    import oracle
+    from paper_2511_21031_gb300 import pab
+    cells = np.sort(np.random.default_rng(12).choice(wl.n_cells, min(n_cells, wl.n_cells), replace=False))
+    sub = wl.subset(cells)
+    sol = pab.Solver(sub.n_cells, sub.n_bins, precision="mixed", s_lognormal=sub.s, R0ref=sub.R0ref,
+                     span_K=sub.span_K, alpha0=sub.alpha0)
+    mom = torch.empty((pab.N_MOMENTS, sub.n_cells), dtype=torch.float64, device="cuda")
+    P = oracle.Params(**sub.fluid)
+    R0, w = oracle.bins(sub.n_bins, sub.R0ref, sub.s, sub.span_K)
+    R = np.repeat(R0[:, None], sub.n_cells, axis=1).copy()
+    V = np.zeros_like(R)
+    h = np.zeros(R.shape, dtype=np.float32)
+    for n in range(n_steps):
+        p = sub.pressure_step(n)
+        sol.step(torch.as_tensor(p, device="cuda"), sub.dt, moments=mom)
+        oracle.step(P, R0, p, sub.dt, R, V, h)
+    mo = oracle.moments(P, R0, w, np.full(sub.n_cells, sol.nb_default), R, V)
+    Rg, Vg, _ = sol.get_state()
+    g = mom.cpu().numpy()
+    Rg = Rg.cpu().numpy()
+    scale = np.sum(w[:, None] * R * R * (np.abs(V) + 1e-2), axis=0)
+    out = {"R": float(np.max(np.abs(Rg - R) / R)),
+           "alpha": float(np.max(np.abs(g[1] - mo[1]) / mo[1])),
+           "R2Rdot": float(np.max(np.abs(g[3] - mo[3]) / scale)),
+           "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {n_steps} steps"}
+    sol.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -208,48 +285,17 @@ def run_ours(args):
     cpu = cpu_baseline(wl, seconds=args.cpu_seconds) if (rank == 0 and ws == 1 and args.cpu_seconds > 0) else None
 
     stream = torch.cuda.Stream()
+    total = args.warmup + args.steps
     with torch.cuda.stream(stream):
         solver = pab.Solver(wl.n_cells, wl.n_bins, precision=precision, s_lognormal=wl.s,
                             R0ref=wl.R0ref, span_K=wl.span_K, alpha0=wl.alpha0)
         if args.block_warps:
             solver.set_block_warps(args.block_warps)
-        total = args.warmup + args.steps
         ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
-        mom = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64, device=dev)
-        for n in range(args.warmup):
-            solver.step(ps[n], wl.dt, moments=mom)
-        solver.moments(out=mom)  # one reduce-only launch (profiled for its per-bin cost)
-        solver.status()
+        solver.moments()  # one reduce-only launch (profiled for its per-bin cost)
     torch.cuda.synchronize()
-
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        t_start.record(stream)
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            solver.step(ps[args.warmup + k], wl.dt, moments=mom)
-            ev[k][1].record(stream)
-        t_end.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    st = solver.status(stream=stream)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    res = _time_steps(solver, wl, ps, args, stream, clocks=ClockSampler(torch.cuda.current_device()))
+    ms_total, launch_ms, st, clk = res["ms_total"], res["launch_ms"], res["status"], res["clocks"]
 
     # end to end through the host-buffer C-ABI entry point (pinned host memory)
     n_e2e = max(1, min(args.steps, 10))
@@ -268,6 +314,8 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     solver.status(stream=stream)
+    solver.close()
+    del ps
 
     bin_steps = wl.n_cells * wl.n_bins * args.steps
     value = bin_steps * ws / (ms_total * 1e-3)
@@ -290,6 +338,31 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "pipe": "fp64+fp32"}
 
+    variants = []
+    if args.variants and ws == 1:
+        for name, vwl in (("grid128 mixed", wl), ("grid256 mixed", make_workload("grid256_mixed", rank))):
+            vs = pab.Solver(vwl.n_cells, vwl.n_bins, precision="mixed", s_lognormal=vwl.s,
+                            R0ref=vwl.R0ref, span_K=vwl.span_K, alpha0=vwl.alpha0)
+            with torch.cuda.stream(stream):
+                vps = [vwl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
+            torch.cuda.synchronize()
+            r = _time_steps(vs, vwl, vps, args, stream)
+            vbs = vwl.n_cells * vwl.n_bins * args.steps
+            variants.append({
+                "workload": vwl.name, "label": name, "precision": "mixed",
+                "value": vbs / (r["ms_total"] * 1e-3), "unit": "bin-steps/s",
+                "ms_per_step": r["ms_total"] / args.steps,
+                "latency_ms": {"p50": float(np.percentile(r["launch_ms"], 50)),
+                               "p99": float(np.percentile(r["launch_ms"], 99))},
+                "trials_per_bin_step": r["status"]["n_attempts"] / vbs,
+                "fp64_trial_fraction": r["status"]["n_fp64"] / max(1, r["status"]["n_attempts"]),
+                "speedup_vs_fp64_grid128": (vbs / (r["ms_total"] * 1e-3)) / value,
+                "error_vs_fp64_oracle": _mixed_error_sample(vwl, min(total, 40)),
+            })
+            vs.close()
+            del vps
+            torch.cuda.synchronize()
+
     fma = None
     if args.peak_probe:
         sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
@@ -308,7 +381,7 @@ def run_ours(args):
             "config": {"workload": wl.name, "cells": wl.n_cells, "bins": wl.n_bins, "s": wl.s,
                        "dt": wl.dt, "forcing": f"{wl.amp} p0 at {wl.freq:g} Hz", "precision": precision,
                        "stepper": "adaptive SSP-RK3(2) tol 1e-4",
-                       "l2": "state 20 B/bin x 65M bins > L2, no flush needed",
+                       "l2": "no flush: the state (20 B per bin-step) is larger than L2",
                        "parallelism": f"{ws} independent blocks (weak)", "seed": wl.seed},
             "gpu_launches": args.steps,
             "latency_ms": {"p50": float(np.percentile(launch_ms, 50)),
@@ -321,10 +394,11 @@ def run_ours(args):
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if variants:
+            line["variants"] = variants
         if fma:
             line["fma_probe"] = fma
         print(json.dumps(line), flush=True)
-    solver.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -342,6 +416,8 @@ def main():
     ap.add_argument("--edge", type=int, default=0, help="grid edge override (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--peak-probe", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the mixed-precision lines (128^3 and 256^3)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -163,6 +163,9 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->ic_rhof = (float)K->ic_rho;
     K->fmu_ic_rhof = (float)K->fmu_ic_rho;
     K->v_floorf = (float)K->v_floor;
+    K->cbrt_tolf = (float)K->cbrt_tol;
+    K->v_collapsef = (float)K->v_collapse;
+    K->r_collapsef = (float)K->r_collapse;
     double m3 = 0.0;
     for (int i = 0; i < c->n_bins; ++i) {
         pab::BinConst &b = K->bins[i];

@@ -230,6 +230,102 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
     return flags;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision adaptive advance.  Same controller as advance_adaptive, with
+// the trial's three right-hand sides in FP32 (deviation form) on increments
+// k_j = h f(stage j) from the accepted state:
+//   y3 - y = (k1 + k2)/6 + 2/3 k3,   y3 - z = (2 k3 - k1 - k2)/3.
+// FP64 holds the state, the embedded error estimate (the k's promoted and
+// combined in FP64), its norm and the accept decision, and the controller's
+// time bookkeeping (t, dt - t, landing on dt).  The growth factor is formed in
+// FP32: the proposal it scales is stored in FP32 between calls anyway.  The
+// FP32 images of the state (xi = R - R0, Rdot) are refreshed only when a trial
+// is accepted.  Bins near collapse (R < r_collapse R0 or |Rdot| > v_collapse)
+// take the FP64 trial.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinConst &bc,
+                                                  double p_inf, float A, double dt, double &R,
+                                                  double &V, float &hc, int &n_att, int &n64)
+{
+    double h = (double)hc;
+    if (!(h > 0.0) || h > dt)
+        h = dt;
+    double t = 0.0;
+    uint32_t flags = 0;
+    int n = 0;
+    float xi = (float)(R - bc.R0);
+    float v = (float)V;
+    const float xi_collapse = (K.r_collapsef - 1.0f) * bc.R0f;
+    for (;;) {
+        if (n >= K.max_attempts) {
+            flags |= PAB_FLAG_STEP_LIMIT;
+            break;
+        }
+        const double rem = dt - t;
+        const bool last = h >= rem;
+        const double ht = last ? rem : h;
+        double err, nR, nV;
+        bool ok;
+        if (xi < xi_collapse || fabsf(v) > K.v_collapsef) {
+            const Trial tr = trial64(K, bc, p_inf, R, V, ht);
+            ++n64;
+            err = error_norm(K, tr);
+            ok = tr.ok;
+            nR = tr.R;
+            nV = tr.V;
+        } else {
+            const float hf = (float)ht;
+            const float a1 = accel32(K, bc, A, xi, v);
+            const float k1R = hf * v, k1V = hf * a1;
+            const float v1 = v + k1V;
+            const float a2 = accel32(K, bc, A, xi + k1R, v1);
+            const float k2R = hf * v1, k2V = hf * a2;
+            const float e2R = 0.25f * (k1R + k2R), e2V = 0.25f * (k1V + k2V);
+            const float v2 = v + e2V;
+            const float a3 = accel32(K, bc, A, xi + e2R, v2);
+            const float k3R = hf * v2, k3V = hf * a3;
+            const float d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
+            const float d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
+            const double eR = fabs(2.0 * (double)k3R - ((double)k1R + (double)k2R));
+            const double eV = fabs(2.0 * (double)k3V - ((double)k1V + (double)k2V));
+            const float R3f = bc.R0f + (xi + d3R);
+            const float rR = 1.0f / (3.0f * fabsf(R3f));
+            const float rV = 1.0f / (3.0f * fmaxf(fabsf(v + d3V), K.v_floorf));
+            err = fmax(eR * (double)rR, eV * (double)rV);
+            ok = (bc.R0f + (xi + k1R) > 0.0f) && (bc.R0f + (xi + e2R) > 0.0f) && (R3f > 0.0f)
+              && isfinite(a1 + a2 + a3);
+            nR = R + (double)d3R;
+            nV = V + (double)d3V;
+        }
+        ++n;
+        float fac;
+        if (!ok || !(err <= DBL_MAX))
+            fac = 0.2f;
+        else if (err == 0.0)
+            fac = 5.0f;
+        else
+            fac = fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf((float)err), 0.2f), 5.0f);
+        if (ok && err <= K.tol) {
+            R = nR;
+            V = nV;
+            xi = (float)(R - bc.R0);
+            v = (float)V;
+            if (last) {
+                const bool clipped = rem < h;
+                h = (clipped && fac >= 1.0f) ? h : ht * (double)fac;
+                break;
+            }
+            t += ht;
+            h = ht * (double)fac;
+        } else {
+            h = ht * (double)fac;
+        }
+    }
+    hc = (float)h;
+    n_att = n;
+    return flags;
+}
+
 // Fixed mode: n equal trials of dt/n, no error estimate (MIXED: FP64 trials
 // only for bins near collapse, as in the adaptive mode).
 template <bool MIXED>

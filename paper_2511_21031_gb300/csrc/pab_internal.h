@@ -41,6 +41,7 @@ struct StepConst {
     double r_collapse;    // mixed: R/R0 below this takes the FP64 path (0.2)
     double nb_default;    // n_b when the caller passes no n_b field
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
+    float cbrt_tolf, v_collapsef, r_collapsef, padf;
     BinConst bins[PAB_MAX_BINS];
 };
 

@@ -190,7 +190,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             } else {
                 float hc = a.h[k];
                 int nd = 0;
-                fl = advance_adaptive<MIXED>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
+                if (MIXED)
+                    fl = advance_mixed(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
+                else
+                    fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
                 a.h[k] = hc;
                 n64 += nd;
             }
