@@ -266,6 +266,85 @@ def _mixed_error_sample(wl, n_steps, n_cells=256):
     return out
 
 
+def _bench_batched(args, stream, dev, n_instances=512):
+    """512 independent instances (edge U{16..96}, Nb in {11,21,31,51}, amplitude
+    U(0.3,1.5) p0, s U(0.2,0.7)) in one persistent mixed-precision launch per
+    step, replayed from a CUDA graph, launch shape from the autotuner."""
+    import torch
+
+    from paper_2511_21031_gb300 import autotune
+    from paper_2511_21031_gb300.batch import Batch
+    insts = workloads.batched_instances(n=n_instances)
+    tune = autotune.tune_batch(insts, precision="mixed")
+    bins = sum(w.n_cells * w.n_bins for w in insts)
+    cells = sum(w.n_cells for w in insts)
+    b = Batch(max_slots=len(insts), precision="mixed", capacity_bins=bins, max_bins=51)
+    b.set_launch(tune["block_warps"], tune["ctas_per_sm"], tune["bins_per_grab"])
+    total = args.warmup + args.steps
+    # one pressure field per step for all instances, generated on the device (outside timing)
+    theta = torch.empty(cells, dtype=torch.float64, device=dev)
+    amp = torch.empty(cells, dtype=torch.float64, device=dev)
+    offs, o = [], 0
+    for w in insts:
+        theta[o:o + w.n_cells] = torch.as_tensor(w.theta, device=dev)
+        amp[o:o + w.n_cells] = w.amp
+        offs.append(o)
+        o += w.n_cells
+    p0 = insts[0].fluid["p0"]
+    om = 2.0 * math.pi * insts[0].freq
+    ps = [p0 + p0 * amp * torch.sin(theta + om * (n + 0.5) * insts[0].dt) for n in range(total)]
+    del theta, amp
+    mom = torch.empty(7 * cells, dtype=torch.float64, device=dev)
+    slots = []
+    for w, off in zip(insts, offs):
+        s_ = b.admit(w.n_cells, w.n_bins, s_lognormal=w.s, R0ref=w.R0ref, span_K=w.span_K,
+                     alpha0=w.alpha0, **w.fluid)
+        slots.append((s_, w, off))
+
+    def bind(n):
+        for s_, w, off in slots:
+            b.bind(s_, ps[n][off:off + w.n_cells], w.dt,
+                   moments=mom[7 * off:7 * (off + w.n_cells)].view(7, w.n_cells))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for n in range(args.warmup):
+            bind(n)
+            b.step(graph=True, stream=stream)
+    torch.cuda.synchronize()
+    attempts0 = sum(b.status(s_, stream=stream)["n_attempts"] for s_, _, _ in slots)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            bind(args.warmup + k)   # host-side pointer update only
+            ev[k][0].record(stream)
+            b.step(graph=True, stream=stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(c) for a, c in ev]
+    st = [b.status(s_, stream=stream) for s_, _, _ in slots]
+    n_att = sum(x["n_attempts"] for x in st)
+    n64 = sum(x["n_fp64"] for x in st)
+    flags = 0
+    for x in st:
+        flags |= x["flags"]
+    b.close()
+    del ps, mom
+    torch.cuda.synchronize()
+    return {"workload": f"batched {len(insts)} instances", "label": "batched mixed (graph)",
+            "precision": "mixed", "instances": len(insts), "cells": cells, "bins": bins,
+            "value": bins * args.steps / (sum(ms) * 1e-3), "unit": "bin-steps/s",
+            "ms_per_step": sum(ms) / args.steps,
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "trials_per_bin_step": n_att / (bins * args.steps),
+            "fp64_trial_fraction": n64 / max(1, n_att), "status_flags": flags,
+            "launch": {"block_warps": tune["block_warps"], "ctas_per_sm": tune["ctas_per_sm"],
+                       "bins_per_grab": tune["bins_per_grab"], "autotuned": True,
+                       "cached": tune.get("cached", False)},
+            "warmup_attempts": attempts0}
+
+
 def run_ours(args):
     import torch
 
@@ -363,6 +442,11 @@ def run_ours(args):
             del vps
             torch.cuda.synchronize()
 
+    if args.variants and args.batched and ws == 1:
+        bv = _bench_batched(args, stream, dev)
+        bv["speedup_vs_fp64_grid128"] = bv["value"] / value
+        variants.append(bv)
+
     fma = None
     if args.peak_probe:
         sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
@@ -417,7 +501,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--peak-probe", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
-                    help="skip the mixed-precision lines (128^3 and 256^3)")
+                    help="skip the mixed-precision and batched lines")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 512-instance batched line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -184,6 +184,31 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
 
 }  // namespace
 
+namespace pab {
+
+pab_status validate_config(const pab_config *c, char *msg, size_t n) { return validate(c, msg, n); }
+
+bool bin_table(const pab_config *c, double *R0, double *w)
+{
+    if (c->R0_host) {
+        double sum = 0.0;
+        for (int i = 0; i < c->n_bins; ++i) {
+            R0[i] = c->R0_host[i];
+            w[i] = c->w_host[i];
+            sum += w[i];
+        }
+        return sum > 0.0;
+    }
+    return lognormal_table(c->n_bins, c->R0ref, c->s_lognormal, c->span_K, R0, w);
+}
+
+void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K)
+{
+    build_const(c, R0, w, K);
+}
+
+}  // namespace pab
+
 extern "C" {
 
 void pab_config_default(pab_config *c)

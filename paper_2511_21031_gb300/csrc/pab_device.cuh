@@ -344,4 +344,59 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
     }
 }
 
+// ---------------------------------------------------------------------------
+// One (bin, cell) over one flow step: non-finite checks, fixed or adaptive
+// advance, status bits.  R, V and hc are updated in place.
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinConst &bc, double p_inf,
+                                                bool p_ok, double dt, double &R, double &V, float &hc,
+                                                int &na, int &n64)
+{
+    na = 0;
+    n64 = 0;
+    if (!p_ok || !isfinite(R) || !isfinite(V))
+        return PAB_FLAG_NONFINITE;
+    uint32_t fl = 0;
+    const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
+    if (K.n_fixed > 0) {
+        advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V);
+        na = K.n_fixed;
+    } else if (MIXED) {
+        fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64);
+    } else {
+        fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64);
+    }
+    if (!isfinite(R) || !isfinite(V))
+        fl |= PAB_FLAG_NONFINITE;
+    else if (!(R > 0.0))
+        fl |= PAB_FLAG_NONPOS;
+    if (fabs(V) >= K.c)
+        fl |= PAB_FLAG_SUPERSONIC;
+    return fl;
+}
+
+// Quadrature terms of one bin at (R, Rdot): w R^3, w R^2 Rdot, w R^3 p_bw,
+// w R^3 Rdot^2 (the wall pressure in FP64, or in FP32 deviation form in MIXED).
+template <bool MIXED>
+__device__ __forceinline__ void quad_terms(const StepConst &K, const BinConst &bc, double R, double V,
+                                           double t[4])
+{
+    const double wr2 = bc.w * R * R;
+    const double wr3 = wr2 * R;
+    double pbw;
+    if (MIXED) {
+        const float xi = (float)(R - bc.R0);
+        const float u = xi * bc.invR0f;
+        const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
+        pbw = bc.peq + (double)(pgdev + (K.two_sigmaf * u - K.four_muf * (float)V) / (float)R);
+    } else {
+        pbw = wall_pressure64(K, bc, R, V);
+    }
+    t[0] = wr3;
+    t[1] = wr2 * V;
+    t[2] = wr3 * pbw;
+    t[3] = wr3 * V * V;
+}
+
 }  // namespace pab

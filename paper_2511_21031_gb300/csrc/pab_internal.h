@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "pab.h"
@@ -65,6 +66,12 @@ struct StepArgs {
     double *out;           // [7][C] or nullptr
     Counters *counters;
 };
+
+// Configuration helpers (pab_api.cu): validation as pab_create does it, the
+// bin table of a configuration, and the kernel constants.
+pab_status validate_config(const pab_config *c, char *msg, size_t n);
+bool bin_table(const pab_config *c, double *R0, double *w);
+void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K);
 
 // Launchers (pab_kernels.cu).  Return the launch error.
 cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,

@@ -12,7 +12,7 @@ import pytest
 from paper_2511_21031_gb300 import pab
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h")]
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h")]
 
 
 def _declared():
@@ -27,7 +27,9 @@ def test_library_exports_every_declared_entry_point():
     assert len(declared) >= 14
     for name in declared:
         assert hasattr(lib, name), name
-    assert set(declared) == set(pab.EXPORTS)
+    from paper_2511_21031_gb300 import batch
+    batch.load()
+    assert set(declared) == set(pab.EXPORTS) | set(batch.EXPORTS)
 
 
 def test_config_layout_matches_c():
@@ -54,6 +56,47 @@ int main(void) {
     for item in out[1:]:
         k, v = item.split("=")
         assert getattr(pab.pab_config, k).offset == int(v), k
+
+
+def test_batch_config_layout_matches_c():
+    from paper_2511_21031_gb300 import batch
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "pab_batch.h"
+int main(void) {
+  printf("%zu", sizeof(pab_batch_config));
+#define O(f) printf(" %s=%zu", #f, offsetof(pab_batch_config, f));
+  O(max_slots) O(precision) O(capacity_bins) O(block_warps) O(ctas_per_sm) O(bins_per_grab) O(max_bins)
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(batch.pab_batch_config)
+    for item in out[1:]:
+        k, v = item.split("=")
+        assert getattr(batch.pab_batch_config, k).offset == int(v), k
+    c = batch.pab_batch_config_default()
+    assert c.max_slots == 512 and c.precision == pab.PAB_MIXED and c.max_bins == pab.MAX_BINS
+
+
+def test_invalid_batch_configs_are_refused_without_device_work():
+    from paper_2511_21031_gb300 import batch
+    lib = batch.load()
+    for bad in (dict(max_slots=0), dict(max_slots=5000), dict(precision=3), dict(block_warps=17),
+                dict(ctas_per_sm=9), dict(bins_per_grab=9), dict(max_bins=64), dict(capacity_bins=-1)):
+        c = batch.pab_batch_config_default(**bad)
+        out = ctypes.c_void_p()
+        assert lib.pab_batch_create(ctypes.byref(c), None, ctypes.byref(out)) == pab.PAB_EINVAL
+        assert out.value is None
+    assert lib.pab_batch_step(None, None) == pab.PAB_EINVAL
+    assert lib.pab_batch_bind(None, 0, None, None, None, 1e-8) == pab.PAB_EINVAL
+    lib.pab_batch_destroy(None)
 
 
 def test_config_defaults_are_water_and_paper_tolerance():
