@@ -345,6 +345,30 @@ def _bench_batched(args, stream, dev, n_instances=512):
             "warmup_attempts": attempts0}
 
 
+def _bench_serving(args, n_requests=16, rate=200.0):
+    """The first n_requests of the seeded Poisson stream (200 req/s; edge lognormal
+    median 78.4 clipped to [32, 192]; Nb in {21, 31}; 200 flow steps each, mixed),
+    served by continuous batching on the wall clock."""
+    from paper_2511_21031_gb300 import autotune
+    from paper_2511_21031_gb300.serve import ServingEngine
+    reqs = workloads.request_stream(n=n_requests, rate=rate)
+    tune = autotune.tune_batch([r.work for r in reqs], precision="mixed", sample=8)
+    eng = ServingEngine(capacity_bins=2_000_000_000, max_slots=256,
+                        launch=(tune["block_warps"], tune["ctas_per_sm"], tune["bins_per_grab"]))
+    rep = eng.run(reqs, clock="wall")
+    eng.close()
+    offered = rate * float(np.mean([r.work.bins_total * r.work.n_steps for r in reqs]))
+    return {"workload": f"serving {n_requests} requests at {rate:g} req/s", "label": "serving mixed",
+            "precision": "mixed", "requests": n_requests,
+            "value": rep["throughput_bin_steps_per_s"], "unit": "bin-steps/s",
+            "gpu_value": rep["gpu_throughput_bin_steps_per_s"],
+            "latency_s": rep["latency_s"], "concurrency": rep["concurrency"],
+            "iterations": rep["iterations"], "elapsed_s": rep["elapsed_s"],
+            "offered_bin_steps_per_s": offered, "status_flags": rep["flags"],
+            "launch": {"block_warps": tune["block_warps"], "ctas_per_sm": tune["ctas_per_sm"],
+                       "bins_per_grab": tune["bins_per_grab"], "autotuned": True}}
+
+
 def run_ours(args):
     import torch
 
@@ -447,6 +471,9 @@ def run_ours(args):
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
         variants.append(bv)
 
+    if args.variants and args.serving and ws == 1:
+        variants.append(_bench_serving(args))
+
     fma = None
     if args.peak_probe:
         sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
@@ -504,6 +531,8 @@ def main():
                     help="skip the mixed-precision and batched lines")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 512-instance batched line")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the continuous-batching serving line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

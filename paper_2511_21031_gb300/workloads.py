@@ -163,14 +163,14 @@ class Request:
 
 
 def request_stream(n: int = 2000, rate: float = 200.0, seed: int = 6, n_steps: int = 200,
-                   edge_lo: int = 32, edge_hi: int = 192) -> List[Request]:
+                   edge_lo: int = 32, edge_hi: int = 192, edge_median: float = 78.4) -> List[Request]:
     """Poisson arrivals; edge L lognormal (median 78.4, log-sd ln6/4) clipped; Nb in {21, 31}."""
     g = _rng(seed)
     t = 0.0
     out = []
     for i in range(n):
         t += float(g.exponential(1.0 / rate))
-        L = int(round(math.exp(g.normal(math.log(78.4), math.log(6.0) / 4.0))))
+        L = int(round(math.exp(g.normal(math.log(edge_median), math.log(6.0) / 4.0))))
         L = min(max(L, edge_lo), edge_hi)
         nb = int(g.choice((21, 31)))
         sd = seed * 100003 + i
