@@ -23,23 +23,28 @@ struct Trial {
 //   d/dt p_bw = -3 gamma (p_b - pv) Rdot/R + (4 mu Rdot + 2 sigma) Rdot/R^2 - 4 mu Rddot/R
 // The Rddot inside d/dt p_bw moves to the left-hand side, whose coefficient
 // becomes R (1 - Rdot/c) + 4 mu/(rho c).  1/c = 0 gives Rayleigh-Plesset.
+// (R0/R)^(3 gamma) is exp(3 gamma log(R0/R)) with CUDA's log and exp: R0/R
+// stays within a few units of 1, where this differs from pow by a few ulp.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double p_inf,
                                           double R, double V)
 {
-    const double iR = 1.0 / R;
+    const double icV = V * K.inv_c;
+    const double den = fma(R, 1.0 - icV, K.fmu_ic_rho);
+    // one division gives both reciprocals: 1/R = den/(R den), 1/den = R/(R den)
+    const double inv = 1.0 / (R * den);
+    const double iR = den * inv;
+    const double iden = R * inv;
     const double VR = V * iR;
     double pg = 0.0;
     if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = bc.pg0 * pow(bc.R0 * iR, K.three_gamma);
+        pg = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));  // p_g0 (R0/R)^(3 gamma)
     const double s = fma(K.four_mu, V, K.two_sigma);
     const double pbw = (K.pv + pg) - s * iR;
     const double dpbw = (s * iR - K.three_gamma * pg) * VR;
-    const double icV = V * K.inv_c;
     const double num = (pbw - p_inf) * K.inv_rho * (1.0 + icV) + R * K.ic_rho * dpbw
                      - 1.5 * V * V * (1.0 - icV * (1.0 / 3.0));
-    const double den = fma(R, 1.0 - icV, K.fmu_ic_rho);
-    return num / den;
+    return num * iden;
 }
 
 // Wall pressure p_bw at (R, Rdot) in FP64 (for the <R^3 p_bw> moment).
@@ -49,7 +54,7 @@ __device__ __forceinline__ double wall_pressure64(const StepConst &K, const BinC
     const double iR = 1.0 / R;
     double pg = 0.0;
     if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = bc.pg0 * pow(bc.R0 * iR, K.three_gamma);
+        pg = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));
     return (K.pv + pg) - fma(K.four_mu, V, K.two_sigma) * iR;
 }
 
