@@ -104,6 +104,16 @@ def _lib():
             lib.orc_linear_advance.argtypes = [_dp, _dp, _fp, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_int32, _i32p]
             lib.orc_linear_advance.restype = ctypes.c_uint32
+            lib.orc_cons_from_prim.argtypes = [ctypes.c_int64, ctypes.c_int32, _dp, _dp, _dp, _dp, _dp]
+            lib.orc_cons_from_prim.restype = None
+            lib.orc_prim_from_cons.argtypes = [ctypes.c_int64, ctypes.c_int32, _dp, _dp, _dp, _dp,
+                                               _dp, _dp, _dp]
+            lib.orc_prim_from_cons.restype = None
+            lib.orc_mixture_pressure.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, _dp]
+            lib.orc_mixture_pressure.restype = None
+            lib.orc_stiffened_gas.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
+                                              ctypes.c_double, _dp]
+            lib.orc_stiffened_gas.restype = None
             _LIB = lib
     return _LIB
 
@@ -205,3 +215,54 @@ def linear_advance(A, y, h, dt, tol, v_floor, max_attempts=100000):
 def equilibrium_nb(alpha0: float, R0, w) -> float:
     """n_b from the initial void fraction at the equilibrium state (Eq. e:ndf)."""
     return alpha0 / (4.0 / 3.0 * math.pi * float(np.dot(_f64(w), _f64(R0) ** 3)))
+
+
+def cons_from_prim(n_b, R, Rdot):
+    """Conservative bubble variables qR = n_b R, qV = n_b Rdot ([B][C])."""
+    n_b = _f64(n_b)
+    R = _f64(R)
+    Rdot = _f64(Rdot)
+    B, C = R.shape
+    qR = np.zeros_like(R)
+    qV = np.zeros_like(R)
+    _lib().orc_cons_from_prim(C, B, _ptr(n_b, _dp), _ptr(R, _dp), _ptr(Rdot, _dp), _ptr(qR, _dp),
+                              _ptr(qV, _dp))
+    return qR, qV
+
+
+def prim_from_cons(w, alpha, qR, qV):
+    """Primitive R, Rdot and n_b from alpha and the conservative variables (Eq. e:ndf)."""
+    w = _f64(w)
+    alpha = _f64(alpha)
+    qR = _f64(qR)
+    qV = _f64(qV)
+    B, C = qR.shape
+    R = np.zeros_like(qR)
+    V = np.zeros_like(qR)
+    nb = np.zeros(C)
+    _lib().orc_prim_from_cons(C, B, _ptr(w, _dp), _ptr(alpha, _dp), _ptr(qR, _dp), _ptr(qV, _dp),
+                              _ptr(R, _dp), _ptr(V, _dp), _ptr(nb, _dp))
+    return R, V, nb
+
+
+def mixture_pressure(moments, p_l, rho_l=None, rho_default=1000.0):
+    """Mixture pressure of Eq. (e:pressure) from the [7][C] moments and p_l [C]."""
+    moments = _f64(moments)
+    p_l = _f64(p_l)
+    C = p_l.shape[0]
+    out = np.zeros(C)
+    rl = _f64(rho_l) if rho_l is not None else None
+    _lib().orc_mixture_pressure(C, _ptr(moments, _dp), _ptr(p_l, _dp),
+                                _ptr(rl, _dp) if rl is not None else None, float(rho_default),
+                                _ptr(out, _dp))
+    return out
+
+
+def stiffened_gas(rho_l, e_l, gamma_l, pi_inf):
+    """Liquid pressure of the stiffened-gas EOS, Eq. (eos_liquid)."""
+    rho_l = _f64(rho_l)
+    e_l = _f64(e_l)
+    out = np.zeros_like(rho_l)
+    _lib().orc_stiffened_gas(rho_l.size, _ptr(rho_l, _dp), _ptr(e_l, _dp), float(gamma_l),
+                             float(pi_inf), _ptr(out, _dp))
+    return out

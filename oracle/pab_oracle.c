@@ -432,3 +432,69 @@ uint32_t orc_linear_advance(const double A[4], double y[2], float *h, double dt,
     lin_ctx L = {{A[0], A[1], A[2], A[3]}};
     return advance_adaptive(lin_rhs_fn, &L, y, h, dt, tol, v_floor, max_attempts, n_attempts);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Carrier-facing forms (Sec. 2.2, Listing 2): conservative bubble variables */
+/* ------------------------------------------------------------------------ */
+/*
+ * The transported bubble variables are n_b phi (Eq. for d(n_b phi)/dt), stored
+ * per bin as qR_i = n_b R_i and qV_i = n_b Rdot_i (Listing 2 writes nbub*R).
+ * Primitive -> conservative is that product.  Conservative -> primitive needs
+ * n_b: from alpha = 4/3 pi n_b sum w R^3 (Eq. e:ndf) with R_i = qR_i / n_b,
+ *   alpha = 4/3 pi sum w qR^3 / n_b^2  =>  n_b = sqrt(4/3 pi sum w qR^3 / alpha).
+ * Layout [B][C]; alpha, n_b per cell [C].
+ */
+void orc_cons_from_prim(int64_t C, int32_t B, const double *n_b, const double *R,
+                        const double *Rdot, double *qR, double *qV)
+{
+    for (int32_t b = 0; b < B; ++b)
+        for (int64_t c = 0; c < C; ++c) {
+            size_t k = (size_t)b * (size_t)C + (size_t)c;
+            qR[k] = n_b[c] * R[k];
+            qV[k] = n_b[c] * Rdot[k];
+        }
+}
+
+void orc_prim_from_cons(int64_t C, int32_t B, const double *w, const double *alpha,
+                        const double *qR, const double *qV, double *R, double *Rdot, double *n_b)
+{
+    for (int64_t c = 0; c < C; ++c) {
+        double s = 0.0;
+        for (int32_t b = 0; b < B; ++b) {
+            double q = qR[(size_t)b * (size_t)C + (size_t)c];
+            s += w[b] * q * q * q;
+        }
+        double nb = sqrt(4.0 / 3.0 * M_PI * s / alpha[c]);
+        n_b[c] = nb;
+        for (int32_t b = 0; b < B; ++b) {
+            size_t k = (size_t)b * (size_t)C + (size_t)c;
+            R[k] = qR[k] / nb;
+            Rdot[k] = qV[k] / nb;
+        }
+    }
+}
+
+/*
+ * Mixture pressure, Eq. (e:pressure):
+ *   p = (1 - alpha) p_l + alpha (<R^3 p_bw>/<R^3> - rho <R^3 Rdot^2>/<R^3>),
+ * with alpha and the two ratios taken from the moments rows 1, 5 and 6 and rho
+ * the liquid density (rho_l per cell, or rho_default when rho_l is NULL).
+ * moments is [7][C].
+ */
+void orc_mixture_pressure(int64_t C, const double *moments, const double *p_l, const double *rho_l,
+                          double rho_default, double *p)
+{
+    for (int64_t c = 0; c < C; ++c) {
+        double alpha = moments[1 * C + c];
+        double rho = rho_l ? rho_l[c] : rho_default;
+        p[c] = (1.0 - alpha) * p_l[c] + alpha * (moments[5 * C + c] - rho * moments[6 * C + c]);
+    }
+}
+
+/* Stiffened-gas liquid pressure, Eq. (eos_liquid): p_l = (gamma_l - 1) rho_l e_l - gamma_l pi_inf. */
+void orc_stiffened_gas(int64_t n, const double *rho_l, const double *e_l, double gamma_l,
+                       double pi_inf, double *p_l)
+{
+    for (int64_t i = 0; i < n; ++i)
+        p_l[i] = (gamma_l - 1.0) * rho_l[i] * e_l[i] - gamma_l * pi_inf;
+}

@@ -477,3 +477,65 @@ def test_oracle_matches_its_golden_regression_fixture():
     np.testing.assert_allclose(R.ravel(), stored["R"], rtol=1e-13)
     np.testing.assert_allclose(V.ravel(), stored["Rdot"], rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(mom.ravel(), stored["moments"], rtol=1e-9, atol=1e-20)
+
+
+# ----------------------------------------------------------------------------
+# Carrier-facing forms: conservative variables, mixture pressure, stiffened gas
+# ----------------------------------------------------------------------------
+def test_conservative_round_trip_recovers_nb_from_alpha():
+    """n_b from alpha (Eq. e:ndf) inverts the product n_b R: alpha computed by the
+    moments (independent code) and q = n_b R give back n_b, R and Rdot."""
+    g = np.random.default_rng(40)
+    R0, w = oracle.bins(21, 10e-6, 0.3, 5.0)
+    C = 50
+    R = R0[:, None] * g.uniform(0.3, 3.0, size=(21, C))
+    V = g.normal(size=(21, C))
+    nb = g.uniform(1e8, 1e12, size=C)
+    alpha = oracle.moments(WATER, R0, w, nb, R, V)[1]
+    qR, qV = oracle.cons_from_prim(nb, R, V)
+    np.testing.assert_allclose(qR, nb * R, rtol=1e-15)
+    R2, V2, nb2 = oracle.prim_from_cons(w, alpha, qR, qV)
+    np.testing.assert_allclose(nb2, nb, rtol=1e-14)
+    np.testing.assert_allclose(R2, R, rtol=1e-14)
+    np.testing.assert_allclose(V2, V, rtol=1e-14, atol=1e-30)
+
+
+def test_mixture_pressure_limits_and_equilibrium():
+    R0, w = oracle.bins(31, 10e-6, 0.5, 5.0)
+    C = 4
+    alphas = np.array([0.0, 1e-5, 1e-2, 1.0])
+    nb = np.array([oracle.equilibrium_nb(max(a, 1e-30), R0, w) for a in alphas])
+    R = np.repeat(R0[:, None], C, axis=1)
+    V = np.zeros_like(R)
+    m = oracle.moments(WATER, R0, w, nb, R, V)
+    p_l = np.full(C, 2.5e5)
+    p = oracle.mixture_pressure(m, p_l)
+    # at rest the bubbles contribute p_bw = p0: p = (1 - alpha) p_l + alpha p0
+    np.testing.assert_allclose(p, (1 - m[1]) * p_l + m[1] * WATER.p0, rtol=1e-14)
+    assert p[0] == pytest.approx(2.5e5, rel=1e-15)
+    np.testing.assert_allclose(oracle.mixture_pressure(m, np.full(C, WATER.p0)), WATER.p0, rtol=1e-14)
+
+
+def test_mixture_pressure_is_linear_in_the_moments():
+    g = np.random.default_rng(41)
+    C = 30
+    m = g.uniform(0.1, 1.0, size=(7, C))
+    m[1] = g.uniform(0, 0.05, size=C)
+    m[5] = g.uniform(5e4, 2e5, size=C)
+    m[6] = g.uniform(0, 100, size=C)
+    p_l = g.uniform(5e4, 3e5, size=C)
+    rho = g.uniform(900, 1100, size=C)
+    p = oracle.mixture_pressure(m, p_l, rho)
+    a = m[1]
+    expect = p_l - a * p_l + a * m[5] - a * rho * m[6]
+    np.testing.assert_allclose(p, expect, rtol=1e-12)
+
+
+def test_stiffened_gas_inverts_its_energy():
+    """e_l = (p_l + gamma_l pi_inf) / ((gamma_l - 1) rho_l) gives back p_l."""
+    g = np.random.default_rng(42)
+    gam, pinf = 6.12, 3.43e8
+    p_l = g.uniform(-5e4, 5e6, size=100)
+    rho = g.uniform(950, 1050, size=100)
+    e = (p_l + gam * pinf) / ((gam - 1.0) * rho)
+    np.testing.assert_allclose(oracle.stiffened_gas(rho, e, gam, pinf), p_l, rtol=0, atol=1e-6 * gam * pinf * 1e-3)
