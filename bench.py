@@ -48,12 +48,12 @@ SM_MAX_MHZ = 2070.0
 # pressure and quadrature sums), counted with ncu
 # (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64^3 x 31
 # grid (three timed launches, 1.3267 trials per bin-step, plus one reduce-only launch).
-FP64_FLOPS_PER_TRIAL = 601.5
-FP64_FLOPS_PER_BINSTEP = 151.4
+FP64_FLOPS_PER_TRIAL = 429.3
+FP64_FLOPS_PER_BINSTEP = 103.4
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
-# on the 64^3 x 31 grid, 281.4 MB / 8.13M bin-steps); scaled by bin-steps.
+# on the 64^3 x 31 grid, 280.8 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 34.6
-FP64_PIPE_ACTIVE_NCU = 0.86
+FP64_PIPE_ACTIVE_NCU = 0.856
 
 
 def _dist():

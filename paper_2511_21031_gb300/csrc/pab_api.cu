@@ -12,6 +12,7 @@
 #include <new>
 
 #include "pab.h"
+#include "pab_closure.h"
 #include "pab_internal.h"
 
 struct pab_s {
@@ -528,6 +529,68 @@ pab_status pab_set_block_warps(pab_t *h, int32_t block_warps)
         return fail(h, PAB_EINVAL, "block_warps must be 1..16");
     h->block_warps = block_warps;
     return PAB_OK;
+}
+
+// ---- carrier-facing forms (pab_closure.h) ---------------------------------
+
+pab_status pab_strang_half(pab_t *h, const double *p_inf_dev, const double *nb_dev, double dt_flow,
+                           double *moments_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!(dt_flow > 0.0) || !std::isfinite(dt_flow))
+        return fail(h, PAB_EINVAL, "pab_strang_half: dt_flow must be positive and finite");
+    return pab_bubble_step(h, p_inf_dev, nb_dev, 0.5 * dt_flow, moments_dev, stream);
+}
+
+pab_status pab_get_conservative(pab_t *h, const double *nb_dev, double *qR_dev, double *qV_dev,
+                                void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!qR_dev || !qV_dev)
+        return fail(h, PAB_EINVAL, "pab_get_conservative: NULL output");
+    cudaError_t e = pab::launch_cons_from_prim(h->K, nb_dev, h->R, h->V, qR_dev, qV_dev,
+                                               (cudaStream_t)stream);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_get_conservative");
+}
+
+pab_status pab_set_conservative(pab_t *h, const double *alpha_dev, const double *qR_dev,
+                                const double *qV_dev, double *nb_out_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!alpha_dev || !qR_dev || !qV_dev)
+        return fail(h, PAB_EINVAL, "pab_set_conservative: NULL input");
+    cudaError_t e = pab::launch_prim_from_cons(h->K, alpha_dev, qR_dev, qV_dev, h->R, h->V, nb_out_dev,
+                                               (cudaStream_t)stream);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_set_conservative");
+}
+
+pab_status pab_mixture_pressure(pab_t *h, const double *moments_dev, const double *p_l_dev,
+                                const double *rho_l_dev, double *p_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!moments_dev || !p_l_dev || !p_dev)
+        return fail(h, PAB_EINVAL, "pab_mixture_pressure: NULL pointer");
+    cudaError_t e = pab::launch_mixture_pressure(h->K.C, moments_dev, p_l_dev, rho_l_dev, h->K.rho,
+                                                 p_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_mixture_pressure");
+}
+
+pab_status pab_stiffened_gas(int64_t n, const double *rho_l_dev, const double *e_l_dev, double gamma_l,
+                             double pi_inf, double *p_l_dev, void *stream)
+{
+    if (n < 0 || !(gamma_l > 1.0) || !std::isfinite(gamma_l) || !std::isfinite(pi_inf))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    if (!rho_l_dev || !e_l_dev || !p_l_dev)
+        return PAB_EINVAL;
+    cudaError_t e = pab::launch_stiffened_gas(n, rho_l_dev, e_l_dev, gamma_l, pi_inf, p_l_dev,
+                                              (cudaStream_t)stream);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
 }
 
 }  // extern "C"

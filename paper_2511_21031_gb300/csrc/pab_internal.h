@@ -81,4 +81,16 @@ cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, 
 cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
                         float *h, cudaStream_t s);
 
+// Launchers of the carrier-facing forms (pab_closure.cu).
+cudaError_t launch_cons_from_prim(const StepConst &K, const double *nb, const double *R,
+                                  const double *V, double *qR, double *qV, cudaStream_t s);
+cudaError_t launch_prim_from_cons(const StepConst &K, const double *alpha, const double *qR,
+                                  const double *qV, double *R, double *V, double *nb_out,
+                                  cudaStream_t s);
+cudaError_t launch_mixture_pressure(long long C, const double *moments, const double *p_l,
+                                    const double *rho_l, double rho_default, double *p,
+                                    cudaStream_t s);
+cudaError_t launch_stiffened_gas(long long n, const double *rho, const double *e, double gamma_l,
+                                 double pi_inf, double *p, cudaStream_t s);
+
 }  // namespace pab

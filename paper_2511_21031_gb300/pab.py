@@ -26,7 +26,9 @@ MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3R
 EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_bubble_step_host", "pab_status_flags", "pab_get_state", "pab_set_state",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
-           "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc")
+           "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
+           "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
+           "pab_stiffened_gas")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -88,6 +90,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_peak_fma": (i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(dbl), vp]),
         "pab_bubble_step_noalloc": (i32, [cfgp, vp, vp, dbl, vp, vp, vp, vp, vp, vp]),
+        "pab_strang_half": (i32, [vp, vp, vp, dbl, vp, vp]),
+        "pab_get_conservative": (i32, [vp, vp, vp, vp, vp]),
+        "pab_set_conservative": (i32, [vp, vp, vp, vp, vp, vp]),
+        "pab_mixture_pressure": (i32, [vp, vp, vp, vp, vp, vp]),
+        "pab_stiffened_gas": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -201,6 +208,21 @@ def pab_bubble_step_noalloc(cfg: pab_config, p_inf_ptr: int, nb_ptr: int, dt: fl
                                         moments_ptr or None, status_ptr or None, stream or None)
     if st != PAB_OK:
         raise PabError(st, "pab_bubble_step_noalloc (details on stderr)")
+
+
+def pab_stiffened_gas(rho_l, e_l, gamma_l: float, pi_inf: float, out=None, stream=None):
+    """Stiffened-gas liquid pressure (torch float64 CUDA tensors of equal length)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(rho_l)
+    for t in (rho_l, e_l, out):
+        if t.dtype != torch.float64 or not t.is_contiguous() or not t.is_cuda or t.numel() != rho_l.numel():
+            raise ValueError("rho_l, e_l and out must be contiguous float64 CUDA tensors of equal size")
+    st = load().pab_stiffened_gas(rho_l.numel(), rho_l.data_ptr(), e_l.data_ptr(), float(gamma_l),
+                                  float(pi_inf), out.data_ptr(), _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_stiffened_gas")
+    return out
 
 
 def pab_destroy(h):
@@ -318,6 +340,48 @@ class Solver:
 
     def set_block_warps(self, w: int):
         pab_set_block_warps(self.handle, w)
+
+    # ---- carrier-facing forms (pab_closure.h) -----------------------------
+    def strang_half(self, p_inf, dt_flow: float, moments=None, nb=None, stream=None):
+        import torch
+        _check(self.handle, load().pab_strang_half(
+            self.handle, self._dev(p_inf, (self.n_cells,), torch.float64, "p_inf") or None,
+            self._dev(nb, (self.n_cells,), torch.float64, "nb") or None, float(dt_flow),
+            self._dev(moments, (N_MOMENTS, self.n_cells), torch.float64, "moments") or None,
+            _stream_handle(stream) or None), "pab_strang_half")
+        return moments
+
+    def get_conservative(self, nb=None, stream=None):
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        qR = torch.empty(shp, dtype=torch.float64, device=self.device)
+        qV = torch.empty_like(qR)
+        _check(self.handle, load().pab_get_conservative(
+            self.handle, self._dev(nb, (self.n_cells,), torch.float64, "nb") or None, qR.data_ptr(),
+            qV.data_ptr(), _stream_handle(stream) or None), "pab_get_conservative")
+        return qR, qV
+
+    def set_conservative(self, alpha, qR, qV, stream=None):
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        nb = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        _check(self.handle, load().pab_set_conservative(
+            self.handle, self._dev(alpha, (self.n_cells,), torch.float64, "alpha"),
+            self._dev(qR, shp, torch.float64, "qR"), self._dev(qV, shp, torch.float64, "qV"),
+            nb.data_ptr(), _stream_handle(stream) or None), "pab_set_conservative")
+        return nb
+
+    def mixture_pressure(self, moments, p_l, rho_l=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        _check(self.handle, load().pab_mixture_pressure(
+            self.handle, self._dev(moments, (N_MOMENTS, self.n_cells), torch.float64, "moments"),
+            self._dev(p_l, (self.n_cells,), torch.float64, "p_l"),
+            self._dev(rho_l, (self.n_cells,), torch.float64, "rho_l") or None,
+            self._dev(out, (self.n_cells,), torch.float64, "p"), _stream_handle(stream) or None),
+            "pab_mixture_pressure")
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -12,7 +12,7 @@ import pytest
 from paper_2511_21031_gb300 import pab
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h")]
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h", "pab_closure.h")]
 
 
 def _declared():
