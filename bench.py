@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2511_21031_gb300 import dist as pdist  # noqa: E402
 from paper_2511_21031_gb300 import workloads  # noqa: E402
 
 METRIC = "bin-steps/s (cells x bins x flow steps)"
@@ -57,19 +58,16 @@ FP64_PIPE_ACTIVE_NCU = 0.856
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return pdist.env_rank()
 
 
 def make_workload(name, rank, edge=0):
     if name == "grid128":
-        return workloads.config_grid128(seed=2 + 1000 * rank, edge=edge or 128)
+        return workloads.config_grid128(seed=pdist.rank_seed(2, rank), edge=edge or 128)
     if name == "grid256_mixed":
-        return workloads.config_grid256_mixed(seed=3 + 1000 * rank)
+        return workloads.config_grid256_mixed(seed=pdist.rank_seed(3, rank))
     if name == "small":
-        return workloads.config_small(seed=1 + 1000 * rank)
+        return workloads.config_small(seed=pdist.rank_seed(1, rank))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -225,10 +223,7 @@ def _time_steps(solver, wl, ps, args, stream, clocks=None):
     ms_total = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     st = solver.status(stream=stream)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=ps[0].device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = pdist.max_over_ranks(ms_total, device=ps[0].device)
     return dict(ms_total=ms_total, launch_ms=launch_ms, status=st, clocks=clk, moments=mom)
 
 
@@ -411,17 +406,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     for k in range(n_e2e):
         solver.step_host(ph[k], wl.dt, moments_host=mh, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = pdist.max_over_ranks(time.perf_counter() - t0, device=dev)
     solver.status(stream=stream)
     solver.close()
     del ps
 
     bin_steps = wl.n_cells * wl.n_bins * args.steps
-    value = bin_steps * ws / (ms_total * 1e-3)
+    value = pdist.weak_scaling_value(bin_steps, ms_total, ws)
     trials_per_binstep = st["n_attempts"] / bin_steps
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     sm_mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
