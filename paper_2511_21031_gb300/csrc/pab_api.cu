@@ -177,7 +177,7 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
         b.R0f = (float)R0[i];
         b.invR0f = (float)(1.0 / R0[i]);
         b.pg0f = (float)b.pg0;
-        b.lnR0f = (float)std::log(R0[i]);
+        b.dpeqf = (float)(b.peq - c->p0);
         m3 += w[i] * R0[i] * R0[i] * R0[i];
     }
     K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;

@@ -250,7 +250,8 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinConst &bc,
                                                   double p_inf, float A, double dt, double &R,
-                                                  double &V, float &hc, int &n_att, int &n64)
+                                                  double &V, float &hc, int &n_att, int &n64,
+                                                  float &xi, float &v)
 {
     double h = (double)hc;
     if (!(h > 0.0) || h > dt)
@@ -258,8 +259,8 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
     double t = 0.0;
     uint32_t flags = 0;
     int n = 0;
-    float xi = (float)(R - bc.R0);
-    float v = (float)V;
+    xi = (float)(R - bc.R0);
+    v = (float)V;
     const float xi_collapse = (K.r_collapsef - 1.0f) * bc.R0f;
     for (;;) {
         if (n >= K.max_attempts) {
@@ -269,8 +270,9 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
         const double rem = dt - t;
         const bool last = h >= rem;
         const double ht = last ? rem : h;
-        double err, nR, nV;
-        bool ok;
+        double err, nR = 0.0, nV = 0.0;
+        float d3R = 0.0f, d3V = 0.0f;
+        bool ok, full64;
         if (xi < xi_collapse || fabsf(v) > K.v_collapsef) {
             const Trial tr = trial64(K, bc, p_inf, R, V, ht);
             ++n64;
@@ -278,6 +280,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             ok = tr.ok;
             nR = tr.R;
             nV = tr.V;
+            full64 = true;
         } else {
             const float hf = (float)ht;
             const float a1 = accel32(K, bc, A, xi, v);
@@ -289,8 +292,8 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const float v2 = v + e2V;
             const float a3 = accel32(K, bc, A, xi + e2R, v2);
             const float k3R = hf * v2, k3V = hf * a3;
-            const float d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
-            const float d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
+            d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
+            d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
             const double eR = fabs(2.0 * (double)k3R - ((double)k1R + (double)k2R));
             const double eV = fabs(2.0 * (double)k3V - ((double)k1V + (double)k2V));
             const float R3f = bc.R0f + (xi + d3R);
@@ -299,20 +302,25 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             err = fmax(eR * (double)rR, eV * (double)rV);
             ok = (bc.R0f + (xi + k1R) > 0.0f) && (bc.R0f + (xi + e2R) > 0.0f) && (R3f > 0.0f)
               && isfinite(a1 + a2 + a3);
-            nR = R + (double)d3R;
-            nV = V + (double)d3V;
+            full64 = false;
         }
         ++n;
+        const float errf = (float)err;
         float fac;
-        if (!ok || !(err <= DBL_MAX))
+        if (!ok || !(errf <= FLT_MAX))
             fac = 0.2f;
-        else if (err == 0.0)
+        else if (errf == 0.0f)
             fac = 5.0f;
         else
-            fac = fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf((float)err), 0.2f), 5.0f);
+            fac = fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf(errf), 0.2f), 5.0f);
         if (ok && err <= K.tol) {
-            R = nR;
-            V = nV;
+            if (full64) {
+                R = nR;
+                V = nV;
+            } else {
+                R += (double)d3R;
+                V += (double)d3V;
+            }
             xi = (float)(R - bc.R0);
             v = (float)V;
             if (last) {
@@ -368,7 +376,8 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
         advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V);
         na = K.n_fixed;
     } else if (MIXED) {
-        fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64);
+        float xi, v;
+        fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64, xi, v);
     } else {
         fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64);
     }

@@ -18,7 +18,7 @@ struct BinConst {
     float R0f;     // R0 in FP32 (mixed path)
     float invR0f;  // 1/R0 in FP32
     float pg0f;    // pg0 in FP32
-    float lnR0f;   // unused padding kept for 16-byte alignment
+    float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
 };
 
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,

@@ -21,11 +21,15 @@ namespace {
 constexpr int kTile = 32;
 constexpr int kMaxWarps = 16;
 
-// Running quadrature sums of one lane (one cell).  In MIXED mode the alpha
-// sum sum w R^3 is compensated (Neumaier).
+// Running quadrature sums of one lane (one cell).  FP64 mode: plain FP64
+// sums.  MIXED mode: the alpha sum sum w R^3 is FP64 and compensated
+// (Neumaier); sum w R^3 p_bw splits into an FP64 part sum w R^3 p_eq and an
+// FP32 part for the deviation of p_bw from p_eq; sum w R^2 Rdot and
+// sum w R^3 Rdot^2 are FP32 sums of FP32 terms.
 template <bool MIXED>
 struct MomAcc {
     double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
+    float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
 
     __device__ __forceinline__ void add_m3(double x)
     {
@@ -40,31 +44,60 @@ struct MomAcc {
             m3 += x;
         }
     }
+
+    // per-lane totals as doubles
+    __device__ __forceinline__ double M2V() const { return MIXED ? (double)m2vf : m2v; }
+    __device__ __forceinline__ double M3P() const { return MIXED ? m3p + (double)m3pf : m3p; }
+    __device__ __forceinline__ double M3V2() const { return MIXED ? (double)m3v2f : m3v2; }
 };
 
+// FP64 mode (and the reduce-only kernel in both modes): terms from the FP64 state.
 template <bool MIXED>
 __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &bc, double R,
                                            double V, MomAcc<MIXED> &acc)
 {
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
-    double pbw;
     if (MIXED) {
-        // deviation of p_bw from its equilibrium value peq, in FP32
         const float xi = (float)(R - bc.R0);
         const float Rf = (float)R;
         const float Vf = (float)V;
         const float u = xi * bc.invR0f;
         const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
         const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * Vf) / Rf;
-        pbw = bc.peq + (double)dev;
+        const float wr3f = (float)wr3;
+        acc.add_m3(wr3);
+        acc.m3p = fma(wr3, bc.peq, acc.m3p);
+        acc.m3pf = fmaf(wr3f, dev, acc.m3pf);
+        acc.m2vf = fmaf((float)wr2, Vf, acc.m2vf);
+        acc.m3v2f = fmaf(wr3f * Vf, Vf, acc.m3v2f);
     } else {
-        pbw = wall_pressure64(K, bc, R, V);
+        const double pbw = wall_pressure64(K, bc, R, V);
+        acc.add_m3(wr3);
+        acc.m2v += wr2 * V;
+        acc.m3p += wr3 * pbw;
+        acc.m3v2 += wr3 * V * V;
     }
+}
+
+// MIXED step kernel: the FP32 images xi = R - R0 and Rdot the advance left
+// behind spare their conversions; w R^3 stays FP64 for the compensated sum.
+template <bool MIXED>
+__device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinConst &bc, double R,
+                                                 float xi, float v, MomAcc<MIXED> &acc)
+{
+    const float Rf = bc.R0f + xi;
+    const float u = xi * bc.invR0f;
+    const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
+    const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * v) / Rf;
+    const double wr3 = bc.w * R * R * R;
+    const float wr2f = (float)bc.w * Rf * Rf;
+    const float wr3f = wr2f * Rf;
     acc.add_m3(wr3);
-    acc.m2v += wr2 * V;
-    acc.m3p += wr3 * pbw;
-    acc.m3v2 += wr3 * V * V;
+    acc.m3p = fma(wr3, bc.peq, acc.m3p);
+    acc.m3pf = fmaf(wr3f, dev, acc.m3pf);
+    acc.m2vf = fmaf(wr2f, v, acc.m2vf);
+    acc.m3v2f = fmaf(wr3f * v, v, acc.m3v2f);
 }
 
 // Combine the warps' partial sums of one tile and write the moments.
@@ -78,9 +111,9 @@ __device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAc
     const int nw = blockDim.x >> 5;
     red[0][warp][lane] = acc.m3;
     red[1][warp][lane] = acc.m3c;
-    red[2][warp][lane] = acc.m2v;
-    red[3][warp][lane] = acc.m3p;
-    red[4][warp][lane] = acc.m3v2;
+    red[2][warp][lane] = acc.M2V();
+    red[3][warp][lane] = acc.M3P();
+    red[4][warp][lane] = acc.M3V2();
     __syncthreads();
     if (warp == 0 && valid) {
         double m3 = red[0][0][lane], m3c = red[1][0][lane];
@@ -171,6 +204,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
 
     MomAcc<MIXED> acc;
     uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
+    const float dp_cell = MIXED ? (float)(K.p0 - p_inf) : 0.0f;  // p_eq - p_inf = dpeq + dp_cell
     for (int b = warp; b < K.B; b += nw) {
         if (!valid)
             continue;
@@ -182,6 +216,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         int na = 0;
         if (!p_ok || !isfinite(R) || !isfinite(V)) {
             fl = PAB_FLAG_NONFINITE;
+        } else if (MIXED && K.n_fixed == 0) {  // (only reachable in the MIXED instantiation)
+            const float A = bc.dpeqf + dp_cell;
+            float hc = a.h[k];
+            int nd = 0;
+            float xi, v;
+            fl = advance_mixed(K, bc, p_inf, A, a.dt, R, V, hc, na, nd, xi, v);
+            a.h[k] = hc;
+            n64 += nd;
+            // the checks read the FP32 images of the new state
+            if (!isfinite(xi) || !isfinite(v))
+                fl |= PAB_FLAG_NONFINITE;
+            else if (!(bc.R0f + xi > 0.0f))
+                fl |= PAB_FLAG_NONPOS;
+            if (fabsf(v) >= (float)K.c)
+                fl |= PAB_FLAG_SUPERSONIC;
+            a.R[k] = R;
+            a.V[k] = V;
+            if (a.out) {
+                if (!isfinite(xi) || !isfinite(v))
+                    accumulate<MIXED>(K, bc, R, V, acc);
+                else
+                    accumulate_mixed<MIXED>(K, bc, R, xi, v, acc);
+            }
+            if (a.attempts)
+                a.attempts[k] = na;
+            fl_or |= fl;
+            n_flag += (fl != 0);
+            n_att += na;
+            continue;
         } else {
             const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
             if (K.n_fixed > 0) {
@@ -190,10 +253,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             } else {
                 float hc = a.h[k];
                 int nd = 0;
-                if (MIXED)
-                    fl = advance_mixed(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
-                else
-                    fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
+                fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
                 a.h[k] = hc;
                 n64 += nd;
             }

@@ -72,13 +72,16 @@ def test_batch_slots_equal_single_instance_steps(precision):
     got = _run_batch(insts, 30, precision)
     for w, g in zip(insts, got):
         ref = _run_single(w, 30, precision)
-        # same per-bin arithmetic; only rounding of the (inlined) code may differ
+        # same per-bin arithmetic; only rounding of the (inlined) code may differ.  The
+        # mixed moments of the two kernels differ in how the FP32 parts are summed
+        # (FP32 running sums vs FP64 sums of per-bin terms), within the mixed budget.
         assert rel_err_R(g["R"], ref["R"]) <= 1e-11
         assert rel_err_V(g["V"], ref["V"], w.fluid) <= 1e-9
         np.testing.assert_array_equal(g["h"] > 0, ref["h"] > 0)
+        mtol = 1e-9 if precision == "fp64" else 1e-6
         for k, e in moment_errors(g["moments"], ref["moments"], ref["R"], ref["V"],
                                   np.array(_bins(w))).items():
-            assert e <= 1e-9, (k, e)
+            assert e <= mtol, (k, e)
         assert abs(g["status"]["n_attempts"] / ref["status"]["n_attempts"] - 1) <= 1e-3
         assert g["status"]["flags"] == 0
 
