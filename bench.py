@@ -397,14 +397,15 @@ def run_ours(args):
 
     # end to end through the host-buffer C-ABI entry point (pinned host memory)
     n_e2e = max(1, min(args.steps, 10))
-    ph = [torch.as_tensor(wl.pressure_step(args.warmup + k)).pin_memory() for k in range(n_e2e)]
+    # the forcing continues where the timed region stopped (steps total .. total + n_e2e)
+    ph = [torch.as_tensor(wl.pressure_step(total + k)).pin_memory() for k in range(n_e2e + 1)]
     mh = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64).pin_memory()
     solver.step_host(ph[0], wl.dt, moments_host=mh, stream=stream)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
-    for k in range(n_e2e):
+    for k in range(1, n_e2e + 1):
         solver.step_host(ph[k], wl.dt, moments_host=mh, stream=stream)
     e2e_s = pdist.max_over_ranks(time.perf_counter() - t0, device=dev)
     solver.status(stream=stream)
@@ -433,7 +434,7 @@ def run_ours(args):
                 "traffic": None, "pipe": "fp64+fp32"}
 
     variants = []
-    if args.variants and ws == 1:
+    if args.variants and args.mixed and ws == 1:
         for name, vwl in (("grid128 mixed", wl), ("grid256 mixed", make_workload("grid256_mixed", rank))):
             vs = pab.Solver(vwl.n_cells, vwl.n_bins, precision="mixed", s_lognormal=vwl.s,
                             R0ref=vwl.R0ref, span_K=vwl.span_K, alpha0=vwl.alpha0)
@@ -458,7 +459,7 @@ def run_ours(args):
             torch.cuda.synchronize()
 
     if args.variants and args.batched and ws == 1:
-        bv = _bench_batched(args, stream, dev)
+        bv = _bench_batched(args, stream, dev, n_instances=args.batch_instances)
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
         variants.append(bv)
 
@@ -524,6 +525,10 @@ def main():
                     help="skip the 512-instance batched line")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving line")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false",
+                    help="skip the single-instance mixed-precision lines")
+    ap.add_argument("--batch-instances", type=int, default=512,
+                    help="instances of the batched line (profiling runs use fewer)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
