@@ -45,16 +45,16 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel executes per trial
 # (one sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination,
-# error norm, controller) and per bin-step outside the trial loop (wall
-# pressure and quadrature sums), counted with ncu
-# (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on) on the 64^3 x 31
-# grid (three timed launches, 1.3267 trials per bin-step, plus one reduce-only launch).
-FP64_FLOPS_PER_TRIAL = 429.3
-FP64_FLOPS_PER_BINSTEP = 103.4
+# error norm, controller) and per bin-step outside the trial loop (load, first
+# exact gas evaluation, wall pressure and quadrature sums): least-squares fit of
+# ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over nine
+# launches of the 64^3 x 31 grid with traced trial counts (residual 3e-4).
+FP64_FLOPS_PER_TRIAL = 254.5
+FP64_FLOPS_PER_BINSTEP = 113.4
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
-# on the 64^3 x 31 grid, 280.8 MB / 8.13M bin-steps); scaled by bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 34.6
-FP64_PIPE_ACTIVE_NCU = 0.856
+# on the 64^3 x 31 grid, 283.5 MB / 8.13M bin-steps); scaled by bin-steps.
+FP64_DRAM_BYTES_PER_BINSTEP = 34.9
+FP64_PIPE_ACTIVE_NCU = 0.854
 
 
 def _dist():
@@ -194,6 +194,14 @@ def _time_steps(solver, wl, ps, args, stream, clocks=None):
     from paper_2511_21031_gb300 import pab
     ws, _, _ = _dist()
     mom = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64, device=ps[0].device)
+    if getattr(args, "trace_trials", False):
+        # profiling aid: trials of every launch (a sync after each; not a timing run)
+        trace = []
+        with torch.cuda.stream(stream):
+            for n in range(args.warmup + args.steps):
+                solver.step(ps[n], wl.dt, moments=mom)
+                trace.append(solver.status(stream=stream)["n_attempts"])
+        return dict(trace=trace)
     with torch.cuda.stream(stream):
         for n in range(args.warmup):
             solver.step(ps[n], wl.dt, moments=mom)
@@ -393,6 +401,12 @@ def run_ours(args):
         solver.moments()  # one reduce-only launch (profiled for its per-bin cost)
     torch.cuda.synchronize()
     res = _time_steps(solver, wl, ps, args, stream, clocks=ClockSampler(torch.cuda.current_device()))
+    if "trace" in res:
+        if rank == 0:
+            print(json.dumps({"trace_trials": res["trace"], "bin_steps_per_launch": wl.n_cells * wl.n_bins,
+                              "workload": wl.name, "precision": precision}), flush=True)
+        solver.close()
+        return 0
     ms_total, launch_ms, st, clk = res["ms_total"], res["launch_ms"], res["status"], res["clocks"]
 
     # end to end through the host-buffer C-ABI entry point (pinned host memory)
@@ -527,6 +541,8 @@ def main():
                     help="skip the continuous-batching serving line")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
                     help="skip the single-instance mixed-precision lines")
+    ap.add_argument("--trace-trials", action="store_true",
+                    help="profiling aid: print the trials of every step launch (no timing)")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="instances of the batched line (profiling runs use fewer)")
     args = ap.parse_args()

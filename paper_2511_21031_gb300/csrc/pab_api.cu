@@ -181,6 +181,16 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
         m3 += w[i] * R0[i] * R0[i] * R0[i];
     }
     K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;
+    // binomial series (1 + d)^(-a) = sum_k C(-a, k) d^k, a = 3 gamma, truncated after
+    // degree kGasTerms-1; the series is used where the first omitted term is below
+    // 1.1e-16 (half an ulp of the result)
+    const double a = 3.0 * c->gamma;
+    double ck = 1.0;
+    for (int k = 0; k < pab::kGasTerms; ++k) {
+        K->gas_c[k] = ck;
+        ck *= (-a - (double)k) / (double)(k + 1);
+    }
+    K->gas_dmax = std::pow(1.1e-16 / std::fabs(ck), 1.0 / (double)pab::kGasTerms);
 }
 
 }  // namespace

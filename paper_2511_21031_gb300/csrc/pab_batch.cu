@@ -217,7 +217,9 @@ __global__ void __launch_bounds__(512)
                 double V = d.V[k];
                 float hc = d.h[k];
                 int na = 0, nd = 0;
-                const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, R, V, hc, na, nd);
+                GasBase g;
+                g.reset();
+                const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, R, V, hc, na, nd, g);
                 d.R[k] = R;  // unchanged when the input was not finite
                 d.V[k] = V;
                 d.h[k] = hc;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(512)
                 n64 += nd;
                 if (d.out) {
                     double t[4];
-                    quad_terms<MIXED>(K, bc, R, V, t);
+                    quad_terms<MIXED>(K, bc, R, V, t, g);
                     for (int m = 0; m < 4; ++m)
                         terms[((size_t)m * max_bins + b) * kTile + lane] = t[m];
                 }

@@ -3,12 +3,59 @@
 // norm, the step-size controller and the adaptive advance of one bin.
 #pragma once
 
+#include <math_constants.h>
+
 #include <cfloat>
 #include <cstdint>
 
 #include "pab_internal.h"
 
 namespace pab {
+
+// Gas pressure p_g0 (R0/R)^(3 gamma) at the last exact evaluation, the base
+// from which nearby radii are reached by the binomial series.
+struct GasBase {
+    double Rb, invRb, Pb;
+    __device__ __forceinline__ void reset()
+    {
+        Rb = CUDART_NAN;  // forces an exact evaluation first
+        invRb = CUDART_NAN;
+        Pb = 0.0;
+    }
+};
+
+// p_g0 (R0/R)^(3 gamma) given R and 1/R.  Within a step the radii stay close
+// to the last exact evaluation Rb: with d = (R - Rb)/Rb,
+//   (R0/R)^(3 gamma) = (R0/Rb)^(3 gamma) (1 + d)^(-3 gamma),
+// and the binomial series of (1 + d)^(-3 gamma) (degree 11, used only where its
+// first omitted term is below half an ulp) replaces CUDA's exp and log.
+// Farther away the value is exact, exp(3 gamma log(R0/R)), and becomes the base.
+__device__ __forceinline__ double gas_pressure(const StepConst &K, const BinConst &bc, double R,
+                                               double iR, GasBase &g)
+{
+    const double d = (R - g.Rb) * g.invRb;
+    if (fabs(d) <= K.gas_dmax) {
+        double s = K.gas_c[kGasTerms - 1];
+#pragma unroll
+        for (int k = kGasTerms - 2; k >= 0; --k)
+            s = fma(s, d, K.gas_c[k]);
+        return g.Pb * s;
+    }
+    const double P = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));
+    g.Rb = R;
+    g.invRb = iR;
+    g.Pb = P;
+    return P;
+}
+
+// x^(-1/3) for x > 0: FP32 seed rcbrtf, then one Newton step for y^-3 = x in
+// FP64, y <- y + y (1 - x y^3)/3 (relative error ~1e-14; the seed's ~1e-7 squared).
+__device__ __forceinline__ double rcbrt_newton(double x)
+{
+    const double y = (double)rcbrtf((float)x);
+    const double e = fma(-x, y * y * y, 1.0);
+    return fma(y * (1.0 / 3.0), e, y);
+}
 
 struct Trial {
     double R, V;    // third-order result y3
@@ -23,11 +70,11 @@ struct Trial {
 //   d/dt p_bw = -3 gamma (p_b - pv) Rdot/R + (4 mu Rdot + 2 sigma) Rdot/R^2 - 4 mu Rddot/R
 // The Rddot inside d/dt p_bw moves to the left-hand side, whose coefficient
 // becomes R (1 - Rdot/c) + 4 mu/(rho c).  1/c = 0 gives Rayleigh-Plesset.
-// (R0/R)^(3 gamma) is exp(3 gamma log(R0/R)) with CUDA's log and exp: R0/R
-// stays within a few units of 1, where this differs from pow by a few ulp.
+// The gas term comes from gas_pressure (binomial series around the last exact
+// evaluation exp(3 gamma log(R0/R)), a few ulp from pow).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double p_inf,
-                                          double R, double V)
+                                          double R, double V, GasBase &g)
 {
     const double icV = V * K.inv_c;
     const double den = fma(R, 1.0 - icV, K.fmu_ic_rho);
@@ -38,7 +85,7 @@ __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc
     const double VR = V * iR;
     double pg = 0.0;
     if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));  // p_g0 (R0/R)^(3 gamma)
+        pg = gas_pressure(K, bc, R, iR, g);  // p_g0 (R0/R)^(3 gamma)
     const double s = fma(K.four_mu, V, K.two_sigma);
     const double pbw = (K.pv + pg) - s * iR;
     const double dpbw = (s * iR - K.three_gamma * pg) * VR;
@@ -49,12 +96,12 @@ __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc
 
 // Wall pressure p_bw at (R, Rdot) in FP64 (for the <R^3 p_bw> moment).
 __device__ __forceinline__ double wall_pressure64(const StepConst &K, const BinConst &bc, double R,
-                                                  double V)
+                                                  double V, GasBase &g)
 {
     const double iR = 1.0 / R;
     double pg = 0.0;
     if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));
+        pg = gas_pressure(K, bc, R, iR, g);
     return (K.pv + pg) - fma(K.four_mu, V, K.two_sigma) * iR;
 }
 
@@ -102,15 +149,15 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc,
 //   y3 = 1/3 y + 2/3 (y2 + h f(y2))           (third order, the one kept)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double p_inf,
-                                         double R, double V, double h)
+                                         double R, double V, double h, GasBase &g)
 {
-    const double a1 = accel64(K, bc, p_inf, R, V);
+    const double a1 = accel64(K, bc, p_inf, R, V, g);
     const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
-    const double a2 = accel64(K, bc, p_inf, y1R, y1V);
+    const double a2 = accel64(K, bc, p_inf, y1R, y1V, g);
     const double uR = fma(h, y1V, y1R), uV = fma(h, a2, y1V);
     const double zR = 0.5 * (R + uR), zV = 0.5 * (V + uV);
     const double y2R = fma(0.75, R, 0.25 * uR), y2V = fma(0.75, V, 0.25 * uV);
-    const double a3 = accel64(K, bc, p_inf, y2R, y2V);
+    const double a3 = accel64(K, bc, p_inf, y2R, y2V, g);
     const double wR = fma(h, y2V, y2R), wV = fma(h, a3, y2V);
     Trial t;
     t.R = fma(2.0 / 3.0, wR, R * (1.0 / 3.0));
@@ -163,13 +210,14 @@ __device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
 }
 
 // Step-size factor clamp(0.9 (tol/err)^(1/3), 0.2, 5); 0.2 after a failed trial.
+// Below err = 1e-30 the clamp gives 5 for any tol >= 1e-18; past FP32 range, 0.2.
 __device__ __forceinline__ double step_factor(const StepConst &K, double err, bool ok)
 {
-    if (!ok || !(err <= DBL_MAX))
+    if (!ok || !(err <= 3.0e38))
         return 0.2;
-    if (err == 0.0)
+    if (err <= 1e-30)
         return 5.0;
-    return fmin(fmax(0.9 * K.cbrt_tol * rcbrt(err), 0.2), 5.0);
+    return fmin(fmax(0.9 * K.cbrt_tol * rcbrt_newton(err), 0.2), 5.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -185,7 +233,8 @@ __device__ __forceinline__ double step_factor(const StepConst &K, double err, bo
 template <bool MIXED>
 __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
                                                      double p_inf, float A, double dt, double &R,
-                                                     double &V, float &hc, int &n_att, int &n64)
+                                                     double &V, float &hc, int &n_att, int &n64,
+                                                     GasBase &g)
 {
     double h = (double)hc;
     if (!(h > 0.0) || h > dt)
@@ -205,13 +254,13 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
         if (MIXED) {
             const bool stiff = (R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse);
             if (stiff) {
-                tr = trial64(K, bc, p_inf, R, V, ht);
+                tr = trial64(K, bc, p_inf, R, V, ht, g);
                 ++n64;
             } else {
                 tr = trial32(K, bc, A, R, V, ht);
             }
         } else {
-            tr = trial64(K, bc, p_inf, R, V, ht);
+            tr = trial64(K, bc, p_inf, R, V, ht, g);
         }
         ++n;
         const double err = error_norm(K, tr);
@@ -274,7 +323,9 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
         float d3R = 0.0f, d3V = 0.0f;
         bool ok, full64;
         if (xi < xi_collapse || fabsf(v) > K.v_collapsef) {
-            const Trial tr = trial64(K, bc, p_inf, R, V, ht);
+            GasBase g;
+            g.reset();
+            const Trial tr = trial64(K, bc, p_inf, R, V, ht, g);
             ++n64;
             err = error_norm(K, tr);
             ok = tr.ok;
@@ -343,7 +394,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
 // only for bins near collapse, as in the adaptive mode).
 template <bool MIXED>
 __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst &bc, double p_inf,
-                                              float A, double dt, double &R, double &V)
+                                              float A, double dt, double &R, double &V, GasBase &g)
 {
     const double h = dt / (double)K.n_fixed;
     for (int i = 0; i < K.n_fixed; ++i) {
@@ -351,7 +402,7 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
         if (MIXED && !((R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse)))
             tr = trial32(K, bc, A, R, V, h);
         else
-            tr = trial64(K, bc, p_inf, R, V, h);
+            tr = trial64(K, bc, p_inf, R, V, h, g);
         R = tr.R;
         V = tr.V;
     }
@@ -364,7 +415,7 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
 template <bool MIXED>
 __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinConst &bc, double p_inf,
                                                 bool p_ok, double dt, double &R, double &V, float &hc,
-                                                int &na, int &n64)
+                                                int &na, int &n64, GasBase &g)
 {
     na = 0;
     n64 = 0;
@@ -373,13 +424,13 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
     uint32_t fl = 0;
     const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
     if (K.n_fixed > 0) {
-        advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V);
+        advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V, g);
         na = K.n_fixed;
     } else if (MIXED) {
         float xi, v;
         fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64, xi, v);
     } else {
-        fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64);
+        fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64, g);
     }
     if (!isfinite(R) || !isfinite(V))
         fl |= PAB_FLAG_NONFINITE;
@@ -394,7 +445,7 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 // w R^3 Rdot^2 (the wall pressure in FP64, or in FP32 deviation form in MIXED).
 template <bool MIXED>
 __device__ __forceinline__ void quad_terms(const StepConst &K, const BinConst &bc, double R, double V,
-                                           double t[4])
+                                           double t[4], GasBase &g)
 {
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
@@ -405,7 +456,7 @@ __device__ __forceinline__ void quad_terms(const StepConst &K, const BinConst &b
         const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
         pbw = bc.peq + (double)(pgdev + (K.two_sigmaf * u - K.four_muf * (float)V) / (float)R);
     } else {
-        pbw = wall_pressure64(K, bc, R, V);
+        pbw = wall_pressure64(K, bc, R, V, g);
     }
     t[0] = wr3;
     t[1] = wr2 * V;

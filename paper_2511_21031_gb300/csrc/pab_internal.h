@@ -21,6 +21,8 @@ struct BinConst {
     float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
 };
 
+constexpr int kGasTerms = 12;  // binomial series of the gas term: degree 11
+
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
 // so warp-uniform reads come from the constant bank.
 struct StepConst {
@@ -41,12 +43,17 @@ struct StepConst {
     double v_collapse;    // mixed: |Rdot| above this takes the FP64 path (c/20)
     double r_collapse;    // mixed: R/R0 below this takes the FP64 path (0.2)
     double nb_default;    // n_b when the caller passes no n_b field
+    // (1 + d)^(-3 gamma) = sum_k gas_c[k] d^k for |d| <= gas_dmax (truncation below half an ulp)
+    double gas_c[kGasTerms];
+    double gas_dmax;
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
     float cbrt_tolf, v_collapsef, r_collapsef, padf;
     BinConst bins[PAB_MAX_BINS];
 };
 
 // Device-side status accumulated over calls until pab_status_flags reads it.
+static_assert(sizeof(StepConst) <= 4000, "StepConst must fit the 4 KB kernel-parameter space");
+
 struct Counters {
     unsigned int flags_or;
     unsigned int pad;

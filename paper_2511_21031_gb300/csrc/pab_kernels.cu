@@ -54,7 +54,7 @@ struct MomAcc {
 // FP64 mode (and the reduce-only kernel in both modes): terms from the FP64 state.
 template <bool MIXED>
 __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &bc, double R,
-                                           double V, MomAcc<MIXED> &acc)
+                                           double V, MomAcc<MIXED> &acc, GasBase &g)
 {
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
@@ -72,7 +72,7 @@ __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &b
         acc.m2vf = fmaf((float)wr2, Vf, acc.m2vf);
         acc.m3v2f = fmaf(wr3f * Vf, Vf, acc.m3v2f);
     } else {
-        const double pbw = wall_pressure64(K, bc, R, V);
+        const double pbw = wall_pressure64(K, bc, R, V, g);
         acc.add_m3(wr3);
         acc.m2v += wr2 * V;
         acc.m3p += wr3 * pbw;
@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         double V = a.V[k];
         uint32_t fl = 0;
         int na = 0;
+        GasBase g;
+        g.reset();
         if (!p_ok || !isfinite(R) || !isfinite(V)) {
             fl = PAB_FLAG_NONFINITE;
         } else if (MIXED && K.n_fixed == 0) {  // (only reachable in the MIXED instantiation)
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             a.V[k] = V;
             if (a.out) {
                 if (!isfinite(xi) || !isfinite(v))
-                    accumulate<MIXED>(K, bc, R, V, acc);
+                    accumulate<MIXED>(K, bc, R, V, acc, g);
                 else
                     accumulate_mixed<MIXED>(K, bc, R, xi, v, acc);
             }
@@ -248,12 +250,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         } else {
             const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
             if (K.n_fixed > 0) {
-                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt, R, V);
+                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt, R, V, g);
                 na = K.n_fixed;
             } else {
                 float hc = a.h[k];
                 int nd = 0;
-                fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd);
+                fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd, g);
                 a.h[k] = hc;
                 n64 += nd;
             }
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         n_flag += (fl != 0);
         n_att += na;
         if (a.out)
-            accumulate<MIXED>(K, bc, R, V, acc);
+            accumulate<MIXED>(K, bc, R, V, acc, g);
     }
     if (a.out)
         reduce_and_store<MIXED>(K, acc, nb, c, valid, a.out);
@@ -296,7 +298,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         if (!valid)
             continue;
         const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        accumulate<MIXED>(K, K.bins[b], Rp[k], Vp[k], acc);
+        GasBase g;
+        g.reset();
+        accumulate<MIXED>(K, K.bins[b], Rp[k], Vp[k], acc, g);
     }
     reduce_and_store<MIXED>(K, acc, nb, c, valid, out);
 }

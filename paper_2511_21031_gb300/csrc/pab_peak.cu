@@ -1,6 +1,8 @@
 // FMA throughput microbenchmark (measurement aid for the roofline).
 #include <cuda_runtime.h>
 
+#include "pab_device.cuh"
+#include "pab_internal.h"
 #include "pab_measure.h"
 
 namespace {
@@ -22,7 +24,45 @@ __global__ void fma_streams(int iters, double *sink)
         (double)(a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7);
 }
 
+__global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, long long n,
+                                  const double *R, const double *Rb, double *gas, double *exact,
+                                  double *rc)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const pab::BinConst &bc = K.bins[0];  // R0 = 1, pg0 = 1
+        pab::GasBase g;
+        g.reset();
+        (void)pab::gas_pressure(K, bc, Rb[i], 1.0 / Rb[i], g);  // exact at the base
+        gas[i] = pab::gas_pressure(K, bc, R[i], 1.0 / R[i], g);
+        exact[i] = exp(K.three_gamma * log(1.0 / R[i]));
+        rc[i] = pab::rcbrt_newton(R[i]);
+    }
+}
+
 }  // namespace
+
+extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
+                                     double *gas_dev, double *exact_dev, double *rcbrt_dev, void *stream)
+{
+    if (n < 0 || !(a > 0.0) || (n > 0 && (!R_dev || !Rb_dev || !gas_dev || !exact_dev || !rcbrt_dev)))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    pab_config c;
+    pab_config_default(&c);
+    c.n_bins = 1;
+    c.gamma = a / 3.0;
+    c.sigma = 0.0;
+    c.pv = 0.0;
+    c.p0 = 1.0;
+    const double R0 = 1.0, w = 1.0;
+    pab::StepConst K;
+    pab::make_const(&c, &R0, &w, &K);  // pg0 = p0 + 0 - 0 = 1
+    math_check_kernel<<<152 * 4, 256, 0, (cudaStream_t)stream>>>(K, n, R_dev, Rb_dev, gas_dev,
+                                                                  exact_dev, rcbrt_dev);
+    return cudaGetLastError() == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
 
 extern "C" pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int32_t iters,
                                    double *sink_dev, float *ms_out, double *fma_out, void *stream)

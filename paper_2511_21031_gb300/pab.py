@@ -28,7 +28,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
-           "pab_stiffened_gas")
+           "pab_stiffened_gas", "pab_math_check")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_set_conservative": (i32, [vp, vp, vp, vp, vp, vp]),
         "pab_mixture_pressure": (i32, [vp, vp, vp, vp, vp, vp]),
         "pab_stiffened_gas": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
+        "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +224,19 @@ def pab_stiffened_gas(rho_l, e_l, gamma_l: float, pi_inf: float, out=None, strea
     if st != PAB_OK:
         raise PabError(st, "pab_stiffened_gas")
     return out
+
+
+def pab_math_check(R, Rb, a: float, stream=None):
+    """(gas series value, exp/log value, x^(-1/3)) of the library's device helpers."""
+    import torch
+    g = torch.empty_like(R)
+    e = torch.empty_like(R)
+    r = torch.empty_like(R)
+    st = load().pab_math_check(R.numel(), R.data_ptr(), Rb.data_ptr(), float(a), g.data_ptr(),
+                               e.data_ptr(), r.data_ptr(), _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_math_check")
+    return g, e, r
 
 
 def pab_destroy(h):
