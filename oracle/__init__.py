@@ -114,6 +114,13 @@ def _lib():
             lib.orc_stiffened_gas.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
                                               ctypes.c_double, _dp]
             lib.orc_stiffened_gas.restype = None
+            _i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.orc_el_advance.argtypes = [P, ctypes.c_int64, _dp, _i64p, _dp, ctypes.c_double, _dp, _dp,
+                                           _fp, _u32p, _i32p]
+            lib.orc_el_advance.restype = None
+            lib.orc_el_smear.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _dp, _dp]
+            lib.orc_el_smear.restype = None
             _LIB = lib
     return _LIB
 
@@ -266,3 +273,35 @@ def stiffened_gas(rho_l, e_l, gamma_l, pi_inf):
     _lib().orc_stiffened_gas(rho_l.size, _ptr(rho_l, _dp), _ptr(e_l, _dp), float(gamma_l),
                              float(pi_inf), _ptr(out, _dp))
     return out
+
+
+def el_advance(params: Params, R0, cell, p_cell, dt, R, Rdot, h):
+    """Advance N Lagrangian bubbles in place (each under its cell's pressure); returns (flags, attempts)."""
+    R0 = _f64(R0)
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    p_cell = _f64(p_cell)
+    N = R0.shape[0]
+    for a, dt_ in ((R, np.float64), (Rdot, np.float64), (h, np.float32)):
+        if a.dtype != dt_ or not a.flags.c_contiguous or a.size != N:
+            raise ValueError("bubble state arrays must be contiguous [N] (R, Rdot f64; h f32)")
+    flags = np.zeros(N, dtype=np.uint32)
+    att = np.zeros(N, dtype=np.int32)
+    cp = params.as_c()
+    _lib().orc_el_advance(ctypes.byref(cp), N, _ptr(R0, _dp), cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          _ptr(p_cell, _dp), float(dt), _ptr(R, _dp), _ptr(Rdot, _dp), _ptr(h, _fp),
+                          _ptr(flags, _u32p), _ptr(att, _i32p))
+    return flags, att
+
+
+def el_smear(pos, R, Rdot, nx, ny, nz, dx, with_rate=True):
+    """Void fraction (and its bubble-growth rate) of Eq. (kernel3D) at the cell centres."""
+    pos = _f64(pos)
+    R = _f64(R)
+    Rdot = _f64(Rdot)
+    N = R.shape[0]
+    alpha = np.zeros(nx * ny * nz)
+    adot = np.zeros(nx * ny * nz) if with_rate else None
+    _lib().orc_el_smear(N, _ptr(pos[0], _dp), _ptr(pos[1], _dp), _ptr(pos[2], _dp), _ptr(R, _dp),
+                        _ptr(Rdot, _dp), int(nx), int(ny), int(nz), float(dx), _ptr(alpha, _dp),
+                        _ptr(adot, _dp) if adot is not None else None)
+    return (alpha, adot) if with_rate else alpha

@@ -498,3 +498,92 @@ void orc_stiffened_gas(int64_t n, const double *rho_l, const double *e_l, double
     for (int64_t i = 0; i < n; ++i)
         p_l[i] = (gamma_l - 1.0) * rho_l[i] * e_l[i] - gamma_l * pi_inf;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Volume-averaged (Euler-Lagrange) model, Sec. 2.1                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * N bubbles at fixed positions x_n (no translation, Sec. 2.1) on a grid of
+ * nx x ny x nz cells of size dx (cell (i,j,k) centred at ((i+1/2)dx, ...),
+ * x fastest in memory).  Each bubble has its own R0_n; its far-field pressure
+ * is the carrier pressure of the cell that contains it (reading), held fixed
+ * over the step.  The bubble ODE is the same Keller-Miksis equation, advanced
+ * by the same adaptive stepper as one bin.  bub_p_cell holds the cell index of
+ * every bubble (-1 outside the grid).
+ */
+void orc_el_advance(const orc_params *P, int64_t N, const double *R0, const int64_t *cell,
+                    const double *p_cell, double dt, double *R, double *Rdot, float *h,
+                    uint32_t *flags, int32_t *attempts)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t n = 0; n < N; ++n) {
+        uint32_t fl = 0;
+        int32_t na = 0;
+        double y[2] = {R[n], Rdot[n]};
+        double p_inf = cell[n] >= 0 ? p_cell[cell[n]] : NAN;
+        if (!isfinite(p_inf) || !isfinite(y[0]) || !isfinite(y[1])) {
+            fl |= ORC_FLAG_NONFINITE;
+        } else {
+            km_ctx ctx = {P, R0[n], p_inf};
+            fl |= advance_adaptive(km_rhs_fn, &ctx, y, &h[n], dt, P->tol, P->v_floor,
+                                   P->max_attempts, &na);
+            if (!isfinite(y[0]) || !isfinite(y[1]))
+                fl |= ORC_FLAG_NONFINITE;
+            else if (!(y[0] > 0.0))
+                fl |= ORC_FLAG_NONPOS;
+            R[n] = y[0];
+            Rdot[n] = y[1];
+        }
+        if (flags)
+            flags[n] = fl;
+        if (attempts)
+            attempts[n] = na;
+    }
+}
+
+/*
+ * Smearing of the bubbles into the Eulerian void fraction, Eq. (kernel3D):
+ *   alpha(x) = sum_n V_n delta(d_n, h_n),   V_n = 4/3 pi R_n^3,
+ *   delta(d, h) = exp(-d^2 / (2 h^2)) / (h^3 (2 pi)^{3/2})  for d/h < 3, else 0,
+ * with d_n the distance from the cell centre to the bubble and the kernel width
+ * h_n = dx when R_n < dx and R_n otherwise (Eq. model_inequality and the rule
+ * after it).  The kernel is evaluated at cell centres (Listing 1).  The rate
+ *   alpha_dot(x) = sum_n (dV_n/dt) delta(d_n, h_n),  dV_n/dt = 4 pi R_n^2 Rdot_n,
+ * is the first term of the d alpha/dt equation; the second, V_n d delta/dt =
+ * -V_n u . grad delta, vanishes for fixed bubbles in a liquid at rest and is
+ * left to the carrier.  Cells outside the grid are skipped.  Plain loops over
+ * bubbles and over every cell of the grid whose centre lies within 3 h_n.
+ * alpha_dot may be NULL.
+ */
+void orc_el_smear(int64_t N, const double *x, const double *y, const double *z, const double *R,
+                  const double *Rdot, int32_t nx, int32_t ny, int32_t nz, double dx,
+                  double *alpha, double *alpha_dot)
+{
+    int64_t ncell = (int64_t)nx * ny * nz;
+    for (int64_t c = 0; c < ncell; ++c) {
+        alpha[c] = 0.0;
+        if (alpha_dot)
+            alpha_dot[c] = 0.0;
+    }
+    double norm = pow(2.0 * M_PI, 1.5);
+    for (int64_t n = 0; n < N; ++n) {
+        double h = R[n] < dx ? dx : R[n];
+        double V = 4.0 / 3.0 * M_PI * R[n] * R[n] * R[n];
+        double Vdot = 4.0 * M_PI * R[n] * R[n] * Rdot[n];
+        for (int32_t k = 0; k < nz; ++k)
+            for (int32_t j = 0; j < ny; ++j)
+                for (int32_t i = 0; i < nx; ++i) {
+                    double cx = (i + 0.5) * dx - x[n];
+                    double cy = (j + 0.5) * dx - y[n];
+                    double cz = (k + 0.5) * dx - z[n];
+                    double d = sqrt(cx * cx + cy * cy + cz * cz);
+                    if (!(d / h < 3.0))
+                        continue;
+                    double delta = exp(-d * d / (2.0 * h * h)) / (h * h * h * norm);
+                    int64_t c = ((int64_t)k * ny + j) * nx + i;
+                    alpha[c] += V * delta;
+                    if (alpha_dot)
+                        alpha_dot[c] += Vdot * delta;
+                }
+    }
+}

@@ -539,3 +539,77 @@ def test_stiffened_gas_inverts_its_energy():
     rho = g.uniform(950, 1050, size=100)
     e = (p_l + gam * pinf) / ((gam - 1.0) * rho)
     np.testing.assert_allclose(oracle.stiffened_gas(rho, e, gam, pinf), p_l, rtol=0, atol=1e-6 * gam * pinf * 1e-3)
+
+
+# ----------------------------------------------------------------------------
+# Volume-averaged (EL) model: Gaussian smearing, Eq. (kernel3D)
+# ----------------------------------------------------------------------------
+def test_el_smear_single_bubble_closed_forms():
+    """One bubble at a cell centre with R < dx (h = dx): the centre value is
+    V/(h^3 (2 pi)^{3/2}); values at equal distance agree; cells at d >= 3h get
+    nothing; the grid sum equals V/(2 pi)^{3/2} times the lattice sum of
+    exp(-|m|^2/2) over integer vectors with |m| < 3."""
+    dx = 75e-6
+    n = 9
+    pos = np.array([[4.5 * dx], [4.5 * dx], [4.5 * dx]])
+    R = np.array([10e-6])
+    V = 4 / 3 * math.pi * R[0] ** 3
+    a, ad = oracle.el_smear(pos, R, np.array([2.0]), n, n, n, dx)
+    a = a.reshape(n, n, n)
+    norm = (2 * math.pi) ** 1.5
+    assert a[4, 4, 4] == pytest.approx(V / (dx ** 3 * norm), rel=1e-14)
+    assert a[4, 4, 5] == pytest.approx(a[4, 5, 4], rel=1e-14) == pytest.approx(a[3, 4, 4], rel=1e-14)
+    assert a[4, 4, 5] / a[4, 4, 4] == pytest.approx(math.exp(-0.5), rel=1e-13)
+    assert a[4, 4, 7] == 0.0 and a[4, 4, 1] == 0.0            # d = 3h exactly: outside
+    assert a[4, 6, 6] > 0                                       # d = 2.83 h: inside
+    lattice = sum(math.exp(-(i * i + j * j + k * k) / 2.0)
+                  for i in range(-3, 4) for j in range(-3, 4) for k in range(-3, 4)
+                  if i * i + j * j + k * k < 9)
+    assert a.sum() * dx ** 3 == pytest.approx(V * lattice / norm, rel=1e-13)
+    # the growth rate uses 4 pi R^2 Rdot in place of V
+    np.testing.assert_allclose(ad.reshape(n, n, n), a * (4 * math.pi * R[0] ** 2 * 2.0) / V, rtol=1e-13)
+
+
+def test_el_smear_width_follows_radius_and_superposes():
+    """h = max(dx, R): a bubble larger than the cell spreads over 3 R; two bubbles add."""
+    dx = 50e-6
+    n = 16
+    big = np.array([[8 * dx], [8 * dx], [8 * dx]])
+    a = oracle.el_smear(big, np.array([80e-6]), np.array([0.0]), n, n, n, dx, with_rate=False)
+    a = a.reshape(n, n, n)
+    h = 80e-6
+    d = math.sqrt(3) * 0.5 * dx                                 # nearest cell centres
+    assert a[8, 8, 8] == pytest.approx(4 / 3 * math.pi * h ** 3 * math.exp(-d * d / (2 * h * h))
+                                       / (h ** 3 * (2 * math.pi) ** 1.5), rel=1e-13)
+    assert a[8, 8, 8 + 4] > 0                                   # 3.5 dx < 3 h = 4.8 dx
+    g = np.random.default_rng(43)
+    pos = g.uniform(0, n * dx, size=(3, 5))
+    Rs = g.uniform(5e-6, 60e-6, size=5)
+    Vd = g.normal(size=5)
+    tot = oracle.el_smear(pos, Rs, Vd, n, n, n, dx)[0]
+    parts = sum(oracle.el_smear(pos[:, i:i + 1], Rs[i:i + 1], Vd[i:i + 1], n, n, n, dx)[0] for i in range(5))
+    np.testing.assert_allclose(tot, parts, rtol=1e-13, atol=1e-30)
+
+
+def test_el_advance_matches_ee_bins_with_the_same_pressure():
+    """A Lagrangian bubble follows the same Keller-Miksis stepper as an EE bin
+    of the same R0 under the same pressure."""
+    P = oracle.Params()
+    g = np.random.default_rng(44)
+    N = 6
+    R0 = g.uniform(3e-6, 30e-6, size=N)
+    p_cell = np.array([P.p0 * 1.3, P.p0 * 0.6])
+    cell = np.array([0, 1, 0, 1, 0, 1])
+    R = R0.copy()
+    V = np.zeros(N)
+    h = np.zeros(N, dtype=np.float32)
+    for _ in range(50):
+        fl, na = oracle.el_advance(P, R0, cell, p_cell, 1e-8, R, V, h)
+        assert not fl.any()
+    for n in range(N):
+        Rb = np.array([[R0[n]]])
+        Vb = np.zeros((1, 1))
+        hb = np.zeros((1, 1), dtype=np.float32)
+        for _ in range(50):
+            oracle.step(P, [R0[n]], [p_cell[cell[n]]], 1e-8, Rb, Vb, hb)
+        assert R[n] == Rb[0, 0] and V[n] == Vb[0, 0]
