@@ -372,6 +372,52 @@ def _bench_serving(args, n_requests=16, rate=200.0):
                        "bins_per_grab": tune["bins_per_grab"], "autotuned": True}}
 
 
+def _bench_el(args, stream, dev):
+    """Volume-averaged (EL) model: fixed bubbles (R0 = 10 um, alpha0 = 1e-3) in a
+    128^3 grid of 75 um cells, each advanced under its cell's pressure (0.5 p0 at
+    100 kHz, random phase per cell) and smeared into alpha and alpha_dot with the
+    truncated Gaussian kernel, every step."""
+    import torch
+
+    from paper_2511_21031_gb300.el import BubbleCloud
+    wl = workloads.bubble_cloud(edge=128, dx=75e-6, alpha0=1e-3)
+    cl = BubbleCloud(wl.pos, wl.R0, wl.edge, wl.edge, wl.edge, wl.dx, **wl.fluid)
+    total = args.warmup + args.steps
+    ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
+    a = torch.empty(wl.edge ** 3, dtype=torch.float64, device=dev)
+    ad = torch.empty_like(a)
+    with torch.cuda.stream(stream):
+        for n in range(args.warmup):
+            cl.step(ps[n], wl.dt, alpha=a, alpha_dot=ad, stream=stream)
+    cl.status(stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(args.steps):
+            cl.step(ps[args.warmup + k], wl.dt, alpha=a, alpha_dot=ad, stream=stream)
+        e1.record(stream)
+        s0.record(stream)
+        for k in range(args.steps):
+            cl.smear(a, ad, stream=stream)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ms_smear = s0.elapsed_time(s1)
+    st = cl.status(stream=stream)
+    cl.close()
+    del ps
+    return {"workload": wl.name, "label": "EL bubbles + Gaussian smearing (FP64)", "precision": "fp64",
+            "bubbles": wl.n_bubbles, "cells": wl.edge ** 3,
+            "value": wl.n_bubbles * args.steps / (ms * 1e-3), "unit": "bubble-steps/s",
+            "ms_per_step": ms / args.steps, "smear_ms_per_step": ms_smear / args.steps,
+            "trials_per_bubble_step": st["n_attempts"] / (wl.n_bubbles * args.steps),
+            "status_flags": st["flags"]}
+
+
 def run_ours(args):
     import torch
 
@@ -477,6 +523,9 @@ def run_ours(args):
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
         variants.append(bv)
 
+    if args.variants and args.el and ws == 1:
+        variants.append(_bench_el(args, stream, dev))
+
     if args.variants and args.serving and ws == 1:
         variants.append(_bench_serving(args))
 
@@ -539,6 +588,8 @@ def main():
                     help="skip the 512-instance batched line")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving line")
+    ap.add_argument("--no-el", dest="el", action="store_false",
+                    help="skip the volume-averaged (EL) line")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
                     help="skip the single-instance mixed-precision lines")
     ap.add_argument("--trace-trials", action="store_true",

@@ -218,6 +218,15 @@ void make_const(const pab_config *c, const double *R0, const double *w, StepCons
     build_const(c, R0, w, K);
 }
 
+BinConst make_bin(const pab_config *c, double R0, double w)
+{
+    StepConst K;
+    pab_config one = *c;
+    one.n_bins = 1;
+    build_const(&one, &R0, &w, &K);
+    return K.bins[0];
+}
+
 }  // namespace pab
 
 extern "C" {

@@ -1,0 +1,440 @@
+// Volume-averaged (Euler-Lagrange) subgrid model: Lagrangian bubbles advanced
+// by the Keller-Miksis stepper of the EE path, and their volumes smeared onto
+// the grid with the truncated Gaussian kernel of Eq. (kernel3D)
+// (include/pab_el.h).
+//
+//   el_advance_kernel  one thread per bubble; the bubble's constants (R0,
+//                      p_g0, ...) come from a per-bubble table in global memory,
+//                      its pressure from the cell that contains it.
+//   el_smear_kernel    one warp per bubble.  The kernel exp(-d^2/(2h^2)) is
+//                      separable: the warp evaluates the 3 x (2m+1) one-
+//                      dimensional factors once (for stencil half-widths m up to
+//                      24 cells; wider kernels evaluate every point), then its
+//                      lanes walk the (2m+1)^3 stencil cube, keep the cells with
+//                      d/h < 3 and add V delta and Vdot delta with FP64 atomics
+//                      (nearby bubbles overlap, Listing 1's "atomic update").
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pab.h"
+#include "pab_device.cuh"
+#include "pab_el.h"
+#include "pab_internal.h"
+
+namespace pab {
+namespace {
+
+constexpr int kSmearWarps = 4;
+constexpr int kCacheHalf = 24;  // stencil half-widths up to this use the separable cache
+constexpr int kSide = 2 * kCacheHalf + 1;
+
+__global__ void __launch_bounds__(256)
+    el_advance_kernel(const __grid_constant__ StepConst K, long long N, const BinConst *__restrict__ bub,
+                      const long long *__restrict__ cell, const double *__restrict__ p_cell, double dt,
+                      double *__restrict__ R, double *__restrict__ V, float *__restrict__ h,
+                      Counters *cnt)
+{
+    __shared__ uint32_t sc[3][8];
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t fl = 0;
+    int na = 0;
+    if (n < N) {
+        const BinConst bc = bub[n];
+        const long long ci = cell[n];
+        const double p_inf = ci >= 0 ? p_cell[ci] : CUDART_NAN;
+        double r = R[n], v = V[n];
+        float hc = h[n];
+        int nd = 0;
+        GasBase g;
+        g.reset();
+        fl = advance_bin<false>(K, bc, p_inf, isfinite(p_inf), dt, r, v, hc, na, nd, g);
+        R[n] = r;  // unchanged when the input was not finite
+        V[n] = v;
+        h[n] = hc;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t f = __reduce_or_sync(0xffffffffu, fl);
+    const uint32_t nf = __reduce_add_sync(0xffffffffu, fl != 0 ? 1u : 0u);
+    const uint32_t a = __reduce_add_sync(0xffffffffu, (uint32_t)na);
+    if (lane == 0) {
+        sc[0][warp] = f;
+        sc[1][warp] = nf;
+        sc[2][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t F = 0;
+        unsigned long long NF = 0, A = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            F |= sc[0][w];
+            NF += sc[1][w];
+            A += sc[2][w];
+        }
+        if (F)
+            atomicOr(&cnt->flags_or, F);
+        if (NF)
+            atomicAdd(&cnt->n_flagged, NF);
+        if (A)
+            atomicAdd(&cnt->n_attempts, A);
+    }
+}
+
+__global__ void __launch_bounds__(kSmearWarps * 32)
+    el_smear_kernel(long long N, const double *__restrict__ px, const double *__restrict__ py,
+                    const double *__restrict__ pz, const double *__restrict__ R,
+                    const double *__restrict__ V, int nx, int ny, int nz, double dx,
+                    double *__restrict__ alpha, double *__restrict__ alpha_dot)
+{
+    __shared__ double fac[kSmearWarps][3][kSide];  // exp(-c^2/(2h^2)) per axis offset
+    __shared__ double sq[kSmearWarps][3][kSide];   // c^2 per axis offset
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const double norm = 15.749609945722419;  // (2 pi)^{3/2}
+    for (long long n = (long long)blockIdx.x * kSmearWarps + warp; n < N;
+         n += (long long)gridDim.x * kSmearWarps) {
+        const double r = R[n];
+        const double h = r < dx ? dx : r;
+        const int m = (int)floor(3.0 * h / dx) + 1;  // cells whose centre can lie within 3h
+        const int side = 2 * m + 1;
+        const bool cached = m <= kCacheHalf;
+        const double pos[3] = {px[n], py[n], pz[n]};
+        int base[3];
+        for (int a = 0; a < 3; ++a)
+            base[a] = (int)floor(pos[a] / dx) - m;
+        const double inv2h2 = 1.0 / (2.0 * h * h);
+        if (cached) {
+            for (int t = lane; t < 3 * side; t += 32) {
+                const int a = t / side, o = t % side;
+                const double cc = ((double)(base[a] + o) + 0.5) * dx - pos[a];
+                sq[warp][a][o] = cc * cc;
+                fac[warp][a][o] = exp(-cc * cc * inv2h2);
+            }
+        }
+        __syncwarp();
+        const double Vb = 4.0 / 3.0 * 3.14159265358979323846 * r * r * r;
+        const double Vd = 4.0 * 3.14159265358979323846 * r * r * V[n];
+        const double scale = 1.0 / (h * h * h * norm);
+        const double lim2 = 9.0 * h * h;
+        const long long count = (long long)side * side * side;
+        for (long long t = lane; t < count; t += 32) {
+            const int oi = (int)(t % side), oj = (int)((t / side) % side), ok = (int)(t / ((long long)side * side));
+            const int i = base[0] + oi, j = base[1] + oj, k = base[2] + ok;
+            if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz)
+                continue;
+            double sx, sy, sz;
+            if (cached) {
+                sx = sq[warp][0][oi];
+                sy = sq[warp][1][oj];
+                sz = sq[warp][2][ok];
+            } else {
+                const double cx = ((double)i + 0.5) * dx - pos[0];
+                const double cy = ((double)j + 0.5) * dx - pos[1];
+                const double cz = ((double)k + 0.5) * dx - pos[2];
+                sx = cx * cx;
+                sy = cy * cy;
+                sz = cz * cz;
+            }
+            const double d2 = sx + sy + sz;
+            bool inside = d2 < lim2;
+            if (fabs(d2 - lim2) <= 1e-12 * lim2)  // on the cut: decide exactly as d/h < 3
+                inside = sqrt(d2) / h < 3.0;
+            if (!inside)
+                continue;
+            const double g = cached ? fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok]
+                                    : exp(-d2 * inv2h2);
+            const double delta = g * scale;
+            const long long c = ((long long)k * ny + j) * nx + i;
+            atomicAdd(&alpha[c], Vb * delta);
+            if (alpha_dot)
+                atomicAdd(&alpha_dot[c], Vd * delta);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+}  // namespace pab
+
+struct pab_el_s {
+    pab_config cfg;
+    pab::StepConst K;
+    long long N = 0;
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0.0;
+    cudaStream_t create_stream = nullptr;
+    double *pos = nullptr;  // [3][N]
+    long long *cell = nullptr;
+    pab::BinConst *bub = nullptr;
+    double *R = nullptr;
+    double *V = nullptr;
+    float *h = nullptr;
+    pab::Counters *counters = nullptr;
+    pab::Counters *counters_host = nullptr;
+    char err[512] = {0};
+};
+
+namespace {
+
+pab_status efail(pab_el_t *e, pab_status s, const char *fmt, ...)
+{
+    if (e) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(e->err, sizeof(e->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+pab_status ecuda(pab_el_t *e, cudaError_t c, const char *what)
+{
+    return efail(e, c == cudaErrorMemoryAllocation ? PAB_ENOMEM : PAB_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(c));
+}
+
+cudaError_t launch_smear(pab_el_t *e, double *alpha, double *alpha_dot, cudaStream_t s)
+{
+    const size_t cells = (size_t)e->nx * e->ny * e->nz;
+    cudaError_t c = cudaMemsetAsync(alpha, 0, cells * sizeof(double), s);
+    if (c == cudaSuccess && alpha_dot)
+        c = cudaMemsetAsync(alpha_dot, 0, cells * sizeof(double), s);
+    if (c != cudaSuccess || e->N == 0)
+        return c;
+    long long blocks = (e->N + pab::kSmearWarps - 1) / pab::kSmearWarps;
+    if (blocks > 152LL * 64)
+        blocks = 152LL * 64;
+    pab::el_smear_kernel<<<(unsigned)blocks, pab::kSmearWarps * 32, 0, s>>>(
+        e->N, e->pos, e->pos + e->N, e->pos + 2 * e->N, e->R, e->V, e->nx, e->ny, e->nz, e->dx, alpha,
+        alpha_dot);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pab_el_last_error(const pab_el_t *e) { return e ? e->err : "NULL handle"; }
+
+pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const double *pos_host,
+                         const double *R0_host, int32_t nx, int32_t ny, int32_t nz, double dx,
+                         void *stream, pab_el_t **out)
+{
+    if (!out)
+        return PAB_EINVAL;
+    *out = nullptr;
+    if (!liquid || n_bubbles < 0 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !std::isfinite(dx) ||
+        (n_bubbles > 0 && (!pos_host || !R0_host))) {
+        fprintf(stderr, "pab_el_create: invalid arguments\n");
+        return PAB_EINVAL;
+    }
+    pab_config c = *liquid;
+    c.n_cells = n_bubbles > 0 ? n_bubbles : 1;
+    c.n_bins = 1;
+    c.R0_host = nullptr;
+    c.w_host = nullptr;
+    c.stepper = PAB_ADAPTIVE;
+    c.precision = PAB_FP64;
+    c.block_warps = 0;
+    char msg[256];
+    if (pab::validate_config(&c, msg, sizeof(msg)) != PAB_OK) {
+        fprintf(stderr, "pab_el_create: %s\n", msg);
+        return PAB_EINVAL;
+    }
+    const long long N = n_bubbles;
+    std::vector<pab::BinConst> bub((size_t)N);
+    std::vector<long long> cell((size_t)N);
+    for (long long n = 0; n < N; ++n) {
+        const double x = pos_host[n], y = pos_host[N + n], z = pos_host[2 * N + n];
+        const double r0 = R0_host[n];
+        if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(r0 > 0.0) ||
+            !std::isfinite(r0)) {
+            fprintf(stderr, "pab_el_create: bubble %lld has a bad position or radius\n", n);
+            return PAB_EINVAL;
+        }
+        bub[(size_t)n] = pab::make_bin(&c, r0, 1.0);
+        const long long i = (long long)std::floor(x / dx), j = (long long)std::floor(y / dx),
+                        k = (long long)std::floor(z / dx);
+        cell[(size_t)n] = (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz)
+                              ? (k * ny + j) * nx + i
+                              : -1;
+    }
+    pab_el_t *e = new (std::nothrow) pab_el_t();
+    if (!e)
+        return PAB_ENOMEM;
+    e->cfg = c;
+    const double one = 1.0;
+    pab::make_const(&c, &one, &one, &e->K);
+    e->N = N;
+    e->nx = nx;
+    e->ny = ny;
+    e->nz = nz;
+    e->dx = dx;
+    e->create_stream = (cudaStream_t)stream;
+    cudaStream_t s = e->create_stream;
+    const size_t n = (size_t)(N > 0 ? N : 1);
+    cudaError_t err = cudaMallocAsync((void **)&e->pos, 3 * n * sizeof(double), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->cell, n * sizeof(long long), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->bub, n * sizeof(pab::BinConst), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->R, n * sizeof(double), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->V, n * sizeof(double), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->h, n * sizeof(float), s);
+    if (err == cudaSuccess)
+        err = cudaMallocAsync((void **)&e->counters, sizeof(pab::Counters), s);
+    if (err == cudaSuccess)
+        err = cudaMallocHost((void **)&e->counters_host, sizeof(pab::Counters));
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(e->counters, 0, sizeof(pab::Counters), s);
+    if (err == cudaSuccess && N > 0) {
+        err = cudaMemcpyAsync(e->pos, pos_host, 3 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(e->cell, cell.data(), (size_t)N * sizeof(long long),
+                                  cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(e->bub, bub.data(), (size_t)N * sizeof(pab::BinConst),
+                                  cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(e->R, R0_host, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(e->V, 0, (size_t)N * sizeof(double), s);
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(e->h, 0, (size_t)N * sizeof(float), s);
+    }
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(s);  // the host tables above go out of scope
+    if (err != cudaSuccess) {
+        fprintf(stderr, "pab_el_create: %s\n", cudaGetErrorString(err));
+        pab_status st = err == cudaErrorMemoryAllocation ? PAB_ENOMEM : PAB_ECUDA;
+        cudaGetLastError();
+        pab_el_destroy(e);
+        return st;
+    }
+    *out = e;
+    return PAB_OK;
+}
+
+void pab_el_destroy(pab_el_t *e)
+{
+    if (!e)
+        return;
+    cudaStream_t s = e->create_stream;
+    void *bufs[] = {e->pos, e->cell, e->bub, e->R, e->V, e->h, e->counters};
+    for (void *b : bufs)
+        if (b)
+            cudaFreeAsync(b, s);
+    cudaStreamSynchronize(s);
+    if (e->counters_host)
+        cudaFreeHost(e->counters_host);
+    delete e;
+}
+
+pab_status pab_el_step(pab_el_t *e, const double *p_cell_dev, double dt, double *alpha_dev,
+                       double *alpha_dot_dev, void *stream)
+{
+    if (!e)
+        return PAB_EINVAL;
+    if (!p_cell_dev)
+        return efail(e, PAB_EINVAL, "pab_el_step: p_cell_dev is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return efail(e, PAB_EINVAL, "pab_el_step: dt must be positive and finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e->N > 0) {
+        const unsigned blocks = (unsigned)((e->N + 255) / 256);
+        pab::el_advance_kernel<<<blocks, 256, 0, s>>>(e->K, e->N, e->bub, e->cell, p_cell_dev, dt,
+                                                      e->R, e->V, e->h, e->counters);
+        cudaError_t c = cudaGetLastError();
+        if (c != cudaSuccess)
+            return ecuda(e, c, "pab_el_step advance");
+    }
+    if (alpha_dev) {
+        cudaError_t c = launch_smear(e, alpha_dev, alpha_dot_dev, s);
+        if (c != cudaSuccess)
+            return ecuda(e, c, "pab_el_step smear");
+    }
+    return PAB_OK;
+}
+
+pab_status pab_el_smear(pab_el_t *e, double *alpha_dev, double *alpha_dot_dev, void *stream)
+{
+    if (!e)
+        return PAB_EINVAL;
+    if (!alpha_dev)
+        return efail(e, PAB_EINVAL, "pab_el_smear: alpha_dev is NULL");
+    cudaError_t c = launch_smear(e, alpha_dev, alpha_dot_dev, (cudaStream_t)stream);
+    return c == cudaSuccess ? PAB_OK : ecuda(e, c, "pab_el_smear");
+}
+
+pab_status pab_el_status(pab_el_t *e, uint32_t *flags, int64_t *n_flagged, int64_t *n_attempts,
+                         void *stream)
+{
+    if (!e)
+        return PAB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t c = cudaMemcpyAsync(e->counters_host, e->counters, sizeof(pab::Counters),
+                                    cudaMemcpyDeviceToHost, s);
+    if (c == cudaSuccess)
+        c = cudaMemsetAsync(e->counters, 0, sizeof(pab::Counters), s);
+    if (c == cudaSuccess)
+        c = cudaStreamSynchronize(s);
+    if (c != cudaSuccess)
+        return ecuda(e, c, "pab_el_status");
+    const pab::Counters k = *e->counters_host;
+    if (flags)
+        *flags = k.flags_or;
+    if (n_flagged)
+        *n_flagged = (int64_t)k.n_flagged;
+    if (n_attempts)
+        *n_attempts = (int64_t)k.n_attempts;
+    if (k.flags_or & PAB_FLAG_NONFINITE)
+        return efail(e, PAB_ENONFINITE, "non-finite pressure or state (bubble outside the grid?)");
+    if (k.flags_or & PAB_FLAG_STEP_LIMIT)
+        return efail(e, PAB_ESTEP_LIMIT, "max_attempts exhausted");
+    return PAB_OK;
+}
+
+pab_status pab_el_get_state(pab_el_t *e, double *R_dev, double *Rdot_dev, float *h_dev, void *stream)
+{
+    if (!e)
+        return PAB_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)e->N;
+    cudaError_t c = cudaSuccess;
+    if (n && R_dev)
+        c = cudaMemcpyAsync(R_dev, e->R, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c == cudaSuccess && n && Rdot_dev)
+        c = cudaMemcpyAsync(Rdot_dev, e->V, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c == cudaSuccess && n && h_dev)
+        c = cudaMemcpyAsync(h_dev, e->h, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return c == cudaSuccess ? PAB_OK : ecuda(e, c, "pab_el_get_state");
+}
+
+pab_status pab_el_set_state(pab_el_t *e, const double *R_dev, const double *Rdot_dev, const float *h_dev,
+                            void *stream)
+{
+    if (!e)
+        return PAB_EINVAL;
+    if (e->N > 0 && (!R_dev || !Rdot_dev))
+        return efail(e, PAB_EINVAL, "pab_el_set_state: R_dev and Rdot_dev are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)e->N;
+    cudaError_t c = cudaSuccess;
+    if (n)
+        c = cudaMemcpyAsync(e->R, R_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c == cudaSuccess && n)
+        c = cudaMemcpyAsync(e->V, Rdot_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c == cudaSuccess && n && h_dev)
+        c = cudaMemcpyAsync(e->h, h_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return c == cudaSuccess ? PAB_OK : ecuda(e, c, "pab_el_set_state");
+}
+
+}  // extern "C"

@@ -79,6 +79,7 @@ struct StepArgs {
 pab_status validate_config(const pab_config *c, char *msg, size_t n);
 bool bin_table(const pab_config *c, double *R0, double *w);
 void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K);
+BinConst make_bin(const pab_config *c, double R0, double w);  // constants of one radius
 
 // Launchers (pab_kernels.cu).  Return the launch error.
 cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,

@@ -177,3 +177,47 @@ def request_stream(n: int = 2000, rate: float = 200.0, seed: int = 6, n_steps: i
         out.append(Request(i, t, Workload(f"req{i}_L{L}_nb{nb}", L ** 3, nb, 0.3, 1e-8, n_steps, 0.5,
                                           1e5, ("random", sd), seed=sd, precision="mixed")))
     return out
+
+
+@dataclasses.dataclass
+class BubbleCloud:
+    """Volume-averaged (EL) workload: fixed bubbles on a grid, forced cell by cell."""
+    name: str
+    edge: int
+    dx: float
+    pos: np.ndarray      # [3][N]
+    R0: np.ndarray       # [N]
+    theta: np.ndarray    # per-cell forcing phase [edge^3]
+    amp: float = 0.5
+    freq: float = 1e5
+    dt: float = 1e-8
+    n_steps: int = 100
+    fluid: dict = dataclasses.field(default_factory=lambda: dict(WATER))
+
+    @property
+    def n_bubbles(self) -> int:
+        return int(self.R0.shape[0])
+
+    def pressure_step(self, n: int, xp=np, device=None):
+        p0 = self.fluid["p0"]
+        w = 2.0 * math.pi * self.freq
+        t = (n + 0.5) * self.dt
+        if xp is np:
+            return p0 + self.amp * p0 * np.sin(w * t + self.theta)
+        th = self.__dict__.setdefault("_th_dev", xp.as_tensor(self.theta, device=device))
+        return p0 + self.amp * p0 * xp.sin(th + w * t)
+
+
+def bubble_cloud(edge: int = 128, dx: float = 75e-6, alpha0: float = 1e-3, R0ref: float = 10e-6,
+                 s: float = 0.0, seed: int = 7, n_steps: int = 100) -> BubbleCloud:
+    """Bubbles placed uniformly in an edge^3 grid of cells dx (the cost test of Sec. 5.2:
+    75 um cells, R0 = 10 um); their number gives void fraction alpha0; s > 0 draws
+    lognormal radii (median R0ref), s = 0 is monodisperse."""
+    g = _rng(seed)
+    L = edge * dx
+    n = int(round(alpha0 * L ** 3 / (4.0 / 3.0 * math.pi * R0ref ** 3)))
+    pos = g.uniform(0.0, L, size=(3, n))
+    R0 = R0ref * np.exp(s * g.normal(size=n)) if s > 0 else np.full(n, R0ref)
+    th = g.uniform(0.0, 2.0 * math.pi, size=edge ** 3)
+    return BubbleCloud(f"el_cloud{edge}^3_a{alpha0:g}", edge, dx, np.ascontiguousarray(pos), R0, th,
+                       n_steps=n_steps)

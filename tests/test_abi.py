@@ -12,7 +12,7 @@ import pytest
 from paper_2511_21031_gb300 import pab
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h", "pab_closure.h")]
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h", "pab_closure.h", "pab_el.h")]
 
 
 def _declared():
@@ -27,9 +27,10 @@ def test_library_exports_every_declared_entry_point():
     assert len(declared) >= 14
     for name in declared:
         assert hasattr(lib, name), name
-    from paper_2511_21031_gb300 import batch
+    from paper_2511_21031_gb300 import batch, el
     batch.load()
-    assert set(declared) == set(pab.EXPORTS) | set(batch.EXPORTS)
+    el.load()
+    assert set(declared) == set(pab.EXPORTS) | set(batch.EXPORTS) | set(el.EXPORTS)
 
 
 def test_config_layout_matches_c():
