@@ -31,14 +31,22 @@ FLAG_SUPERSONIC = 4
 FLAG_NONPOS = 8
 
 
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+          "-D_GNU_SOURCE"]
+
+
+def compile_to(src: str, out: str) -> str:
+    """Compile an oracle source file to a shared library (FP64, no FMA contraction, no fast-math)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no FMA contraction, no fast-math)."""
+    """Compile the oracle in place when missing or older than its source."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+        compile_to(_SRC, _LIB_PATH)
     return _LIB_PATH
 
 
@@ -82,7 +90,10 @@ def _lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
-            lib = ctypes.CDLL(build())
+            # PAB_ORACLE_LIB: a compiled copy of this oracle with one planted mistake,
+            # used only by tests/test_oracle_mutations.py to show the pins catch it
+            alt = os.environ.get("PAB_ORACLE_LIB")
+            lib = ctypes.CDLL(alt if alt else build())
             P = ctypes.POINTER(_Params)
             lib.orc_bins.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, _dp, _dp]
