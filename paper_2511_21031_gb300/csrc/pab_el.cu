@@ -91,8 +91,12 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                     const double *__restrict__ V, int nx, int ny, int nz, double dx,
                     double *__restrict__ alpha, double *__restrict__ alpha_dot)
 {
-    __shared__ double fac[kSmearWarps][3][kSide];  // exp(-c^2/(2h^2)) per axis offset
-    __shared__ double sq[kSmearWarps][3][kSide];   // c^2 per axis offset
+    // per warp and axis offset: the squared distance (FP64 and FP32) and the 1-D
+    // Gaussian factor; the x factor carries V/(h^3 (2 pi)^{3/2}) so that a stencil
+    // point costs two FP64 multiplies (three with the rate)
+    __shared__ double fac[kSmearWarps][3][kSide];
+    __shared__ double sq[kSmearWarps][3][kSide];
+    __shared__ float sqf[kSmearWarps][3][kSide];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const double norm = 15.749609945722419;  // (2 pi)^{3/2}
@@ -103,56 +107,59 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
         const int m = (int)floor(3.0 * h / dx) + 1;  // cells whose centre can lie within 3h
         const int side = 2 * m + 1;
         const bool cached = m <= kCacheHalf;
-        const double pos[3] = {px[n], py[n], pz[n]};
-        int base[3];
-        for (int a = 0; a < 3; ++a)
-            base[a] = (int)floor(pos[a] / dx) - m;
+        const double x0 = px[n], y0 = py[n], z0 = pz[n];
+        const int bx = (int)floor(x0 / dx) - m, by = (int)floor(y0 / dx) - m, bz = (int)floor(z0 / dx) - m;
         const double inv2h2 = 1.0 / (2.0 * h * h);
+        const double Vb = 4.0 / 3.0 * 3.14159265358979323846 * r * r * r;
+        const double Vd = 4.0 * 3.14159265358979323846 * r * r * V[n];
+        const double amp = Vb / (h * h * h * norm);  // V times the kernel's normalisation
+        const double rate = Vd / Vb;                  // alpha_dot / alpha of this bubble
         if (cached) {
             for (int t = lane; t < 3 * side; t += 32) {
                 const int a = t / side, o = t % side;
-                const double cc = ((double)(base[a] + o) + 0.5) * dx - pos[a];
-                sq[warp][a][o] = cc * cc;
-                fac[warp][a][o] = exp(-cc * cc * inv2h2);
+                const double pa = a == 0 ? x0 : (a == 1 ? y0 : z0);
+                const int ba = a == 0 ? bx : (a == 1 ? by : bz);
+                const double cc = ((double)(ba + o) + 0.5) * dx - pa;
+                const double c2 = cc * cc;
+                sq[warp][a][o] = c2;
+                sqf[warp][a][o] = (float)c2;
+                const double f = exp(-c2 * inv2h2);
+                fac[warp][a][o] = a == 0 ? f * amp : f;
             }
         }
         __syncwarp();
-        const double Vb = 4.0 / 3.0 * 3.14159265358979323846 * r * r * r;
-        const double Vd = 4.0 * 3.14159265358979323846 * r * r * V[n];
-        const double scale = 1.0 / (h * h * h * norm);
         const double lim2 = 9.0 * h * h;
+        const float lim2f = (float)lim2;
         const long long count = (long long)side * side * side;
         for (long long t = lane; t < count; t += 32) {
             const int oi = (int)(t % side), oj = (int)((t / side) % side), ok = (int)(t / ((long long)side * side));
-            const int i = base[0] + oi, j = base[1] + oj, k = base[2] + ok;
+            const int i = bx + oi, j = by + oj, k = bz + ok;
             if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz)
                 continue;
-            double sx, sy, sz;
+            double a;
             if (cached) {
-                sx = sq[warp][0][oi];
-                sy = sq[warp][1][oj];
-                sz = sq[warp][2][ok];
+                const float d2f = sqf[warp][0][oi] + sqf[warp][1][oj] + sqf[warp][2][ok];
+                bool inside = d2f < lim2f;
+                if (fabsf(d2f - lim2f) <= 1e-5f * lim2f) {  // near the cut: decide as d/h < 3
+                    const double d2 = sq[warp][0][oi] + sq[warp][1][oj] + sq[warp][2][ok];
+                    inside = sqrt(d2) / h < 3.0;
+                }
+                if (!inside)
+                    continue;
+                a = fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok];
             } else {
-                const double cx = ((double)i + 0.5) * dx - pos[0];
-                const double cy = ((double)j + 0.5) * dx - pos[1];
-                const double cz = ((double)k + 0.5) * dx - pos[2];
-                sx = cx * cx;
-                sy = cy * cy;
-                sz = cz * cz;
+                const double cx = ((double)i + 0.5) * dx - x0;
+                const double cy = ((double)j + 0.5) * dx - y0;
+                const double cz = ((double)k + 0.5) * dx - z0;
+                const double d2 = cx * cx + cy * cy + cz * cz;
+                if (!(sqrt(d2) / h < 3.0))
+                    continue;
+                a = amp * exp(-d2 * inv2h2);
             }
-            const double d2 = sx + sy + sz;
-            bool inside = d2 < lim2;
-            if (fabs(d2 - lim2) <= 1e-12 * lim2)  // on the cut: decide exactly as d/h < 3
-                inside = sqrt(d2) / h < 3.0;
-            if (!inside)
-                continue;
-            const double g = cached ? fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok]
-                                    : exp(-d2 * inv2h2);
-            const double delta = g * scale;
             const long long c = ((long long)k * ny + j) * nx + i;
-            atomicAdd(&alpha[c], Vb * delta);
+            atomicAdd(&alpha[c], a);
             if (alpha_dot)
-                atomicAdd(&alpha_dot[c], Vd * delta);
+                atomicAdd(&alpha_dot[c], a * rate);
         }
         __syncwarp();
     }
