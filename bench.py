@@ -45,12 +45,12 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel executes per trial
 # (one sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination,
-# error norm, controller) and per bin-step outside the trial loop (load, first
-# exact gas evaluation, wall pressure and quadrature sums): least-squares fit of
-# ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over nine
-# launches of the 64^3 x 31 grid with traced trial counts (residual 3e-4).
-FP64_FLOPS_PER_TRIAL = 254.5
-FP64_FLOPS_PER_BINSTEP = 113.4
+# error norm, controller) and per bin-step outside the trial loop (load, wall
+# pressure and quadrature sums): least-squares fit of ncu's
+# smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over six launches
+# of the 64^3 x 31 grid with traced trial counts (residual 3e-4).
+FP64_FLOPS_PER_TRIAL = 260.5
+FP64_FLOPS_PER_BINSTEP = 62.2
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
 # on the 64^3 x 31 grid, 283.5 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 34.9

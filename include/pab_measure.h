@@ -30,18 +30,22 @@ pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int3
                         double *sink_dev, float *ms_out, double *fma_out, void *stream);
 
 /*
- * Values of two FP64 device helpers, for the tests to compare with
+ * Values of the FP64 device helpers, for the tests to compare with
  * high-precision references (no counterpart in the paper):
- *   gas_dev[i]   = the library's (1/R[i])^a reached from the base radius Rb[i]
- *                  (exact value at Rb[i] times the binomial series of
- *                  (1 + d)^(-a), d = (R[i] - Rb[i]) / Rb[i], or the exact value
- *                  when |d| is beyond the series' range);
- *   exact_dev[i] = exp(a log(1/R[i])) with CUDA's exp and log;
- *   rcbrt_dev[i] = the library's R[i]^(-1/3) (FP32 seed, one FP64 Newton step).
- * All arrays [n] FP64 on the device; a = 3 gamma > 0.  Errors: PAB_EINVAL, PAB_ECUDA.
+ *   gas_dev[i]     = the library's (1/R[i])^a reached from the base radius Rb[i]
+ *                    (exact value at Rb[i] times the binomial series of
+ *                    (1 + d)^(-a), d = (R[i] - Rb[i]) / Rb[i], or the exact value
+ *                    when |d| is beyond the series' range);
+ *   gas_tab_dev[i] = the same value from the node table a handle uses (nearest
+ *                    node x_j = q^j of R[i], node value times the series);
+ *   exact_dev[i]   = exp(a log(1/R[i])) with CUDA's exp and log;
+ *   rcbrt_dev[i]   = the library's R[i]^(-1/3) (FP32 seed, one FP64 Newton step).
+ * All arrays [n] FP64 on the device; a = 3 gamma > 0.  Allocates and frees a
+ * small table.  Errors: PAB_EINVAL, PAB_ECUDA.
  */
 pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
-                          double *gas_dev, double *exact_dev, double *rcbrt_dev, void *stream);
+                          double *gas_dev, double *gas_tab_dev, double *exact_dev, double *rcbrt_dev,
+                          void *stream);
 
 #ifdef __cplusplus
 }

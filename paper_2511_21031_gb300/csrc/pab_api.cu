@@ -24,6 +24,7 @@ struct pab_s {
     double *V = nullptr;
     float *h = nullptr;
     int32_t *attempts = nullptr;
+    double *gas_tab = nullptr;  // gas-term nodes (K.gas_tab points here)
     pab::Counters *counters = nullptr;
     pab::Counters *counters_host = nullptr;  // pinned
     double *stage_p = nullptr;                // host entry point staging [C]
@@ -178,6 +179,7 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
         b.invR0f = (float)(1.0 / R0[i]);
         b.pg0f = (float)b.pg0;
         b.dpeqf = (float)(b.peq - c->p0);
+        b.invR0 = 1.0 / R0[i];
         m3 += w[i] * R0[i] * R0[i] * R0[i];
     }
     K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;
@@ -191,6 +193,9 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
         ck *= (-a - (double)k) / (double)(k + 1);
     }
     K->gas_dmax = std::pow(1.1e-16 / std::fabs(ck), 1.0 / (double)pab::kGasTerms);
+    K->gas_tab = nullptr;  // the handle attaches its table after allocating it
+    K->gas_inv_log2q = 0.0;
+    K->gas_J = 0;
 }
 
 }  // namespace
@@ -216,6 +221,25 @@ bool bin_table(const pab_config *c, double *R0, double *w)
 void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K)
 {
     build_const(c, R0, w, K);
+}
+
+// Nodes x_j = q^j with (sqrt(q) - 1) = 0.9 d_max, so that the nearest node of any
+// x in [q^-J, q^J] lies within the series' range; J covers R/R0 from 1/25 to 25.
+void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *inv_log2q)
+{
+    const double sq = 1.0 + 0.9 * dmax;
+    const double q = sq * sq;
+    const double lq = std::log(q);
+    *J = (int)std::ceil(std::log(25.0) / lq);
+    *inv_log2q = 1.0 / std::log2(q);
+    tab->resize((size_t)3 * (2 * *J + 1));
+    for (int j = -*J; j <= *J; ++j) {
+        const double x = std::exp((double)j * lq);
+        double *e = tab->data() + 3 * (size_t)(j + *J);
+        e[0] = x;
+        e[1] = 1.0 / x;
+        e[2] = std::pow(x, -a);
+    }
 }
 
 BinConst make_bin(const pab_config *c, double R0, double w)
@@ -329,6 +353,21 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
         e = cudaMallocAsync((void **)&h->counters, sizeof(pab::Counters), s);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&h->counters_host, sizeof(pab::Counters));
+    std::vector<double> tab;
+    int J = 0;
+    double il2q = 0.0;
+    pab::gas_table(3.0 * cfg->gamma, h->K.gas_dmax, &tab, &J, &il2q);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void **)&h->gas_tab, tab.size() * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->gas_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // tab is a host temporary
+    if (e == cudaSuccess) {
+        h->K.gas_tab = h->gas_tab;
+        h->K.gas_J = J;
+        h->K.gas_inv_log2q = il2q;
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->counters, 0, sizeof(pab::Counters), s);
     if (e == cudaSuccess && h->attempts)
@@ -355,7 +394,7 @@ void pab_destroy(pab_t *h)
     cudaGetDevice(&cur);
     if (cur != h->device)
         cudaSetDevice(h->device);
-    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->counters, h->stage_p, h->stage_nb,
+    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->gas_tab, h->counters, h->stage_p, h->stage_nb,
                     h->stage_out};
     for (void *b : bufs)
         if (b)

@@ -24,23 +24,41 @@ struct GasBase {
     }
 };
 
-// p_g0 (R0/R)^(3 gamma) given R and 1/R.  Within a step the radii stay close
-// to the last exact evaluation Rb: with d = (R - Rb)/Rb,
-//   (R0/R)^(3 gamma) = (R0/Rb)^(3 gamma) (1 + d)^(-3 gamma),
-// and the binomial series of (1 + d)^(-3 gamma) (degree 11, used only where its
-// first omitted term is below half an ulp) replaces CUDA's exp and log.
-// Farther away the value is exact, exp(3 gamma log(R0/R)), and becomes the base.
+// (1 + d)^(-3 gamma) by its binomial series (degree 11); callers keep |d| within
+// gas_dmax, where the first omitted term is below half an ulp.
+__device__ __forceinline__ double gas_series(const StepConst &K, double d)
+{
+    double s = K.gas_c[kGasTerms - 1];
+#pragma unroll
+    for (int k = kGasTerms - 2; k >= 0; --k)
+        s = fma(s, d, K.gas_c[k]);
+    return s;
+}
+
+// p_g0 (R0/R)^(3 gamma) given R and 1/R.
+//  - With a node table (a handle's gas_tab): x = R/R0 goes to the nearest node
+//    x_j = q^j (picked with an FP32 log2), and (R0/R)^(3 gamma) = T_j (1 + d)^(-3 gamma)
+//    with d = (x - x_j)/x_j, |d| <= sqrt(q) - 1 < gas_dmax.  A pure function of R:
+//    no exp or log while R/R0 stays within the table.
+//  - Otherwise (or outside the table): the radii of one step stay close to the
+//    last exact evaluation R_b in g, reached by the same series in
+//    d = (R - R_b)/R_b; farther away the value is exact, exp(3 gamma log(R0/R)),
+//    and becomes the new base.
 __device__ __forceinline__ double gas_pressure(const StepConst &K, const BinConst &bc, double R,
                                                double iR, GasBase &g)
 {
-    const double d = (R - g.Rb) * g.invRb;
-    if (fabs(d) <= K.gas_dmax) {
-        double s = K.gas_c[kGasTerms - 1];
-#pragma unroll
-        for (int k = kGasTerms - 2; k >= 0; --k)
-            s = fma(s, d, K.gas_c[k]);
-        return g.Pb * s;
+    if (K.gas_tab) {
+        const double x = R * bc.invR0;
+        const int j = __float2int_rn(__log2f((float)x) * (float)K.gas_inv_log2q);
+        if (j >= -K.gas_J && j <= K.gas_J) {
+            const double *e = K.gas_tab + 3 * (j + K.gas_J);
+            const double d = (x - e[0]) * e[1];
+            return bc.pg0 * e[2] * gas_series(K, d);
+        }
     }
+    const double d = (R - g.Rb) * g.invRb;
+    if (fabs(d) <= K.gas_dmax)
+        return g.Pb * gas_series(K, d);
     const double P = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));
     g.Rb = R;
     g.invRb = iR;

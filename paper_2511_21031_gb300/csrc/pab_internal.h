@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pab.h"
 
 namespace pab {
@@ -19,6 +21,7 @@ struct BinConst {
     float invR0f;  // 1/R0 in FP32
     float pg0f;    // pg0 in FP32
     float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
+    double invR0;  // 1/R0
 };
 
 constexpr int kGasTerms = 12;  // binomial series of the gas term: degree 11
@@ -46,6 +49,12 @@ struct StepConst {
     // (1 + d)^(-3 gamma) = sum_k gas_c[k] d^k for |d| <= gas_dmax (truncation below half an ulp)
     double gas_c[kGasTerms];
     double gas_dmax;
+    // optional table of nodes x_j = q^j, j = -gas_J..gas_J, as {x_j, 1/x_j, x_j^(-3 gamma)}:
+    // (R/R0)^(-3 gamma) = T_j (1 + d)^(-3 gamma) with d = (R/R0 - x_j)/x_j (nullptr: no table)
+    const double *gas_tab;
+    double gas_inv_log2q;  // 1/log2(q)
+    int32_t gas_J;
+    int32_t gas_pad;
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
     float cbrt_tolf, v_collapsef, r_collapsef, padf;
     BinConst bins[PAB_MAX_BINS];
@@ -80,6 +89,8 @@ pab_status validate_config(const pab_config *c, char *msg, size_t n);
 bool bin_table(const pab_config *c, double *R0, double *w);
 void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K);
 BinConst make_bin(const pab_config *c, double R0, double w);  // constants of one radius
+// Host values of the gas-term table for a = 3 gamma (3 * (2 J + 1) doubles) and its spacing.
+void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *inv_log2q);
 
 // Launchers (pab_kernels.cu).  Return the launch error.
 cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,

@@ -1,6 +1,8 @@
 // FMA throughput microbenchmark (measurement aid for the roofline).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "pab_device.cuh"
 #include "pab_internal.h"
 #include "pab_measure.h"
@@ -24,9 +26,9 @@ __global__ void fma_streams(int iters, double *sink)
         (double)(a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7);
 }
 
-__global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, long long n,
-                                  const double *R, const double *Rb, double *gas, double *exact,
-                                  double *rc)
+__global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, const double *tab,
+                                  long long n, const double *R, const double *Rb, double *gas,
+                                  double *gas_tab, double *exact, double *rc)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -35,6 +37,11 @@ __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, long
         g.reset();
         (void)pab::gas_pressure(K, bc, Rb[i], 1.0 / Rb[i], g);  // exact at the base
         gas[i] = pab::gas_pressure(K, bc, R[i], 1.0 / R[i], g);
+        pab::StepConst Kt = K;  // the same constants with the node table attached
+        Kt.gas_tab = tab;
+        pab::GasBase g2;
+        g2.reset();
+        gas_tab[i] = pab::gas_pressure(Kt, Kt.bins[0], R[i], 1.0 / R[i], g2);
         exact[i] = exp(K.three_gamma * log(1.0 / R[i]));
         rc[i] = pab::rcbrt_newton(R[i]);
     }
@@ -43,9 +50,11 @@ __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, long
 }  // namespace
 
 extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
-                                     double *gas_dev, double *exact_dev, double *rcbrt_dev, void *stream)
+                                     double *gas_dev, double *gas_tab_dev, double *exact_dev,
+                                     double *rcbrt_dev, void *stream)
 {
-    if (n < 0 || !(a > 0.0) || (n > 0 && (!R_dev || !Rb_dev || !gas_dev || !exact_dev || !rcbrt_dev)))
+    if (n < 0 || !(a > 0.0) ||
+        (n > 0 && (!R_dev || !Rb_dev || !gas_dev || !gas_tab_dev || !exact_dev || !rcbrt_dev)))
         return PAB_EINVAL;
     if (n == 0)
         return PAB_OK;
@@ -59,9 +68,27 @@ extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const doubl
     const double R0 = 1.0, w = 1.0;
     pab::StepConst K;
     pab::make_const(&c, &R0, &w, &K);  // pg0 = p0 + 0 - 0 = 1
-    math_check_kernel<<<152 * 4, 256, 0, (cudaStream_t)stream>>>(K, n, R_dev, Rb_dev, gas_dev,
-                                                                  exact_dev, rcbrt_dev);
-    return cudaGetLastError() == cudaSuccess ? PAB_OK : PAB_ECUDA;
+    std::vector<double> tab;
+    int J = 0;
+    double il2q = 0.0;
+    pab::gas_table(a, K.gas_dmax, &tab, &J, &il2q);
+    K.gas_J = J;
+    K.gas_inv_log2q = il2q;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *tab_dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tab_dev, tab.size() * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        math_check_kernel<<<152 * 4, 256, 0, s>>>(K, tab_dev, n, R_dev, Rb_dev, gas_dev, gas_tab_dev,
+                                                   exact_dev, rcbrt_dev);
+        e = cudaGetLastError();
+    }
+    if (tab_dev)
+        cudaFreeAsync(tab_dev, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
 }
 
 extern "C" pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int32_t iters,
