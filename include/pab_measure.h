@@ -47,6 +47,30 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
                           double *gas_dev, double *gas_tab_dev, double *exact_dev, double *rcbrt_dev,
                           void *stream);
 
+/*
+ * Values of the helpers that take work off the FP64 pipe, for the tests to
+ * compare with the hardware's own conversions, compares and division (no
+ * counterpart in the paper).  For i < n:
+ *   f2d_dev[i]  = the library's integer float -> double of f_dev[i];
+ *   f2d_hw[i]   = (double)f_dev[i] by the conversion instruction;
+ *   rcp_dev[i]  = the library's reciprocal of x_dev[i];
+ *   div_dev[i]  = 1.0 / x_dev[i] (IEEE division);
+ *   seed_dev[i] = the rcp.approx.ftz.f64 estimate the reciprocal starts from;
+ *   cmp_dev[i]  = bit k set when the library's k-th predicate disagrees with the
+ *                 IEEE one: 0 x > 0, 1 x <= y, 2 isfinite(x), 3 |x| >= y,
+ *                 4 fmax(|x|, y) (compared as bit patterns), 5 fmin(|x|, y),
+ *                 6 (float)x (bit patterns, with subnormal float results
+ *                 flushed to a signed zero; NaN for NaN), 7 the embedded
+ *                 difference 2 k3 - (k1 + k2) of k1 = f, k2 = (float)x,
+ *                 k3 = (float)y against FP64 within 4 ulp of its terms;
+ *                 y_dev[i] must be a finite number >= +0.
+ * f_dev [n] float; the others [n] double (cmp_dev [n] uint8), all on the device.
+ * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.
+ */
+pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, const double *y_dev,
+                          double *f2d_dev, double *f2d_hw, double *rcp_dev, double *div_dev,
+                          double *seed_dev, uint8_t *cmp_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

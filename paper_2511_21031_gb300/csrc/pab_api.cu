@@ -152,6 +152,10 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->two_sigma = 2.0 * c->sigma;
     K->ic_rho = K->inv_c / c->rho;
     K->fmu_ic_rho = 4.0 * c->mu * K->inv_c / c->rho;
+    K->fmu_rho = 4.0 * c->mu / c->rho;
+    K->tsig_rho = 2.0 * c->sigma / c->rho;
+    K->pv_rho = c->pv / c->rho;
+    K->m05_inv_c = -0.5 * K->inv_c;
     K->tol = c->tol;
     K->cbrt_tol = std::cbrt(c->tol);
     K->v_floor = c->v_floor >= 0.0 ? c->v_floor : 1e-3 * std::sqrt(c->p0 / c->rho);
@@ -168,18 +172,22 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->cbrt_tolf = (float)K->cbrt_tol;
     K->v_collapsef = (float)K->v_collapse;
     K->r_collapsef = (float)K->r_collapse;
+    K->cf = (float)c->c;
     double m3 = 0.0;
     for (int i = 0; i < c->n_bins; ++i) {
         pab::BinConst &b = K->bins[i];
         b.R0 = R0[i];
         b.w = w[i];
-        b.pg0 = c->gas_mode == PAB_GAS_POLYTROPIC ? c->p0 + 2.0 * c->sigma / R0[i] - c->pv : 0.0;
-        b.peq = c->pv + b.pg0 - 2.0 * c->sigma / R0[i];
+        const double pg0 =
+            c->gas_mode == PAB_GAS_POLYTROPIC ? c->p0 + 2.0 * c->sigma / R0[i] - c->pv : 0.0;
+        const double peq = c->pv + pg0 - 2.0 * c->sigma / R0[i];
         b.R0f = (float)R0[i];
         b.invR0f = (float)(1.0 / R0[i]);
-        b.pg0f = (float)b.pg0;
-        b.dpeqf = (float)(b.peq - c->p0);
+        b.pg0f = (float)pg0;
+        b.dpeqf = (float)(peq - c->p0);
         b.invR0 = 1.0 / R0[i];
+        b.A1 = pg0 / c->rho;
+        b.A2 = 3.0 * c->gamma * pg0 / c->rho * K->inv_c;
         m3 += w[i] * R0[i] * R0[i] * R0[i];
     }
     K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;
@@ -191,10 +199,12 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     for (int k = 0; k < pab::kGasTerms; ++k) {
         K->gas_c[k] = ck;
         ck *= (-a - (double)k) / (double)(k + 1);
+        if (k + 1 == pab::kGasTabTerms)
+            K->gas_dmax_tab = std::pow(1.1e-16 / std::fabs(ck), 1.0 / (double)pab::kGasTabTerms);
     }
     K->gas_dmax = std::pow(1.1e-16 / std::fabs(ck), 1.0 / (double)pab::kGasTerms);
     K->gas_tab = nullptr;  // the handle attaches its table after allocating it
-    K->gas_inv_log2q = 0.0;
+    K->gas_inv_log2q = 0.0f;
     K->gas_J = 0;
 }
 
@@ -232,13 +242,14 @@ void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *
     const double lq = std::log(q);
     *J = (int)std::ceil(std::log(25.0) / lq);
     *inv_log2q = 1.0 / std::log2(q);
-    tab->resize((size_t)3 * (2 * *J + 1));
+    tab->resize((size_t)4 * (2 * *J + 1));
     for (int j = -*J; j <= *J; ++j) {
         const double x = std::exp((double)j * lq);
-        double *e = tab->data() + 3 * (size_t)(j + *J);
+        double *e = tab->data() + 4 * (size_t)(j + *J);
         e[0] = x;
         e[1] = 1.0 / x;
         e[2] = std::pow(x, -a);
+        e[3] = 0.0;
     }
 }
 
@@ -356,7 +367,7 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
     std::vector<double> tab;
     int J = 0;
     double il2q = 0.0;
-    pab::gas_table(3.0 * cfg->gamma, h->K.gas_dmax, &tab, &J, &il2q);
+    pab::gas_table(3.0 * cfg->gamma, h->K.gas_dmax_tab, &tab, &J, &il2q);
     if (e == cudaSuccess)
         e = cudaMallocAsync((void **)&h->gas_tab, tab.size() * sizeof(double), s);
     if (e == cudaSuccess)
@@ -366,7 +377,7 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
     if (e == cudaSuccess) {
         h->K.gas_tab = h->gas_tab;
         h->K.gas_J = J;
-        h->K.gas_inv_log2q = il2q;
+        h->K.gas_inv_log2q = (float)il2q;
     }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->counters, 0, sizeof(pab::Counters), s);

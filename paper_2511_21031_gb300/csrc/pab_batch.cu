@@ -251,12 +251,7 @@ __global__ void __launch_bounds__(512)
             for (int b = 0; b < d.B; ++b) {
                 const double x = terms[((size_t)0 * max_bins + b) * kTile + lane];
                 if (MIXED) {
-                    const double t = m3 + x;
-                    if (fabs(m3) >= fabs(x))
-                        m3c += (m3 - t) + x;
-                    else
-                        m3c += (x - t) + m3;
-                    m3 = t;
+                    neumaier_add(m3, m3c, x);
                 } else {
                     m3 += x;
                 }

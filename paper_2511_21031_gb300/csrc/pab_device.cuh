@@ -8,119 +8,118 @@
 #include <cfloat>
 #include <cstdint>
 
+#include "pab_bits.cuh"
 #include "pab_internal.h"
 
 namespace pab {
 
-// Gas pressure p_g0 (R0/R)^(3 gamma) at the last exact evaluation, the base
-// from which nearby radii are reached by the binomial series.
+// Gas factor G = (R0/R)^(3 gamma) at the last exact evaluation, the base from
+// which nearby radii are reached by the binomial series.
 struct GasBase {
-    double Rb, invRb, Pb;
+    double Rb, invRb, Gb;
     __device__ __forceinline__ void reset()
     {
         Rb = CUDART_NAN;  // forces an exact evaluation first
         invRb = CUDART_NAN;
-        Pb = 0.0;
+        Gb = 0.0;
     }
 };
 
-// (1 + d)^(-3 gamma) by its binomial series (degree 11); callers keep |d| within
-// gas_dmax, where the first omitted term is below half an ulp.
+// (1 + d)^(-3 gamma) by its binomial series truncated after N terms; callers
+// keep |d| within the bound for N (gas_dmax for kGasTerms, gas_dmax_tab for
+// kGasTabTerms), where the first omitted term is below half an ulp.
+template <int N>
 __device__ __forceinline__ double gas_series(const StepConst &K, double d)
 {
-    double s = K.gas_c[kGasTerms - 1];
+    double s = K.gas_c[N - 1];
 #pragma unroll
-    for (int k = kGasTerms - 2; k >= 0; --k)
+    for (int k = N - 2; k >= 0; --k)
         s = fma(s, d, K.gas_c[k]);
     return s;
 }
 
-// p_g0 (R0/R)^(3 gamma) given R and 1/R.
+// G = (R0/R)^(3 gamma) for R > 0.
 //  - With a node table (a handle's gas_tab): x = R/R0 goes to the nearest node
-//    x_j = q^j (picked with an FP32 log2), and (R0/R)^(3 gamma) = T_j (1 + d)^(-3 gamma)
-//    with d = (x - x_j)/x_j, |d| <= sqrt(q) - 1 < gas_dmax.  A pure function of R:
-//    no exp or log while R/R0 stays within the table.
+//    x_j = q^j (picked in FP32: log2(x)/log2(q) rounded), and G = T_j (1 + d)^(-3 gamma)
+//    with d = (x - x_j)/x_j, |d| < gas_dmax_tab (degree-7 series). A pure
+//    function of R: no exp or log while R/R0 stays within the table.
 //  - Otherwise (or outside the table): the radii of one step stay close to the
-//    last exact evaluation R_b in g, reached by the same series in
-//    d = (R - R_b)/R_b; farther away the value is exact, exp(3 gamma log(R0/R)),
+//    last exact evaluation R_b in g, reached by the degree-11 series in
+//    d = (R - R_b)/R_b; farther away the value is exact, exp(-3 gamma log(R/R0)),
 //    and becomes the new base.
-__device__ __forceinline__ double gas_pressure(const StepConst &K, const BinConst &bc, double R,
-                                               double iR, GasBase &g)
+__device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst &bc, double R,
+                                             GasBase &g)
 {
     if (K.gas_tab) {
-        const double x = R * bc.invR0;
-        const int j = __float2int_rn(__log2f((float)x) * (float)K.gas_inv_log2q);
+        const float xf = d2f(R) * bc.invR0f;
+        const int j = __float2int_rn(__log2f(xf) * K.gas_inv_log2q);
         if (j >= -K.gas_J && j <= K.gas_J) {
-            const double *e = K.gas_tab + 3 * (j + K.gas_J);
-            const double d = (x - e[0]) * e[1];
-            return bc.pg0 * e[2] * gas_series(K, d);
+            const double2 *e = reinterpret_cast<const double2 *>(K.gas_tab) + 2 * (j + K.gas_J);
+            const double2 n0 = __ldg(e), n1 = __ldg(e + 1);  // {x_j, 1/x_j}, {T_j, 0}
+            const double d = fma(R, bc.invR0, -n0.x) * n0.y;
+            return n1.x * gas_series<kGasTabTerms>(K, d);
         }
     }
     const double d = (R - g.Rb) * g.invRb;
-    if (fabs(d) <= K.gas_dmax)
-        return g.Pb * gas_series(K, d);
-    const double P = bc.pg0 * exp(K.three_gamma * log(bc.R0 * iR));
+    if (le(abs_nn(d), K.gas_dmax))
+        return g.Gb * gas_series<kGasTerms>(K, d);
+    const double G = exp(-K.three_gamma * log(R * bc.invR0));
     g.Rb = R;
-    g.invRb = iR;
-    g.Pb = P;
-    return P;
+    g.invRb = rcp64(R);
+    g.Gb = G;
+    return G;
 }
 
 // x^(-1/3) for x > 0: FP32 seed rcbrtf, then one Newton step for y^-3 = x in
 // FP64, y <- y + y (1 - x y^3)/3 (relative error ~1e-14; the seed's ~1e-7 squared).
 __device__ __forceinline__ double rcbrt_newton(double x)
 {
-    const double y = (double)rcbrtf((float)x);
+    const double y = f2d(rcbrtf(d2f(x)));
     const double e = fma(-x, y * y * y, 1.0);
     return fma(y * (1.0 / 3.0), e, y);
 }
 
 struct Trial {
     double R, V;    // third-order result y3
-    double eR, eV;  // |y3 - y2| per component (embedded second-order difference)
+    double eR, eV;  // y3 - z per component (embedded second-order difference; its sign is dropped
+                    // where error_norm multiplies it)
     bool ok;        // every stage radius positive and y3 finite
 };
 
 // ---------------------------------------------------------------------------
 // Keller-Miksis acceleration, Eq. (keller_miksis), FP64.
-//   p_b = pv + p_g0 (R0/R)^(3 gamma)       (Ando's ODE without transfer terms)
-//   p_bw = p_b - (4 mu Rdot + 2 sigma)/R
-//   d/dt p_bw = -3 gamma (p_b - pv) Rdot/R + (4 mu Rdot + 2 sigma) Rdot/R^2 - 4 mu Rddot/R
+//   p_b = pv + p_g0 G,  G = (R0/R)^(3 gamma)   (Ando's ODE without transfer terms)
+//   p_bw = p_b - s/R,   s = 4 mu Rdot + 2 sigma
+//   d/dt p_bw = -3 gamma p_g0 G Rdot/R + s Rdot/R^2 - 4 mu Rddot/R
 // The Rddot inside d/dt p_bw moves to the left-hand side, whose coefficient
-// becomes R (1 - Rdot/c) + 4 mu/(rho c).  1/c = 0 gives Rayleigh-Plesset.
-// The gas term comes from gas_pressure (binomial series around the last exact
-// evaluation exp(3 gamma log(R0/R)), a few ulp from pow).
+// becomes den = R (1 - Rdot/c) + 4 mu/(rho c).  Collecting the right-hand side
+// over rho, the s/R terms of (p_bw - p_inf)(1 + Rdot/c)/rho and of
+// (R/(rho c)) d/dt p_bw add up to -s/(rho R), which leaves
+//   Rddot = (N0 R - s/rho) / (R den),
+//   N0 = (B0 + A1 G)(1 + Rdot/c) - Rdot (A2 G + Rdot (3/2 - Rdot/(2c))),
+// with B0 = (pv - p_inf)/rho per cell, A1 = p_g0/rho and A2 = 3 gamma p_g0/(rho c)
+// per bin: one reciprocal and no other division.  1/c = 0 gives Rayleigh-Plesset.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double p_inf,
+__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
                                           double R, double V, GasBase &g)
 {
-    const double icV = V * K.inv_c;
-    const double den = fma(R, 1.0 - icV, K.fmu_ic_rho);
-    // one division gives both reciprocals: 1/R = den/(R den), 1/den = R/(R den)
-    const double inv = 1.0 / (R * den);
-    const double iR = den * inv;
-    const double iden = R * inv;
-    const double VR = V * iR;
-    double pg = 0.0;
-    if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = gas_pressure(K, bc, R, iR, g);  // p_g0 (R0/R)^(3 gamma)
-    const double s = fma(K.four_mu, V, K.two_sigma);
-    const double pbw = (K.pv + pg) - s * iR;
-    const double dpbw = (s * iR - K.three_gamma * pg) * VR;
-    const double num = (pbw - p_inf) * K.inv_rho * (1.0 + icV) + R * K.ic_rho * dpbw
-                     - 1.5 * V * V * (1.0 - icV * (1.0 / 3.0));
-    return num * iden;
+    const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
+    const double den = fma(R, fma(V, -K.inv_c, 1.0), K.fmu_ic_rho);
+    const double inv = rcp64(R * den);
+    const double P = fma(bc.A1, G, B0);
+    const double q = fma(V, fma(V, K.m05_inv_c, 1.5), bc.A2 * G);
+    const double N0 = fma(P, fma(V, K.inv_c, 1.0), -V * q);
+    const double s_rho = fma(K.fmu_rho, V, K.tsig_rho);
+    return fma(N0, R, -s_rho) * inv;
 }
 
-// Wall pressure p_bw at (R, Rdot) in FP64 (for the <R^3 p_bw> moment).
-__device__ __forceinline__ double wall_pressure64(const StepConst &K, const BinConst &bc, double R,
-                                                  double V, GasBase &g)
+// Wall pressure over rho, p_bw/rho = pv/rho + A1 G - s/(rho R), in FP64 (for
+// the <R^3 p_bw> moment; the sums are scaled by rho once per cell).
+__device__ __forceinline__ double wall_pressure_rho64(const StepConst &K, const BinConst &bc,
+                                                      double R, double V, GasBase &g)
 {
-    const double iR = 1.0 / R;
-    double pg = 0.0;
-    if (K.gas_mode == PAB_GAS_POLYTROPIC)
-        pg = gas_pressure(K, bc, R, iR, g);
-    return (K.pv + pg) - fma(K.four_mu, V, K.two_sigma) * iR;
+    const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
+    return fma(-fma(K.fmu_rho, V, K.tsig_rho), rcp64(R), fma(bc.A1, G, K.pv_rho));
 }
 
 // ---------------------------------------------------------------------------
@@ -166,24 +165,38 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc,
 //   y2 = 3/4 y + 1/4 u;  z = 1/2 (y + u)      (z: second order)
 //   y3 = 1/3 y + 2/3 (y2 + h f(y2))           (third order, the one kept)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double p_inf,
+__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
                                          double R, double V, double h, GasBase &g)
 {
-    const double a1 = accel64(K, bc, p_inf, R, V, g);
+    const double a1 = accel64(K, bc, B0, R, V, g);
     const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
-    const double a2 = accel64(K, bc, p_inf, y1R, y1V, g);
+    const double a2 = accel64(K, bc, B0, y1R, y1V, g);
     const double uR = fma(h, y1V, y1R), uV = fma(h, a2, y1V);
     const double zR = 0.5 * (R + uR), zV = 0.5 * (V + uV);
     const double y2R = fma(0.75, R, 0.25 * uR), y2V = fma(0.75, V, 0.25 * uV);
-    const double a3 = accel64(K, bc, p_inf, y2R, y2V, g);
+    const double a3 = accel64(K, bc, B0, y2R, y2V, g);
     const double wR = fma(h, y2V, y2R), wV = fma(h, a3, y2V);
     Trial t;
     t.R = fma(2.0 / 3.0, wR, R * (1.0 / 3.0));
     t.V = fma(2.0 / 3.0, wV, V * (1.0 / 3.0));
-    t.eR = fabs(t.R - zR);
-    t.eV = fabs(t.V - zV);
-    t.ok = (y1R > 0.0) && (y2R > 0.0) && (t.R > 0.0) && (fabs(t.V) <= DBL_MAX);
+    t.eR = t.R - zR;
+    t.eV = t.V - zV;
+    t.ok = gt0(y1R) && gt0(y2R) && gt0(t.R) && finite64(t.V);
     return t;
+}
+
+// The embedded difference 2 k3 - (k1 + k2) of FP32 increments, from exact
+// parts: k1 + k2 = s + e_s and 2 k3 - s = d + e_d by FP32 TwoSum (2 k3 is
+// exact), so the difference is d + (e_d - e_s) exactly.  The three parts are
+// combined in FP64 (e_d - e_s is exact there whenever their exponents differ
+// by less than 29), so the result is the exact difference rounded once to
+// FP64, at two FP64 additions where the direct FP64 form takes three.
+__device__ __forceinline__ double embedded_diff(float k1, float k2, float k3)
+{
+    float s, es, d, ed;
+    two_sum(k1, k2, s, es);
+    two_sum(2.0f * k3, -s, d, ed);
+    return f2d(d) + (f2d(ed) - f2d(es));
 }
 
 // The same trial with the three right-hand sides in FP32 on increments from
@@ -194,9 +207,9 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
 __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc, float A, double R,
                                          double V, double h)
 {
-    const float xi0 = (float)(R - bc.R0);
-    const float v0 = (float)V;
-    const float hf = (float)h;
+    const float xi0 = d2f(R - bc.R0);
+    const float v0 = d2f(V);
+    const float hf = d2f(h);
     const float a1 = accel32(K, bc, A, xi0, v0);
     const float k1R = hf * v0, k1V = hf * a1;
     const float v1 = v0 + k1V;
@@ -209,33 +222,33 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
     const float d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
     const float d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
     Trial t;
-    t.R = R + (double)d3R;
-    t.V = V + (double)d3V;
-    t.eR = fabs(2.0 * (double)k3R - ((double)k1R + (double)k2R)) * (1.0 / 3.0);
-    t.eV = fabs(2.0 * (double)k3V - ((double)k1V + (double)k2V)) * (1.0 / 3.0);
+    t.R = R + f2d(d3R);
+    t.V = V + f2d(d3V);
+    t.eR = embedded_diff(k1R, k2R, k3R) * (1.0 / 3.0);
+    t.eV = embedded_diff(k1V, k2V, k3V) * (1.0 / 3.0);
     const float r1 = bc.R0f + (xi0 + k1R), r2 = bc.R0f + (xi0 + e2R);
-    t.ok = (r1 > 0.0f) && (r2 > 0.0f) && (t.R > 0.0) && (fabs(t.V) <= DBL_MAX)
-        && isfinite(a1 + a2 + a3);
+    t.ok = (r1 > 0.0f) && (r2 > 0.0f) && gt0(t.R) && finite64(t.V) && isfinite(a1 + a2 + a3);
     return t;
 }
 
 // Relative error of a trial: max(|dR|/|R3|, |dRdot|/max(|Rdot3|, v_floor)).
+// Every operand is >= 0; a NaN (only in a trial that failed, whose error is
+// never used) makes the result NaN.
 __device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
 {
-    const double aR = fabs(t.R);
-    const double vs = fmax(fabs(t.V), K.v_floor);
-    return fmax(t.eR * vs, t.eV * aR) / (aR * vs);
+    const double vs = max_nn(abs_nn(t.V), K.v_floor);
+    return max_nn(fabs(t.eR) * vs, fabs(t.eV) * fabs(t.R)) * rcp64(fabs(t.R) * vs);
 }
 
 // Step-size factor clamp(0.9 (tol/err)^(1/3), 0.2, 5); 0.2 after a failed trial.
 // Below err = 1e-30 the clamp gives 5 for any tol >= 1e-18; past FP32 range, 0.2.
 __device__ __forceinline__ double step_factor(const StepConst &K, double err, bool ok)
 {
-    if (!ok || !(err <= 3.0e38))
+    if (!ok || !le(err, 3.0e38))
         return 0.2;
-    if (err <= 1e-30)
+    if (le(err, 1e-30))
         return 5.0;
-    return fmin(fmax(0.9 * K.cbrt_tol * rcbrt_newton(err), 0.2), 5.0);
+    return min_nn(max_nn(0.9 * K.cbrt_tol * rcbrt_newton(err), 0.2), 5.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,8 +267,9 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
                                                      double &V, float &hc, int &n_att, int &n64,
                                                      GasBase &g)
 {
-    double h = (double)hc;
-    if (!(h > 0.0) || h > dt)
+    const double B0 = (K.pv - p_inf) * K.inv_rho;
+    double h = f2d(hc);
+    if (!gt0(h) || !le(h, dt))
         h = dt;
     double t = 0.0;
     uint32_t flags = 0;
@@ -266,29 +280,29 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
             break;
         }
         const double rem = dt - t;
-        const bool last = h >= rem;
+        const bool last = le(rem, h);
         const double ht = last ? rem : h;
         Trial tr;
         if (MIXED) {
             const bool stiff = (R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse);
             if (stiff) {
-                tr = trial64(K, bc, p_inf, R, V, ht, g);
+                tr = trial64(K, bc, B0, R, V, ht, g);
                 ++n64;
             } else {
                 tr = trial32(K, bc, A, R, V, ht);
             }
         } else {
-            tr = trial64(K, bc, p_inf, R, V, ht, g);
+            tr = trial64(K, bc, B0, R, V, ht, g);
         }
         ++n;
         const double err = error_norm(K, tr);
         const double fac = step_factor(K, err, tr.ok);
-        if (tr.ok && err <= K.tol) {
+        if (tr.ok && le(err, K.tol)) {
             R = tr.R;
             V = tr.V;
             if (last) {
-                const bool clipped = rem < h;
-                h = (clipped && fac >= 1.0) ? h : ht * fac;
+                const bool clipped = !le(h, rem);
+                h = (clipped && le(1.0, fac)) ? h : ht * fac;
                 break;
             }
             t += ht;
@@ -297,7 +311,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
             h = ht * fac;
         }
     }
-    hc = (float)h;
+    hc = d2f(h);
     n_att = n;
     return flags;
 }
@@ -320,14 +334,14 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
                                                   double &V, float &hc, int &n_att, int &n64,
                                                   float &xi, float &v)
 {
-    double h = (double)hc;
-    if (!(h > 0.0) || h > dt)
+    double h = f2d(hc);
+    if (!gt0(h) || !le(h, dt))
         h = dt;
     double t = 0.0;
     uint32_t flags = 0;
     int n = 0;
-    xi = (float)(R - bc.R0);
-    v = (float)V;
+    xi = d2f(R - bc.R0);
+    v = d2f(V);
     const float xi_collapse = (K.r_collapsef - 1.0f) * bc.R0f;
     for (;;) {
         if (n >= K.max_attempts) {
@@ -335,7 +349,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             break;
         }
         const double rem = dt - t;
-        const bool last = h >= rem;
+        const bool last = le(rem, h);
         const double ht = last ? rem : h;
         double err, nR = 0.0, nV = 0.0;
         float d3R = 0.0f, d3V = 0.0f;
@@ -343,7 +357,8 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
         if (xi < xi_collapse || fabsf(v) > K.v_collapsef) {
             GasBase g;
             g.reset();
-            const Trial tr = trial64(K, bc, p_inf, R, V, ht, g);
+            const double B0 = (K.pv - p_inf) * K.inv_rho;
+            const Trial tr = trial64(K, bc, B0, R, V, ht, g);
             ++n64;
             err = error_norm(K, tr);
             ok = tr.ok;
@@ -351,7 +366,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             nV = tr.V;
             full64 = true;
         } else {
-            const float hf = (float)ht;
+            const float hf = d2f(ht);
             const float a1 = accel32(K, bc, A, xi, v);
             const float k1R = hf * v, k1V = hf * a1;
             const float v1 = v + k1V;
@@ -363,18 +378,18 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const float k3R = hf * v2, k3V = hf * a3;
             d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
             d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
-            const double eR = fabs(2.0 * (double)k3R - ((double)k1R + (double)k2R));
-            const double eV = fabs(2.0 * (double)k3V - ((double)k1V + (double)k2V));
+            const double eR = embedded_diff(k1R, k2R, k3R);
+            const double eV = embedded_diff(k1V, k2V, k3V);
             const float R3f = bc.R0f + (xi + d3R);
             const float rR = 1.0f / (3.0f * fabsf(R3f));
             const float rV = 1.0f / (3.0f * fmaxf(fabsf(v + d3V), K.v_floorf));
-            err = fmax(eR * (double)rR, eV * (double)rV);
+            err = max_nn(fabs(eR) * f2d(rR), fabs(eV) * f2d(rV));
             ok = (bc.R0f + (xi + k1R) > 0.0f) && (bc.R0f + (xi + e2R) > 0.0f) && (R3f > 0.0f)
               && isfinite(a1 + a2 + a3);
             full64 = false;
         }
         ++n;
-        const float errf = (float)err;
+        const float errf = d2f(err);
         float fac;
         if (!ok || !(errf <= FLT_MAX))
             fac = 0.2f;
@@ -382,28 +397,28 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             fac = 5.0f;
         else
             fac = fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf(errf), 0.2f), 5.0f);
-        if (ok && err <= K.tol) {
+        if (ok && le(err, K.tol)) {
             if (full64) {
                 R = nR;
                 V = nV;
             } else {
-                R += (double)d3R;
-                V += (double)d3V;
+                R += f2d(d3R);
+                V += f2d(d3V);
             }
-            xi = (float)(R - bc.R0);
-            v = (float)V;
+            xi = d2f(R - bc.R0);
+            v = d2f(V);
             if (last) {
-                const bool clipped = rem < h;
-                h = (clipped && fac >= 1.0f) ? h : ht * (double)fac;
+                const bool clipped = !le(h, rem);
+                h = (clipped && fac >= 1.0f) ? h : ht * f2d(fac);
                 break;
             }
             t += ht;
-            h = ht * (double)fac;
+            h = ht * f2d(fac);
         } else {
-            h = ht * (double)fac;
+            h = ht * f2d(fac);
         }
     }
-    hc = (float)h;
+    hc = d2f(h);
     n_att = n;
     return flags;
 }
@@ -415,12 +430,13 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
                                               float A, double dt, double &R, double &V, GasBase &g)
 {
     const double h = dt / (double)K.n_fixed;
+    const double B0 = (K.pv - p_inf) * K.inv_rho;
     for (int i = 0; i < K.n_fixed; ++i) {
         Trial tr;
         if (MIXED && !((R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse)))
             tr = trial32(K, bc, A, R, V, h);
         else
-            tr = trial64(K, bc, p_inf, R, V, h, g);
+            tr = trial64(K, bc, B0, R, V, h, g);
         R = tr.R;
         V = tr.V;
     }
@@ -437,10 +453,10 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 {
     na = 0;
     n64 = 0;
-    if (!p_ok || !isfinite(R) || !isfinite(V))
+    if (!p_ok || !finite64(R) || !finite64(V))
         return PAB_FLAG_NONFINITE;
     uint32_t fl = 0;
-    const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
+    const float A = MIXED ? bc.dpeqf + d2f(K.p0 - p_inf) : 0.0f;
     if (K.n_fixed > 0) {
         advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V, g);
         na = K.n_fixed;
@@ -450,11 +466,11 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
     } else {
         fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64, g);
     }
-    if (!isfinite(R) || !isfinite(V))
+    if (!finite64(R) || !finite64(V))
         fl |= PAB_FLAG_NONFINITE;
-    else if (!(R > 0.0))
+    else if (!gt0(R))
         fl |= PAB_FLAG_NONPOS;
-    if (fabs(V) >= K.c)
+    if (abs_ge(V, K.c))
         fl |= PAB_FLAG_SUPERSONIC;
     return fl;
 }
@@ -469,12 +485,12 @@ __device__ __forceinline__ void quad_terms(const StepConst &K, const BinConst &b
     const double wr3 = wr2 * R;
     double pbw;
     if (MIXED) {
-        const float xi = (float)(R - bc.R0);
+        const float xi = d2f(R - bc.R0);
         const float u = xi * bc.invR0f;
         const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-        pbw = bc.peq + (double)(pgdev + (K.two_sigmaf * u - K.four_muf * (float)V) / (float)R);
+        pbw = K.p0 + f2d(bc.dpeqf + (pgdev + (K.two_sigmaf * u - K.four_muf * d2f(V)) / d2f(R)));
     } else {
-        pbw = wall_pressure64(K, bc, R, V, g);
+        pbw = K.rho * wall_pressure_rho64(K, bc, R, V, g);
     }
     t[0] = wr3;
     t[1] = wr2 * V;

@@ -11,20 +11,25 @@
 
 namespace pab {
 
-// Per-bin constants, computed once in FP64 on the host at create time.
+// Per-bin constants, computed once in FP64 on the host at create time, with
+// pg0 = p0 + 2 sigma/R0 - pv the gas pressure at equilibrium (0 for an empty
+// cavity) and peq = pv + pg0 - 2 sigma/R0 the wall pressure at rest at R0.
+// 56 bytes: 63 of them keep StepConst within the 4 KB of kernel parameters
+// that are read like any other constant.
 struct BinConst {
     double R0;     // equilibrium radius R0_i
     double w;      // quadrature weight w_i (sums to one over the bins)
-    double pg0;    // gas pressure at equilibrium: p0 + 2 sigma/R0 - pv (0 for an empty cavity)
-    double peq;    // pv + pg0 - 2 sigma/R0: the wall pressure at R = R0, Rdot = 0
+    double invR0;  // 1/R0
+    double A1;     // pg0 / rho
+    double A2;     // 3 gamma pg0 / (rho c)
     float R0f;     // R0 in FP32 (mixed path)
     float invR0f;  // 1/R0 in FP32
     float pg0f;    // pg0 in FP32
     float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
-    double invR0;  // 1/R0
 };
 
-constexpr int kGasTerms = 12;  // binomial series of the gas term: degree 11
+constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
+constexpr int kGasTabTerms = 8;  // degree 7 around the nodes of a gas table
 
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
 // so warp-uniform reads come from the constant bank.
@@ -40,6 +45,10 @@ struct StepConst {
     double two_sigma;     // 2 sigma
     double ic_rho;        // (1/c)/rho
     double fmu_ic_rho;    // 4 mu (1/c)/rho
+    double fmu_rho;       // 4 mu / rho
+    double tsig_rho;      // 2 sigma / rho
+    double pv_rho;        // pv / rho
+    double m05_inv_c;     // -0.5 / c
     double tol;
     double cbrt_tol;      // tol^(1/3)
     double v_floor;
@@ -49,19 +58,21 @@ struct StepConst {
     // (1 + d)^(-3 gamma) = sum_k gas_c[k] d^k for |d| <= gas_dmax (truncation below half an ulp)
     double gas_c[kGasTerms];
     double gas_dmax;
-    // optional table of nodes x_j = q^j, j = -gas_J..gas_J, as {x_j, 1/x_j, x_j^(-3 gamma)}:
+    double gas_dmax_tab;  // the same bound for the degree kGasTabTerms-1 of the table path
+    // optional table of nodes x_j = q^j, j = -gas_J..gas_J, as {x_j, 1/x_j, x_j^(-3 gamma), 0}:
     // (R/R0)^(-3 gamma) = T_j (1 + d)^(-3 gamma) with d = (R/R0 - x_j)/x_j (nullptr: no table)
     const double *gas_tab;
-    double gas_inv_log2q;  // 1/log2(q)
+    float gas_inv_log2q;  // 1/log2(q)
     int32_t gas_J;
-    int32_t gas_pad;
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
-    float cbrt_tolf, v_collapsef, r_collapsef, padf;
+    float cbrt_tolf, v_collapsef, r_collapsef, cf;
     BinConst bins[PAB_MAX_BINS];
 };
 
-// Device-side status accumulated over calls until pab_status_flags reads it.
+static_assert(sizeof(BinConst) == 56, "BinConst layout");
 static_assert(sizeof(StepConst) <= 4000, "StepConst must fit the 4 KB kernel-parameter space");
+
+// Device-side status accumulated over calls until pab_status_flags reads it.
 
 struct Counters {
     unsigned int flags_or;
@@ -89,7 +100,7 @@ pab_status validate_config(const pab_config *c, char *msg, size_t n);
 bool bin_table(const pab_config *c, double *R0, double *w);
 void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K);
 BinConst make_bin(const pab_config *c, double R0, double w);  // constants of one radius
-// Host values of the gas-term table for a = 3 gamma (3 * (2 J + 1) doubles) and its spacing.
+// Host values of the gas-term table for a = 3 gamma (4 * (2 J + 1) doubles) and its spacing.
 void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *inv_log2q);
 
 // Launchers (pab_kernels.cu).  Return the launch error.

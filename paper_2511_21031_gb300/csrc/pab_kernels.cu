@@ -22,10 +22,11 @@ constexpr int kTile = 32;
 constexpr int kMaxWarps = 16;
 
 // Running quadrature sums of one lane (one cell).  FP64 mode: plain FP64
-// sums.  MIXED mode: the alpha sum sum w R^3 is FP64 and compensated
-// (Neumaier); sum w R^3 p_bw splits into an FP64 part sum w R^3 p_eq and an
-// FP32 part for the deviation of p_bw from p_eq; sum w R^2 Rdot and
-// sum w R^3 Rdot^2 are FP32 sums of FP32 terms.
+// sums (the pressure sum of w R^3 p_bw/rho).  MIXED mode: the alpha sum
+// sum w R^3 is FP64 and compensated (Neumaier); sum w R^3 p_bw splits into
+// p0 sum w R^3, formed once per cell from the alpha sum, and an FP32 sum of
+// w R^3 (p_bw - p0); sum w R^2 Rdot and sum w R^3 Rdot^2 are FP32 sums of
+// FP32 terms.
 template <bool MIXED>
 struct MomAcc {
     double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
@@ -34,21 +35,16 @@ struct MomAcc {
     __device__ __forceinline__ void add_m3(double x)
     {
         if (MIXED) {
-            const double t = m3 + x;
-            if (fabs(m3) >= fabs(x))
-                m3c += (m3 - t) + x;
-            else
-                m3c += (x - t) + m3;
-            m3 = t;
+            neumaier_add(m3, m3c, x);
         } else {
             m3 += x;
         }
     }
 
     // per-lane totals as doubles
-    __device__ __forceinline__ double M2V() const { return MIXED ? (double)m2vf : m2v; }
-    __device__ __forceinline__ double M3P() const { return MIXED ? m3p + (double)m3pf : m3p; }
-    __device__ __forceinline__ double M3V2() const { return MIXED ? (double)m3v2f : m3v2; }
+    __device__ __forceinline__ double M2V() const { return MIXED ? f2d(m2vf) : m2v; }
+    __device__ __forceinline__ double M3P() const { return MIXED ? f2d(m3pf) : m3p; }
+    __device__ __forceinline__ double M3V2() const { return MIXED ? f2d(m3v2f) : m3v2; }
 };
 
 // FP64 mode (and the reduce-only kernel in both modes): terms from the FP64 state.
@@ -59,23 +55,22 @@ __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &b
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
     if (MIXED) {
-        const float xi = (float)(R - bc.R0);
-        const float Rf = (float)R;
-        const float Vf = (float)V;
+        const float xi = d2f(R - bc.R0);
+        const float Rf = d2f(R);
+        const float Vf = d2f(V);
         const float u = xi * bc.invR0f;
         const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
         const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * Vf) / Rf;
-        const float wr3f = (float)wr3;
+        const float wr3f = d2f(wr3);
         acc.add_m3(wr3);
-        acc.m3p = fma(wr3, bc.peq, acc.m3p);
-        acc.m3pf = fmaf(wr3f, dev, acc.m3pf);
-        acc.m2vf = fmaf((float)wr2, Vf, acc.m2vf);
+        acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
+        acc.m2vf = fmaf(d2f(wr2), Vf, acc.m2vf);
         acc.m3v2f = fmaf(wr3f * Vf, Vf, acc.m3v2f);
     } else {
-        const double pbw = wall_pressure64(K, bc, R, V, g);
+        const double pbw_rho = wall_pressure_rho64(K, bc, R, V, g);
         acc.add_m3(wr3);
         acc.m2v += wr2 * V;
-        acc.m3p += wr3 * pbw;
+        acc.m3p += wr3 * pbw_rho;
         acc.m3v2 += wr3 * V * V;
     }
 }
@@ -90,12 +85,12 @@ __device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinCo
     const float u = xi * bc.invR0f;
     const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
     const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * v) / Rf;
-    const double wr3 = bc.w * R * R * R;
-    const float wr2f = (float)bc.w * Rf * Rf;
-    const float wr3f = wr2f * Rf;
+    const double wr2 = bc.w * R * R;
+    const double wr3 = wr2 * R;
+    const float wr2f = d2f(wr2);
+    const float wr3f = d2f(wr3);
     acc.add_m3(wr3);
-    acc.m3p = fma(wr3, bc.peq, acc.m3p);
-    acc.m3pf = fmaf(wr3f, dev, acc.m3pf);
+    acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
     acc.m2vf = fmaf(wr2f, v, acc.m2vf);
     acc.m3v2f = fmaf(wr3f * v, v, acc.m3v2f);
 }
@@ -121,12 +116,7 @@ __device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAc
         for (int w = 1; w < nw; ++w) {
             const double x = red[0][w][lane];
             if (MIXED) {
-                const double t = m3 + x;
-                if (fabs(m3) >= fabs(x))
-                    m3c += (m3 - t) + x;
-                else
-                    m3c += (x - t) + m3;
-                m3 = t;
+                neumaier_add(m3, m3c, x);
                 m3c += red[1][w][lane];
             } else {
                 m3 += x;
@@ -145,7 +135,7 @@ __device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAc
         out[2 * C + c] = m3;
         out[3 * C + c] = m2v;
         out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
-        out[5 * C + c] = m3p * inv_m3;
+        out[5 * C + c] = MIXED ? fma(m3p, inv_m3, K.p0) : K.rho * m3p * inv_m3;
         out[6 * C + c] = m3v2 * inv_m3;
     }
 }
@@ -199,12 +189,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     const int64_t c = (int64_t)blockIdx.x * kTile + lane;
     const bool valid = c < K.C;
     const double p_inf = valid ? a.p_inf[c] : K.p0;
-    const bool p_ok = isfinite(p_inf);
+    const bool p_ok = finite64(p_inf);
     const double nb = valid ? (a.nb ? a.nb[c] : K.nb_default) : 0.0;
 
     MomAcc<MIXED> acc;
     uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
-    const float dp_cell = MIXED ? (float)(K.p0 - p_inf) : 0.0f;  // p_eq - p_inf = dpeq + dp_cell
+    const float dp_cell = MIXED ? d2f(K.p0 - p_inf) : 0.0f;  // p_eq - p_inf = dpeq + dp_cell
     for (int b = warp; b < K.B; b += nw) {
         if (!valid)
             continue;
@@ -216,7 +206,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         int na = 0;
         GasBase g;
         g.reset();
-        if (!p_ok || !isfinite(R) || !isfinite(V)) {
+        if (!p_ok || !finite64(R) || !finite64(V)) {
             fl = PAB_FLAG_NONFINITE;
         } else if (MIXED && K.n_fixed == 0) {  // (only reachable in the MIXED instantiation)
             const float A = bc.dpeqf + dp_cell;
@@ -231,7 +221,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                 fl |= PAB_FLAG_NONFINITE;
             else if (!(bc.R0f + xi > 0.0f))
                 fl |= PAB_FLAG_NONPOS;
-            if (fabsf(v) >= (float)K.c)
+            if (fabsf(v) >= K.cf)
                 fl |= PAB_FLAG_SUPERSONIC;
             a.R[k] = R;
             a.V[k] = V;
@@ -248,7 +238,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             n_att += na;
             continue;
         } else {
-            const float A = MIXED ? (float)(bc.peq - p_inf) : 0.0f;
+            const float A = MIXED ? bc.dpeqf + dp_cell : 0.0f;
             if (K.n_fixed > 0) {
                 advance_fixed<MIXED>(K, bc, p_inf, A, a.dt, R, V, g);
                 na = K.n_fixed;
@@ -259,11 +249,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                 a.h[k] = hc;
                 n64 += nd;
             }
-            if (!isfinite(R) || !isfinite(V))
+            if (!finite64(R) || !finite64(V))
                 fl |= PAB_FLAG_NONFINITE;
-            else if (!(R > 0.0))
+            else if (!gt0(R))
                 fl |= PAB_FLAG_NONPOS;
-            if (fabs(V) >= K.c)
+            if (abs_ge(V, K.c))
                 fl |= PAB_FLAG_SUPERSONIC;
             a.R[k] = R;
             a.V[k] = V;

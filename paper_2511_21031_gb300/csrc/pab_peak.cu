@@ -1,6 +1,8 @@
 // FMA throughput microbenchmark (measurement aid for the roofline).
 #include <cuda_runtime.h>
 
+#include <cfloat>
+
 #include <vector>
 
 #include "pab_device.cuh"
@@ -32,22 +34,87 @@ __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, cons
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const pab::BinConst &bc = K.bins[0];  // R0 = 1, pg0 = 1
+        const pab::BinConst &bc = K.bins[0];  // R0 = 1
         pab::GasBase g;
         g.reset();
-        (void)pab::gas_pressure(K, bc, Rb[i], 1.0 / Rb[i], g);  // exact at the base
-        gas[i] = pab::gas_pressure(K, bc, R[i], 1.0 / R[i], g);
+        (void)pab::gas_factor(K, bc, Rb[i], g);  // exact at the base
+        gas[i] = pab::gas_factor(K, bc, R[i], g);
         pab::StepConst Kt = K;  // the same constants with the node table attached
         Kt.gas_tab = tab;
         pab::GasBase g2;
         g2.reset();
-        gas_tab[i] = pab::gas_pressure(Kt, Kt.bins[0], R[i], 1.0 / R[i], g2);
+        gas_tab[i] = pab::gas_factor(Kt, Kt.bins[0], R[i], g2);
         exact[i] = exp(K.three_gamma * log(1.0 / R[i]));
         rc[i] = pab::rcbrt_newton(R[i]);
     }
 }
 
+__global__ void bits_check_kernel(long long n, const float *f, const double *x, const double *y,
+                                  double *f2d, double *f2d_hw, double *rcp, double *dv, double *seed,
+                                  uint8_t *cmp)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        f2d[i] = pab::f2d(f[i]);
+        f2d_hw[i] = (double)f[i];
+        const double xi = x[i], yi = y[i];
+        rcp[i] = pab::rcp64(xi);
+        dv[i] = 1.0 / xi;
+        double s0;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(s0) : "d"(xi));
+        seed[i] = s0;
+        const double ax = fabs(xi);
+        uint32_t bad = 0;
+        bad |= (pab::gt0(xi) != (xi > 0.0)) << 0;
+        bad |= (pab::le(xi, yi) != (xi <= yi)) << 1;
+        bad |= (pab::finite64(xi) != (bool)isfinite(xi)) << 2;
+        bad |= (pab::abs_ge(xi, yi) != (ax >= yi)) << 3;
+        if (!isnan(xi)) {  // the max/min helpers take numbers >= +0
+            bad |= (pab::ubits(pab::max_nn(ax, yi)) != pab::ubits(fmax(ax, yi))) << 4;
+            bad |= (pab::ubits(pab::min_nn(ax, yi)) != pab::ubits(fmin(ax, yi))) << 5;
+            // the library flushes subnormal float results to a signed zero
+            float hw = __double2float_rn(xi);
+            if (fabsf(hw) < FLT_MIN)
+                hw = copysignf(0.0f, hw);
+            bad |= (__float_as_uint(pab::d2f(xi)) != __float_as_uint(hw)) << 6;
+        } else {
+            bad |= (!isnan(pab::d2f(xi))) << 6;
+        }
+        // the embedded difference against the same quantity in FP64 (two
+        // roundings there, about one in the library)
+        const float k1 = f[i], k2 = __double2float_rn(xi), k3 = __double2float_rn(yi);
+        if (isfinite(k1) && isfinite(k2) && isfinite(k3) && fabsf(k1) < 1e38f && fabsf(k2) < 1e38f &&
+            fabsf(k3) < 1e38f) {
+            const double ref = 2.0 * (double)k3 - ((double)k1 + (double)k2);
+            const double got = pab::embedded_diff(k1, k2, k3);
+            const double tol = 4.0 * DBL_EPSILON * (fabs(2.0 * (double)k3) + fabs((double)k1) +
+                                                    fabs((double)k2));
+            bad |= (!(fabs(got - ref) <= tol)) << 7;
+        }
+        cmp[i] = (uint8_t)bad;
+    }
+}
+
 }  // namespace
+
+extern "C" pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev,
+                                     const double *y_dev, double *f2d_dev, double *f2d_hw,
+                                     double *rcp_dev, double *div_dev, double *seed_dev,
+                                     uint8_t *cmp_dev, void *stream)
+{
+    if (n < 0 || (n > 0 && (!f_dev || !x_dev || !y_dev || !f2d_dev || !f2d_hw || !rcp_dev ||
+                            !div_dev || !seed_dev || !cmp_dev)))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    bits_check_kernel<<<152 * 4, 256, 0, s>>>(n, f_dev, x_dev, y_dev, f2d_dev, f2d_hw, rcp_dev,
+                                               div_dev, seed_dev, cmp_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
 
 extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
                                      double *gas_dev, double *gas_tab_dev, double *exact_dev,
@@ -71,9 +138,9 @@ extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const doubl
     std::vector<double> tab;
     int J = 0;
     double il2q = 0.0;
-    pab::gas_table(a, K.gas_dmax, &tab, &J, &il2q);
+    pab::gas_table(a, K.gas_dmax_tab, &tab, &J, &il2q);
     K.gas_J = J;
-    K.gas_inv_log2q = il2q;
+    K.gas_inv_log2q = (float)il2q;
     cudaStream_t s = (cudaStream_t)stream;
     double *tab_dev = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&tab_dev, tab.size() * sizeof(double), s);

@@ -28,7 +28,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
-           "pab_stiffened_gas", "pab_math_check")
+           "pab_stiffened_gas", "pab_math_check", "pab_bits_check")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_mixture_pressure": (i32, [vp, vp, vp, vp, vp, vp]),
         "pab_stiffened_gas": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
         "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp, vp]),
+        "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +224,20 @@ def pab_stiffened_gas(rho_l, e_l, gamma_l: float, pi_inf: float, out=None, strea
                                   float(pi_inf), out.data_ptr(), _stream_handle(stream) or None)
     if st != PAB_OK:
         raise PabError(st, "pab_stiffened_gas")
+    return out
+
+
+def pab_bits_check(f, x, y, stream=None):
+    """Library helpers against the hardware: dict of f2d, f2d_hw, rcp, div, seed, cmp."""
+    import torch
+    out = {k: torch.empty_like(x) for k in ("f2d", "f2d_hw", "rcp", "div", "seed")}
+    out["cmp"] = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    st = load().pab_bits_check(x.numel(), f.data_ptr(), x.data_ptr(), y.data_ptr(),
+                               out["f2d"].data_ptr(), out["f2d_hw"].data_ptr(),
+                               out["rcp"].data_ptr(), out["div"].data_ptr(), out["seed"].data_ptr(),
+                               out["cmp"].data_ptr(), _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_bits_check")
     return out
 
 
