@@ -79,6 +79,28 @@ class Params:
                        int(self.gas_mode), int(self.max_attempts), self.tol, vf)
 
 
+class _Transfer(ctypes.Structure):
+    _fields_ = [("R_g", ctypes.c_double), ("R_v", ctypes.c_double), ("T_w", ctypes.c_double),
+                ("k_bw", ctypes.c_double), ("D", ctypes.c_double), ("beta_T", ctypes.c_double),
+                ("beta_c", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class Transfer:
+    """Gas/vapour contents with constant wall transfer coefficients (SI units).
+    Defaults: air and water vapour at 20 C; beta_T and beta_c are inputs."""
+    R_g: float = 287.05
+    R_v: float = 461.5
+    T_w: float = 293.15
+    k_bw: float = 0.0257
+    D: float = 2.42e-5
+    beta_T: float = 5.0
+    beta_c: float = 5.0
+
+    def as_c(self) -> _Transfer:
+        return _Transfer(self.R_g, self.R_v, self.T_w, self.k_bw, self.D, self.beta_T, self.beta_c)
+
+
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -132,6 +154,22 @@ def _lib():
             lib.orc_el_smear.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _dp, _dp]
             lib.orc_el_smear.restype = None
+            T = ctypes.POINTER(_Transfer)
+            lib.orc_transfer_gas_mass.argtypes = [P, T, ctypes.c_double]
+            lib.orc_transfer_gas_mass.restype = ctypes.c_double
+            lib.orc_transfer_init.argtypes = [P, T, ctypes.c_double, _dp]
+            lib.orc_transfer_init.restype = None
+            lib.orc_transfer_rates.argtypes = [P, T, ctypes.c_double, _dp, _dp, _dp]
+            lib.orc_transfer_rates.restype = None
+            lib.orc_transfer_rhs.argtypes = [P, T, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            lib.orc_transfer_rhs.restype = None
+            lib.orc_transfer_step.argtypes = [P, T, ctypes.c_int64, ctypes.c_int32, _dp, _dp,
+                                              ctypes.c_double, ctypes.c_int32, _dp, _dp, _dp, _dp,
+                                              _fp, _u32p, _i32p]
+            lib.orc_transfer_step.restype = None
+            lib.orc_transfer_moments.argtypes = [P, ctypes.c_int64, ctypes.c_int32, _dp, _dp, _dp,
+                                                 _dp, _dp, _dp]
+            lib.orc_transfer_moments.restype = None
             _LIB = lib
     return _LIB
 
@@ -316,3 +354,75 @@ def el_smear(pos, R, Rdot, nx, ny, nz, dx, with_rate=True):
                         _ptr(Rdot, _dp), int(nx), int(ny), int(nz), float(dx), _ptr(alpha, _dp),
                         _ptr(adot, _dp) if adot is not None else None)
     return (alpha, adot) if with_rate else alpha
+
+
+# ---------------------------------------------------------------------------
+# Non-polytropic contents: state (R, Rdot, p_b, m_v) per bin.
+# ---------------------------------------------------------------------------
+def transfer_gas_mass(params: Params, tr: Transfer, R0: float) -> float:
+    """Non-condensable gas mass of a bubble in equilibrium at R0."""
+    cp, ct = params.as_c(), tr.as_c()
+    return float(_lib().orc_transfer_gas_mass(ctypes.byref(cp), ctypes.byref(ct), float(R0)))
+
+
+def transfer_init(params: Params, tr: Transfer, R0: float):
+    """Equilibrium state (R, Rdot, p_b, m_v) of bin R0."""
+    y = np.zeros(4)
+    cp, ct = params.as_c(), tr.as_c()
+    _lib().orc_transfer_init(ctypes.byref(cp), ctypes.byref(ct), float(R0), _ptr(y, _dp))
+    return y
+
+
+def transfer_rates(params: Params, tr: Transfer, m_g: float, y):
+    """(dp_b/dt, dm_v/dt) at state y = (R, Rdot, p_b, m_v)."""
+    y = _f64(y)
+    a = np.zeros(1)
+    b = np.zeros(1)
+    cp, ct = params.as_c(), tr.as_c()
+    _lib().orc_transfer_rates(ctypes.byref(cp), ctypes.byref(ct), float(m_g), _ptr(y, _dp),
+                              _ptr(a, _dp), _ptr(b, _dp))
+    return float(a[0]), float(b[0])
+
+
+def transfer_rhs(params: Params, tr: Transfer, m_g: float, p_inf: float, y):
+    """Right-hand side (f[4], p_bw) of the four-component system at y."""
+    y = _f64(y)
+    f = np.zeros(4)
+    pbw = np.zeros(1)
+    cp, ct = params.as_c(), tr.as_c()
+    _lib().orc_transfer_rhs(ctypes.byref(cp), ctypes.byref(ct), float(m_g), float(p_inf),
+                            _ptr(y, _dp), _ptr(f, _dp), _ptr(pbw, _dp))
+    return f, float(pbw[0])
+
+
+def transfer_step(params: Params, tr: Transfer, R0, p_inf, dt, R, Rdot, pb, mv, h, n_fixed: int = 0):
+    """Advance [B][C] state (R, Rdot, p_b, m_v f64; h f32) in place; returns (flags, attempts)."""
+    R0 = _f64(R0)
+    p_inf = _f64(p_inf)
+    B = R0.shape[0]
+    C = p_inf.shape[0]
+    for a, dt_ in ((R, np.float64), (Rdot, np.float64), (pb, np.float64), (mv, np.float64),
+                   (h, np.float32)):
+        if a.dtype != dt_ or not a.flags.c_contiguous or a.size != B * C:
+            raise ValueError("state arrays must be contiguous [B][C]")
+    flags = np.zeros((B, C), dtype=np.uint32)
+    attempts = np.zeros((B, C), dtype=np.int32)
+    cp, ct = params.as_c(), tr.as_c()
+    _lib().orc_transfer_step(ctypes.byref(cp), ctypes.byref(ct), C, B, _ptr(R0, _dp), _ptr(p_inf, _dp),
+                             float(dt), int(n_fixed), _ptr(R, _dp), _ptr(Rdot, _dp), _ptr(pb, _dp),
+                             _ptr(mv, _dp), _ptr(h, _fp), _ptr(flags, _u32p), _ptr(attempts, _i32p))
+    return flags, attempts
+
+
+def transfer_moments(params: Params, w, n_b, R, Rdot, pb):
+    """[7][C] moments with p_bw from the state p_b (rows as moments())."""
+    w = _f64(w)
+    n_b = _f64(n_b)
+    R, Rdot, pb = _f64(R), _f64(Rdot), _f64(pb)
+    B = w.shape[0]
+    C = n_b.shape[0]
+    out = np.zeros((7, C))
+    cp = params.as_c()
+    _lib().orc_transfer_moments(ctypes.byref(cp), C, B, _ptr(w, _dp), _ptr(n_b, _dp), _ptr(R, _dp),
+                                _ptr(Rdot, _dp), _ptr(pb, _dp), _ptr(out, _dp))
+    return out

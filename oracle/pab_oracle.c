@@ -587,3 +587,257 @@ void orc_el_smear(int64_t N, const double *x, const double *y, const double *z, 
                 }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Non-polytropic bubble contents (Sec. 2): gas and vapour with heat and     */
+/* mass transfer at the wall, reduced-order form with constant transfer      */
+/* coefficients.                                                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * The bubble holds a fixed mass m_g of non-condensable gas (gas constant R_g)
+ * and a vapour mass m_v (gas constant R_v); its pressure p_b is a state. The
+ * state per bin is y = (R, Rdot, p_b, m_v). The paper fixes:
+ *   - Eq. (keller_miksis) with p_bw = p_b - 4 mu Rdot/R - 2 sigma/R;
+ *   - Eq. (massVaporRate): mdot_v = D rho_bw / (1 - chi_vw) dchi_v/dr|_R;
+ *   - Ando's pressure equation:
+ *       dp_b/dt = (3 gamma_b / R) (-Rdot p_b + R_v T_bw mdot_v
+ *                                  + (gamma_b - 1)/gamma_b k_bw dT/dr|_R).
+ * Readings of what the paper leaves to the cited reduced-order model:
+ *   - the wall gradients are constant coefficients times the difference
+ *     between wall and bubble mean over R:
+ *       dchi_v/dr|_R = beta_c (chi_vw - chi_mean) / R,
+ *       dT/dr|_R     = beta_T (T_w - T_mean) / R;
+ *   - the wall stays at the liquid temperature T_w (T_bw = T_w) and the vapour
+ *     there is saturated at p_v (the handle's vapour pressure);
+ *   - T_mean from the ideal-gas mixture: p_b V = (m_g R_g + m_v R_v) T_mean,
+ *     V = 4/3 pi R^3; chi_mean = m_v / (m_v + m_g);
+ *   - wall vapour mass fraction and density from the partial pressures p_v and
+ *     p_b - p_v at T_w: chi_vw = (p_v/R_v) / (p_v/R_v + (p_b - p_v)/R_g),
+ *     rho_bw = (p_v/R_v + (p_b - p_v)/R_g) / T_w;
+ *   - mdot_v is a flux per unit wall area: dm_v/dt = 4 pi R^2 mdot_v;
+ *   - gamma_b is the handle's gamma; m_g follows from equilibrium at R0:
+ *     m_g = (p0 + 2 sigma/R0 - p_v) (4/3 pi R0^3) / (R_g T_w);
+ *   - the error norm stays the one of R and Rdot (Sec. 3 names those two).
+ * With beta_T = beta_c = 0 the pressure equation reduces to
+ * dp_b/dt = -3 gamma_b Rdot p_b / R, whose solution is the polytropic law.
+ */
+typedef struct {
+    double R_g, R_v;     /* gas constants of the gas and of the vapour */
+    double T_w;          /* wall (liquid) temperature */
+    double k_bw;         /* thermal conductivity of the contents at the wall */
+    double D;            /* binary diffusion coefficient of vapour in gas */
+    double beta_T;       /* heat transfer coefficient (dimensionless) */
+    double beta_c;       /* mass transfer coefficient (dimensionless) */
+} orc_transfer;
+
+/* Gas mass of a bubble of equilibrium radius R0. */
+double orc_transfer_gas_mass(const orc_params *P, const orc_transfer *T, double R0)
+{
+    double V0 = 4.0 / 3.0 * M_PI * R0 * R0 * R0;
+    return (P->p0 + 2.0 * P->sigma / R0 - P->pv) * V0 / (T->R_g * T->T_w);
+}
+
+/* Equilibrium state of bin R0: R = R0, Rdot = 0, p_b = p0 + 2 sigma/R0,
+ * m_v = p_v V0 / (R_v T_w) (saturated vapour at the wall temperature). */
+void orc_transfer_init(const orc_params *P, const orc_transfer *T, double R0, double y[4])
+{
+    double V0 = 4.0 / 3.0 * M_PI * R0 * R0 * R0;
+    y[0] = R0;
+    y[1] = 0.0;
+    y[2] = P->p0 + 2.0 * P->sigma / R0;
+    y[3] = P->pv * V0 / (T->R_v * T->T_w);
+}
+
+/* dp_b/dt and dm_v/dt at (R, Rdot, p_b, m_v) for the gas mass m_g. */
+void orc_transfer_rates(const orc_params *P, const orc_transfer *T, double m_g,
+                        const double y[4], double *dpb, double *dmv)
+{
+    double R = y[0], Rdot = y[1], p_b = y[2], m_v = y[3];
+    double V = 4.0 / 3.0 * M_PI * R * R * R;
+    double T_mean = p_b * V / (m_g * T->R_g + m_v * T->R_v);
+    double chi_mean = m_v / (m_v + m_g);
+    double rho_v_w = P->pv / (T->R_v * T->T_w);
+    double rho_g_w = (p_b - P->pv) / (T->R_g * T->T_w);
+    double rho_bw = rho_v_w + rho_g_w;
+    double chi_vw = rho_v_w / rho_bw;
+    double dchi_dr = T->beta_c * (chi_vw - chi_mean) / R;
+    double dT_dr = T->beta_T * (T->T_w - T_mean) / R;
+    double mdot_v = T->D * rho_bw / (1.0 - chi_vw) * dchi_dr;
+    double gb = P->gamma;
+    *dpb = 3.0 * gb / R * (-Rdot * p_b + T->R_v * T->T_w * mdot_v + (gb - 1.0) / gb * T->k_bw * dT_dr);
+    *dmv = 4.0 * M_PI * R * R * mdot_v;
+}
+
+/* Keller-Miksis (Eq. keller_miksis) with the bubble pressure as a state: the
+ * wall-pressure rate dp_bw/dt = dp_b/dt + 4 mu Rdot^2/R^2 + 2 sigma Rdot/R^2
+ * - 4 mu Rddot/R, whose Rddot term moves to the left-hand side. */
+void orc_transfer_rhs(const orc_params *P, const orc_transfer *T, double m_g, double p_inf,
+                      const double y[4], double f[4], double *pbw_out)
+{
+    double R = y[0], Rdot = y[1], p_b = y[2];
+    double inv_c = 1.0 / P->c;
+    double dpb, dmv;
+    orc_transfer_rates(P, T, m_g, y, &dpb, &dmv);
+    double p_bw = p_b - 4.0 * P->mu * Rdot / R - 2.0 * P->sigma / R;
+    double dp_bw_explicit = dpb + 4.0 * P->mu * Rdot * Rdot / (R * R)
+                          + 2.0 * P->sigma * Rdot / (R * R);
+    double rhs = (p_bw - p_inf) / P->rho * (1.0 + Rdot * inv_c)
+               + R * inv_c / P->rho * dp_bw_explicit
+               - 1.5 * Rdot * Rdot * (1.0 - Rdot * inv_c / 3.0);
+    double lhs_coef = R * (1.0 - Rdot * inv_c) + 4.0 * P->mu * inv_c / P->rho;
+    f[0] = Rdot;
+    f[1] = rhs / lhs_coef;
+    f[2] = dpb;
+    f[3] = dmv;
+    if (pbw_out)
+        *pbw_out = p_bw;
+}
+
+/* The SSP-RK3 trial with the embedded Heun member (as orc_ssprk3_trial), on
+ * the four components. */
+static void transfer_trial(const orc_params *P, const orc_transfer *T, double m_g, double p_inf,
+                           const double y[4], double h, double y3[4], double z[4],
+                           double stage_R[2])
+{
+    double f[4], y1[4], y2[4];
+    orc_transfer_rhs(P, T, m_g, p_inf, y, f, NULL);
+    for (int k = 0; k < 4; ++k)
+        y1[k] = y[k] + h * f[k];
+    orc_transfer_rhs(P, T, m_g, p_inf, y1, f, NULL);
+    for (int k = 0; k < 4; ++k) {
+        z[k] = 0.5 * y[k] + 0.5 * (y1[k] + h * f[k]);
+        y2[k] = 0.75 * y[k] + 0.25 * (y1[k] + h * f[k]);
+    }
+    orc_transfer_rhs(P, T, m_g, p_inf, y2, f, NULL);
+    for (int k = 0; k < 4; ++k)
+        y3[k] = y[k] / 3.0 + 2.0 / 3.0 * (y2[k] + h * f[k]);
+    stage_R[0] = y1[0];
+    stage_R[1] = y2[0];
+}
+
+/* The adaptive controller of advance_adaptive on the four components (the
+ * error norm reads R and Rdot only). */
+static uint32_t transfer_advance(const orc_params *P, const orc_transfer *T, double m_g,
+                                 double p_inf, double y[4], float *h_carry, double dt,
+                                 int32_t n_fixed, int32_t *n_attempts)
+{
+    double y3[4], z[4], stage_R[2];
+    if (n_fixed > 0) {
+        double hf = dt / (double)n_fixed;
+        for (int32_t i = 0; i < n_fixed; ++i) {
+            transfer_trial(P, T, m_g, p_inf, y, hf, y3, z, stage_R);
+            for (int k = 0; k < 4; ++k)
+                y[k] = y3[k];
+        }
+        *n_attempts = n_fixed;
+        return 0;
+    }
+    double h = (double)(*h_carry);
+    if (!(h > 0.0) || isinf(h) || h > dt)
+        h = dt;
+    double t = 0.0;
+    int32_t attempts = 0;
+    uint32_t flags = 0;
+    for (;;) {
+        if (attempts >= P->max_attempts) {
+            flags |= ORC_FLAG_STEP_LIMIT;
+            break;
+        }
+        double remaining = dt - t;
+        int last = (h >= remaining);
+        double h_try = last ? remaining : h;
+        transfer_trial(P, T, m_g, p_inf, y, h_try, y3, z, stage_R);
+        ++attempts;
+        double err = orc_error_norm(y3, z, P->v_floor);
+        int positive = stage_R[0] > 0.0 && stage_R[1] > 0.0 && y3[0] > 0.0;
+        double fac = orc_step_factor(err, P->tol);
+        if (err <= P->tol && positive) {
+            for (int k = 0; k < 4; ++k)
+                y[k] = y3[k];
+            if (last) {
+                int clipped = remaining < h;
+                h = (clipped && fac >= 1.0) ? h : h_try * fac;
+                break;
+            }
+            t += h_try;
+            h = h_try * fac;
+        } else {
+            if (!positive && fac > 0.2)
+                fac = 0.2;
+            h = h_try * fac;
+        }
+    }
+    *h_carry = (float)h;
+    *n_attempts = attempts;
+    return flags;
+}
+
+/* orc_step for the transfer model: the state adds p_b and m_v ([B][C] each). */
+void orc_transfer_step(const orc_params *P, const orc_transfer *T, int64_t C, int32_t B,
+                       const double *R0, const double *p_inf, double dt, int32_t n_fixed,
+                       double *R, double *Rdot, double *pb, double *mv, float *h,
+                       uint32_t *flags, int32_t *attempts)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < C; ++c) {
+        for (int32_t b = 0; b < B; ++b) {
+            size_t k = (size_t)b * (size_t)C + (size_t)c;
+            uint32_t fl = 0;
+            int32_t na = 0;
+            double y[4] = {R[k], Rdot[k], pb[k], mv[k]};
+            int finite = isfinite(p_inf[c]);
+            for (int i = 0; i < 4; ++i)
+                finite = finite && isfinite(y[i]);
+            if (!finite) {
+                fl |= ORC_FLAG_NONFINITE;
+            } else {
+                double m_g = orc_transfer_gas_mass(P, T, R0[b]);
+                fl |= transfer_advance(P, T, m_g, p_inf[c], y, &h[k], dt, n_fixed, &na);
+                if (!isfinite(y[0]) || !isfinite(y[1]) || !isfinite(y[2]) || !isfinite(y[3]))
+                    fl |= ORC_FLAG_NONFINITE;
+                else if (!(y[0] > 0.0))
+                    fl |= ORC_FLAG_NONPOS;
+                if (fabs(y[1]) >= P->c)
+                    fl |= ORC_FLAG_SUPERSONIC;
+                R[k] = y[0];
+                Rdot[k] = y[1];
+                pb[k] = y[2];
+                mv[k] = y[3];
+            }
+            if (flags)
+                flags[k] = fl;
+            if (attempts)
+                attempts[k] = na;
+        }
+    }
+}
+
+/* orc_moments with p_bw = p_b - 4 mu Rdot/R - 2 sigma/R from the state p_b. */
+void orc_transfer_moments(const orc_params *P, int64_t C, int32_t B, const double *w,
+                          const double *n_b, const double *R, const double *Rdot,
+                          const double *pb, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < C; ++c) {
+        double M3 = 0.0, M2V = 0.0, M3P = 0.0, M3V2 = 0.0;
+        for (int32_t b = 0; b < B; ++b) {
+            size_t k = (size_t)b * (size_t)C + (size_t)c;
+            double r = R[k];
+            double v = Rdot[k];
+            double p_bw = pb[k] - 4.0 * P->mu * v / r - 2.0 * P->sigma / r;
+            double r3 = r * r * r;
+            M3 += w[b] * r3;
+            M2V += w[b] * r * r * v;
+            M3P += w[b] * r3 * p_bw;
+            M3V2 += w[b] * r3 * v * v;
+        }
+        double alpha = 4.0 / 3.0 * M_PI * n_b[c] * M3;
+        out[0 * C + c] = n_b[c];
+        out[1 * C + c] = alpha;
+        out[2 * C + c] = M3;
+        out[3 * C + c] = M2V;
+        out[4 * C + c] = 3.0 * alpha * M2V / M3;
+        out[5 * C + c] = M3P / M3;
+        out[6 * C + c] = M3V2 / M3;
+    }
+}
