@@ -1,8 +1,10 @@
 """The pins catch planted mistakes: each case compiles a copy of the oracle
 with one plausible slip (a dropped term, a wrong sign, coefficient or index)
-and requires tests/test_oracle_pins.py (without its golden regression
-fixture, which only guards drift) to fail against it.  The mistakes live
-only in temporary copies; the oracle itself is untouched."""
+and requires the pins of that part of the oracle (tests/test_oracle_pins.py
+without its golden regression fixture, which only guards drift, or
+tests/test_oracle_transfer.py for the non-polytropic contents) to fail
+against it.  The mistakes live only in temporary copies; the oracle itself is
+untouched."""
 import os
 import subprocess
 import sys
@@ -45,18 +47,54 @@ MUTATIONS = [
      "p_l[i] = (gamma_l - 1.0) * rho_l[i] * e_l[i] - pi_inf;"),
 ]
 
+# Mistakes in the non-polytropic contents, caught by tests/test_oracle_transfer.py.
+TRANSFER_MUTATIONS = [
+    ("heat term without (gamma-1)/gamma", "(gb - 1.0) / gb * T->k_bw * dT_dr", "T->k_bw * dT_dr"),
+    ("vapour enthalpy with the gas constant of the gas", "T->R_v * T->T_w * mdot_v", "T->R_g * T->T_w * mdot_v"),
+    ("vapour mass rate without the wall area", "*dmv = 4.0 * M_PI * R * R * mdot_v;", "*dmv = 4.0 * M_PI * R * mdot_v;"),
+    ("mean temperature with one gas constant", "(m_g * T->R_g + m_v * T->R_v)", "((m_g + m_v) * T->R_g)"),
+    ("sign of the compression term", "(-Rdot * p_b +", "(Rdot * p_b +"),
+    ("wall temperature gradient reversed", "(T->T_w - T_mean) / R", "(T_mean - T->T_w) / R"),
+    ("wall vapour fraction of the gas", "double chi_vw = rho_v_w / rho_bw;", "double chi_vw = rho_g_w / rho_bw;"),
+    ("last stage weights of the four-component trial", "y3[k] = y[k] / 3.0 + 2.0 / 3.0 * (y2[k] + h * f[k]);",
+     "y3[k] = y[k] / 2.0 + 1.0 / 2.0 * (y2[k] + h * f[k]);"),
+    ("transfer moments without surface tension", "double p_bw = pb[k] - 4.0 * P->mu * v / r - 2.0 * P->sigma / r;",
+     "double p_bw = pb[k] - 4.0 * P->mu * v / r;"),
+]
 
-@pytest.mark.parametrize("name,orig,mutant", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(name, orig, mutant, tmp_path):
-    src = open(SRC).read()
-    assert src.count(orig) == 1, f"mutation anchor not unique: {orig}"
+# The non-polytropic section repeats some of the polytropic text; each mutation
+# is placed in its own part of the file.
+MARK = "/* Non-polytropic bubble contents"
+
+
+def _run_mutant(name, head, tail, pins, tmp_path):
     msrc = tmp_path / "mutant.c"
-    msrc.write_text(src.replace(orig, mutant))
+    msrc.write_text(head + tail)
     lib = oracle.compile_to(str(msrc), str(tmp_path / "libmutant.so"))
     env = dict(os.environ, PAB_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins),
                         "-x", "-q", "-p", "no:cacheprovider", "-k", "not golden_regression"],
                        cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout
+
+
+def _parts():
+    src = open(SRC).read()
+    i = src.index(MARK)
+    return src[:i], src[i:]
+
+
+@pytest.mark.parametrize("name,orig,mutant", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, orig, mutant, tmp_path):
+    head, tail = _parts()
+    assert head.count(orig) == 1, f"mutation anchor not unique: {orig}"
+    _run_mutant(name, head.replace(orig, mutant), tail, "test_oracle_pins.py", tmp_path)
+
+
+@pytest.mark.parametrize("name,orig,mutant", TRANSFER_MUTATIONS, ids=[m[0] for m in TRANSFER_MUTATIONS])
+def test_transfer_pins_catch_planted_mistake(name, orig, mutant, tmp_path):
+    head, tail = _parts()
+    assert tail.count(orig) == 1, f"mutation anchor not unique: {orig}"
+    _run_mutant(name, head, tail.replace(orig, mutant), "test_oracle_transfer.py", tmp_path)
