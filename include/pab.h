@@ -60,7 +60,7 @@ enum { PAB_FP64 = 0, PAB_MIXED = 1 };
 /* stepper */
 enum { PAB_ADAPTIVE = 0, PAB_FIXED = 1 };
 /* gas_mode */
-enum { PAB_GAS_POLYTROPIC = 0, PAB_GAS_EMPTY = 1 };
+enum { PAB_GAS_POLYTROPIC = 0, PAB_GAS_EMPTY = 1, PAB_GAS_TRANSFER = 2 };
 
 /* Per-bin status bits (OR-ed into the handle's status word). */
 #define PAB_FLAG_STEP_LIMIT 1u   /* attempts exhausted; the bin keeps its last accepted state */
@@ -80,7 +80,9 @@ typedef struct {
     int64_t n_cells;        /* C >= 1 */
     int32_t n_bins;         /* Nb: 1, or odd 3..PAB_MAX_BINS (Simpson needs odd Nb) */
     int32_t gas_mode;       /* PAB_GAS_POLYTROPIC: p_b = pv + p_g0 (R0/R)^(3 gamma),
-                               p_g0 = p0 + 2 sigma/R0 - pv; PAB_GAS_EMPTY: p_b = pv */
+                               p_g0 = p0 + 2 sigma/R0 - pv; PAB_GAS_EMPTY: p_b = pv;
+                               PAB_GAS_TRANSFER: p_b and the vapour mass are states with
+                               heat and mass transfer at the wall (pab_transfer.h) */
     double rho, c, mu, sigma, p0, gamma, pv;   /* c = INFINITY: incompressible (RP) limit */
     double R0ref;           /* median equilibrium radius of the lognormal */
     double s_lognormal;     /* shape s of the lognormal (> 0 when Nb > 1) */
@@ -97,6 +99,12 @@ typedef struct {
     double Rdot0_ref;       /* initial Rdot_i = Rdot0_ref * R0_i / R0ref (0: rest) */
     int32_t record_attempts;/* non-zero: keep per-bin trial counts of the last call */
     int32_t block_warps;    /* warps per CTA (0: default); cells per CTA is 32 */
+    /* Contents with heat and mass transfer (gas_mode PAB_GAS_TRANSFER; FP64 only;
+     * pab_transfer.h): gas constants of the gas and of the vapour, wall (liquid)
+     * temperature, thermal conductivity of the contents, vapour-gas diffusion
+     * coefficient, and the constant heat and mass transfer coefficients.
+     * Defaults: air and water vapour at 20 C, beta_T = beta_c = 5. */
+    double R_g, R_v, T_w, k_bw, D_vg, beta_T, beta_c;
 } pab_config;
 
 /* Fill *cfg with the defaults above (n_cells = 1, n_bins = 21). */

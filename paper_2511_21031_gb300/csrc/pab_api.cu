@@ -12,6 +12,7 @@
 #include <new>
 
 #include "pab.h"
+#include "pab_transfer.h"
 #include "pab_closure.h"
 #include "pab_internal.h"
 
@@ -25,6 +26,8 @@ struct pab_s {
     float *h = nullptr;
     int32_t *attempts = nullptr;
     double *gas_tab = nullptr;  // gas-term nodes (K.gas_tab points here)
+    double *pb = nullptr;       // [Nb][C] bubble pressure (PAB_GAS_TRANSFER)
+    double *mv = nullptr;       // [Nb][C] vapour mass (PAB_GAS_TRANSFER)
     pab::Counters *counters = nullptr;
     pab::Counters *counters_host = nullptr;  // pinned
     double *stage_p = nullptr;                // host entry point staging [C]
@@ -98,8 +101,21 @@ pab_status validate(const pab_config *c, char *msg, size_t n)
     if (!finite_pos(c->rho) || !(c->c > 0.0) || !(c->mu >= 0.0) || !(c->sigma >= 0.0) ||
         !finite_pos(c->p0) || !finite_pos(c->gamma) || !(c->pv >= 0.0) || !std::isfinite(c->pv))
         BAD("fluid constants out of range");
-    if (c->gas_mode != PAB_GAS_POLYTROPIC && c->gas_mode != PAB_GAS_EMPTY)
-        BAD("gas_mode must be 0 or 1");
+    if (c->gas_mode != PAB_GAS_POLYTROPIC && c->gas_mode != PAB_GAS_EMPTY &&
+        c->gas_mode != PAB_GAS_TRANSFER)
+        BAD("gas_mode must be 0, 1 or 2");
+    if (c->gas_mode == PAB_GAS_TRANSFER) {
+        if (c->precision != PAB_FP64)
+            BAD("gas_mode PAB_GAS_TRANSFER runs in PAB_FP64 only");
+        if (!(c->pv < c->p0))
+            BAD("gas_mode PAB_GAS_TRANSFER needs pv < p0 (a positive gas partial pressure)");
+        if (!finite_pos(c->R_g) || !finite_pos(c->R_v) || !finite_pos(c->T_w))
+            BAD("R_g, R_v and T_w must be positive");
+        const double nn[] = {c->k_bw, c->D_vg, c->beta_T, c->beta_c};
+        for (double x : nn)
+            if (!(x >= 0.0) || !std::isfinite(x))
+                BAD("k_bw, D_vg, beta_T and beta_c must be finite and >= 0");
+    }
     if (c->precision != PAB_FP64 && c->precision != PAB_MIXED)
         BAD("precision must be PAB_FP64 or PAB_MIXED");
     if (c->stepper != PAB_ADAPTIVE && c->stepper != PAB_FIXED)
@@ -173,6 +189,14 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->v_collapsef = (float)K->v_collapse;
     K->r_collapsef = (float)K->r_collapse;
     K->cf = (float)c->c;
+    K->tr_Rg = c->R_g;
+    K->tr_Rv = c->R_v;
+    K->tr_Tw = c->T_w;
+    K->tr_RvTw = c->R_v * c->T_w;
+    K->tr_rho_vw = c->gas_mode == PAB_GAS_TRANSFER ? c->pv / (c->R_v * c->T_w) : 0.0;
+    K->tr_inv_RgTw = c->gas_mode == PAB_GAS_TRANSFER ? 1.0 / (c->R_g * c->T_w) : 0.0;
+    K->tr_kT = (c->gamma - 1.0) / c->gamma * c->k_bw * c->beta_T;
+    K->tr_Dc = c->D_vg * c->beta_c;
     double m3 = 0.0;
     for (int i = 0; i < c->n_bins; ++i) {
         pab::BinConst &b = K->bins[i];
@@ -292,6 +316,13 @@ void pab_config_default(pab_config *c)
     c->v_floor = -1.0;
     c->alpha0 = 4e-5;
     c->Rdot0_ref = 0.0;
+    c->R_g = 287.05;
+    c->R_v = 461.5;
+    c->T_w = 293.15;
+    c->k_bw = 0.0257;
+    c->D_vg = 2.42e-5;
+    c->beta_T = 5.0;
+    c->beta_c = 5.0;
     c->record_attempts = 0;
     c->block_warps = 0;
 }
@@ -385,6 +416,13 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
         e = cudaMemsetAsync(h->attempts, 0, n * sizeof(int32_t), s);
     if (e == cudaSuccess)
         e = pab::launch_init(h->K, cfg->Rdot0_ref, cfg->R0ref, h->R, h->V, h->h, s);
+    if (e == cudaSuccess && cfg->gas_mode == PAB_GAS_TRANSFER) {
+        e = cudaMallocAsync((void **)&h->pb, n * sizeof(double), s);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void **)&h->mv, n * sizeof(double), s);
+        if (e == cudaSuccess)
+            e = pab::launch_transfer_init(h->K, h->pb, h->mv, s);
+    }
     if (e != cudaSuccess) {
         pab_status st = e == cudaErrorMemoryAllocation ? PAB_ENOMEM : PAB_ECUDA;
         fprintf(stderr, "pab_create: %s\n", cudaGetErrorString(e));
@@ -405,8 +443,8 @@ void pab_destroy(pab_t *h)
     cudaGetDevice(&cur);
     if (cur != h->device)
         cudaSetDevice(h->device);
-    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->gas_tab, h->counters, h->stage_p, h->stage_nb,
-                    h->stage_out};
+    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
+                    h->stage_nb, h->stage_out};
     for (void *b : bufs)
         if (b)
             cudaFreeAsync(b, s);
@@ -437,7 +475,11 @@ pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_d
     a.attempts = h->attempts;
     a.out = moments_dev;
     a.counters = h->counters;
-    cudaError_t e = pab::launch_step(h->K, h->cfg.precision, a, h->block_warps, (cudaStream_t)stream);
+    a.pb = h->pb;
+    a.mv = h->mv;
+    cudaError_t e = h->cfg.gas_mode == PAB_GAS_TRANSFER
+                        ? pab::launch_transfer_step(h->K, a, h->block_warps, (cudaStream_t)stream)
+                        : pab::launch_step(h->K, h->cfg.precision, a, h->block_warps, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(h, e, "pab_bubble_step launch");
     return PAB_OK;
@@ -449,8 +491,11 @@ pab_status pab_moments(pab_t *h, const double *nb_dev, double *moments_dev, void
         return PAB_EINVAL;
     if (!moments_dev)
         return fail(h, PAB_EINVAL, "pab_moments: moments_dev is NULL");
-    cudaError_t e = pab::launch_moments(h->K, h->cfg.precision, nb_dev, h->R, h->V, moments_dev,
-                                        h->block_warps, (cudaStream_t)stream);
+    cudaError_t e = h->cfg.gas_mode == PAB_GAS_TRANSFER
+                        ? pab::launch_transfer_moments(h->K, nb_dev, h->R, h->V, h->pb, moments_dev,
+                                                       h->block_warps, (cudaStream_t)stream)
+                        : pab::launch_moments(h->K, h->cfg.precision, nb_dev, h->R, h->V, moments_dev,
+                                              h->block_warps, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(h, e, "pab_moments launch");
     return PAB_OK;
@@ -718,6 +763,10 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
         fprintf(stderr, "pab_bubble_step_noalloc: %s\n", msg);
         return PAB_EINVAL;
     }
+    if (cfg->gas_mode == PAB_GAS_TRANSFER) {
+        fprintf(stderr, "pab_bubble_step_noalloc: gas_mode PAB_GAS_TRANSFER needs a handle\n");
+        return PAB_EINVAL;
+    }
     double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
     if (cfg->R0_host) {
         for (int i = 0; i < cfg->n_bins; ++i) {
@@ -756,4 +805,37 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
         return PAB_ECUDA;
     }
     return PAB_OK;
+}
+
+extern "C" pab_status pab_get_contents(pab_t *h, double *pb_dev, double *mv_dev, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (h->cfg.gas_mode != PAB_GAS_TRANSFER)
+        return fail(h, PAB_EINVAL, "pab_get_contents: the handle has no PAB_GAS_TRANSFER contents");
+    const size_t n = n_state(h) * sizeof(double);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (pb_dev)
+        e = cudaMemcpyAsync(pb_dev, h->pb, n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && mv_dev)
+        e = cudaMemcpyAsync(mv_dev, h->mv, n, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_get_contents");
+}
+
+extern "C" pab_status pab_set_contents(pab_t *h, const double *pb_dev, const double *mv_dev,
+                                       void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (h->cfg.gas_mode != PAB_GAS_TRANSFER)
+        return fail(h, PAB_EINVAL, "pab_set_contents: the handle has no PAB_GAS_TRANSFER contents");
+    const size_t n = n_state(h) * sizeof(double);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (pb_dev)
+        e = cudaMemcpyAsync(h->pb, pb_dev, n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && mv_dev)
+        e = cudaMemcpyAsync(h->mv, mv_dev, n, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_set_contents");
 }

@@ -589,6 +589,8 @@ pab_status pab_batch_admit(pab_batch_t *b, const pab_config *cfg, void *stream, 
     char msg[256];
     if (pab::validate_config(cfg, msg, sizeof(msg)) != PAB_OK)
         return bfail(b, PAB_EINVAL, "pab_batch_admit: %s", msg);
+    if (cfg->gas_mode == PAB_GAS_TRANSFER)
+        return bfail(b, PAB_EINVAL, "pab_batch_admit: gas_mode PAB_GAS_TRANSFER is not batched");
     if (cfg->n_bins > b->cfg.max_bins)
         return bfail(b, PAB_EINVAL, "pab_batch_admit: n_bins %d above the batch's max_bins %d",
                      cfg->n_bins, b->cfg.max_bins);

@@ -253,6 +253,10 @@ pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const doub
         fprintf(stderr, "pab_el_create: %s\n", msg);
         return PAB_EINVAL;
     }
+    if (c.gas_mode == PAB_GAS_TRANSFER) {
+        fprintf(stderr, "pab_el_create: gas_mode PAB_GAS_TRANSFER is not available here\n");
+        return PAB_EINVAL;
+    }
     const long long N = n_bubbles;
     std::vector<pab::BinConst> bub((size_t)N);
     std::vector<long long> cell((size_t)N);

@@ -55,6 +55,14 @@ struct StepConst {
     double v_collapse;    // mixed: |Rdot| above this takes the FP64 path (c/20)
     double r_collapse;    // mixed: R/R0 below this takes the FP64 path (0.2)
     double nb_default;    // n_b when the caller passes no n_b field
+    // contents with heat and mass transfer (gas_mode PAB_GAS_TRANSFER)
+    double tr_Rg, tr_Rv;  // gas constants of the gas and of the vapour
+    double tr_Tw;         // wall temperature
+    double tr_RvTw;       // R_v T_w
+    double tr_rho_vw;     // pv / (R_v T_w): vapour density at the wall
+    double tr_inv_RgTw;   // 1 / (R_g T_w)
+    double tr_kT;         // (gamma - 1)/gamma k_bw beta_T
+    double tr_Dc;         // D beta_c
     // (1 + d)^(-3 gamma) = sum_k gas_c[k] d^k for |d| <= gas_dmax (truncation below half an ulp)
     double gas_c[kGasTerms];
     double gas_dmax;
@@ -92,6 +100,8 @@ struct StepArgs {
     int32_t *attempts;     // [B][C] or nullptr
     double *out;           // [7][C] or nullptr
     Counters *counters;
+    double *pb = nullptr;  // [B][C] bubble pressure (PAB_GAS_TRANSFER)
+    double *mv = nullptr;  // [B][C] vapour mass (PAB_GAS_TRANSFER)
 };
 
 // Configuration helpers (pab_api.cu): validation as pab_create does it, the
@@ -110,6 +120,13 @@ cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, 
                            const double *V, double *out, int block_warps, cudaStream_t s);
 cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
                         float *h, cudaStream_t s);
+// Contents with transfer (pab_transfer.cu): the step, the moments and the equilibrium
+// contents p_b = p0 + 2 sigma/R0, m_v = pv V0/(R_v T_w).
+cudaError_t launch_transfer_step(const StepConst &K, const StepArgs &a, int block_warps, cudaStream_t s);
+cudaError_t launch_transfer_moments(const StepConst &K, const double *nb, const double *R,
+                                    const double *V, const double *pb, double *out, int block_warps,
+                                    cudaStream_t s);
+cudaError_t launch_transfer_init(const StepConst &K, double *pb, double *mv, cudaStream_t s);
 
 // Launchers of the carrier-facing forms (pab_closure.cu).
 cudaError_t launch_cons_from_prim(const StepConst &K, const double *nb, const double *R,

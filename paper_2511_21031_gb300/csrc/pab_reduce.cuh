@@ -1,0 +1,139 @@
+// Per-cell quadrature reduction shared by the step kernels: running sums of
+// one lane (one cell), the combination of a tile's warps in shared memory with
+// the store of the 7 moments, and the CTA's status counters.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pab_bits.cuh"
+#include "pab_internal.h"
+
+namespace pab {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kMaxWarps = 16;
+
+// Running quadrature sums of one lane (one cell).  FP64 mode: plain FP64
+// sums (the pressure sum of w R^3 p_bw/rho).  MIXED mode: the alpha sum
+// sum w R^3 is FP64 and compensated (Neumaier); sum w R^3 p_bw splits into
+// p0 sum w R^3, formed once per cell from the alpha sum, and an FP32 sum of
+// w R^3 (p_bw - p0); sum w R^2 Rdot and sum w R^3 Rdot^2 are FP32 sums of
+// FP32 terms.
+template <bool MIXED>
+struct MomAcc {
+    double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
+    float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
+
+    __device__ __forceinline__ void add_m3(double x)
+    {
+        if (MIXED) {
+            neumaier_add(m3, m3c, x);
+        } else {
+            m3 += x;
+        }
+    }
+
+    // per-lane totals as doubles
+    __device__ __forceinline__ double M2V() const { return MIXED ? f2d(m2vf) : m2v; }
+    __device__ __forceinline__ double M3P() const { return MIXED ? f2d(m3pf) : m3p; }
+    __device__ __forceinline__ double M3V2() const { return MIXED ? f2d(m3v2f) : m3v2; }
+};
+
+// Combine the warps' partial sums of one tile and write the moments.
+template <bool MIXED>
+__device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAcc<MIXED> &acc,
+                                                 double nb, int64_t c, bool valid, double *out)
+{
+    __shared__ double red[5][kMaxWarps][kTile];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    red[0][warp][lane] = acc.m3;
+    red[1][warp][lane] = acc.m3c;
+    red[2][warp][lane] = acc.M2V();
+    red[3][warp][lane] = acc.M3P();
+    red[4][warp][lane] = acc.M3V2();
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double m3 = red[0][0][lane], m3c = red[1][0][lane];
+        double m2v = red[2][0][lane], m3p = red[3][0][lane], m3v2 = red[4][0][lane];
+        for (int w = 1; w < nw; ++w) {
+            const double x = red[0][w][lane];
+            if (MIXED) {
+                neumaier_add(m3, m3c, x);
+                m3c += red[1][w][lane];
+            } else {
+                m3 += x;
+            }
+            m2v += red[2][w][lane];
+            m3p += red[3][w][lane];
+            m3v2 += red[4][w][lane];
+        }
+        if (MIXED)
+            m3 += m3c;
+        const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
+        const double inv_m3 = 1.0 / m3;
+        const int64_t C = K.C;
+        out[0 * C + c] = nb;
+        out[1 * C + c] = alpha;
+        out[2 * C + c] = m3;
+        out[3 * C + c] = m2v;
+        out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
+        out[5 * C + c] = MIXED ? fma(m3p, inv_m3, K.p0) : K.rho * m3p * inv_m3;
+        out[6 * C + c] = m3v2 * inv_m3;
+    }
+}
+
+// Block-wide sums of the status counters, one atomic per CTA and counter.
+__device__ __forceinline__ void flush_counters(uint32_t fl_or, uint32_t n_flag, uint32_t n_att,
+                                               uint32_t n64, Counters *cnt)
+{
+    __shared__ uint32_t sc[4][kMaxWarps];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    fl_or = __reduce_or_sync(0xffffffffu, fl_or);
+    n_flag = __reduce_add_sync(0xffffffffu, n_flag);
+    n_att = __reduce_add_sync(0xffffffffu, n_att);
+    n64 = __reduce_add_sync(0xffffffffu, n64);
+    if (lane == 0) {
+        sc[0][warp] = fl_or;
+        sc[1][warp] = n_flag;
+        sc[2][warp] = n_att;
+        sc[3][warp] = n64;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t f = 0;
+        unsigned long long a = 0, b = 0, d = 0;
+        for (int w = 0; w < nw; ++w) {
+            f |= sc[0][w];
+            a += sc[1][w];
+            b += sc[2][w];
+            d += sc[3][w];
+        }
+        if (f)
+            atomicOr(&cnt->flags_or, f);
+        if (a)
+            atomicAdd(&cnt->n_flagged, a);
+        if (b)
+            atomicAdd(&cnt->n_attempts, b);
+        if (d)
+            atomicAdd(&cnt->n_fp64, d);
+    }
+}
+
+__host__ __device__ inline int clamp_warps(int w, int B)
+{
+    if (w <= 0)
+        w = 8;
+    if (w > kMaxWarps)
+        w = kMaxWarps;
+    if (w > B)
+        w = B;
+    return w < 1 ? 1 : w;
+}
+
+}  // namespace
+}  // namespace pab

@@ -1,0 +1,273 @@
+// The bubble source update with heat and mass transfer in the contents
+// (gas_mode PAB_GAS_TRANSFER, FP64): four states per (bin, cell), R, Rdot, the
+// bubble pressure p_b and the vapour mass m_v.  The work decomposition is the
+// one of step_kernel (a CTA owns 32 cells, its warps stride over the bins, the
+// moments are reduced in the same launch); the model is stated in
+// pab_transfer.h.
+#include <cuda_runtime.h>
+
+#include "pab_device.cuh"
+#include "pab_internal.h"
+#include "pab_reduce.cuh"
+
+namespace pab {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct State4 {
+    double R, V, pb, mv;
+};
+
+struct Trial4 {
+    State4 y;        // third-order result
+    double eR, eV;   // y3 - z of R and Rdot (the embedded second-order difference)
+    bool ok;         // stage radii positive and Rdot finite
+};
+
+// m_g R_g of a bin: the gas of equilibrium at R0, (p0 + 2 sigma/R0 - pv) V0 / T_w.
+__device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc)
+{
+    const double V0 = (4.0 / 3.0 * kPi) * bc.R0 * bc.R0 * bc.R0;
+    return (K.p0 + K.two_sigma * bc.invR0 - K.pv) * V0 / K.tr_Tw;
+}
+
+// dp_b/dt and dm_v/dt (Ando's pressure equation and Eq. massVaporRate with
+// constant-coefficient wall gradients), iR = 1/R.
+__device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, const State4 &s,
+                                               double iR, double &dpb, double &dmv)
+{
+    const double Vb = (4.0 / 3.0 * kPi) * s.R * s.R * s.R;
+    const double T_mean = s.pb * Vb * rcp64(fma(s.mv, K.tr_Rv, mRg));
+    const double mvRg = s.mv * K.tr_Rg;
+    const double chi_mean = mvRg * rcp64(mvRg + mRg);      // m_v / (m_v + m_g)
+    const double rho_gw = (s.pb - K.pv) * K.tr_inv_RgTw;   // gas density at the wall
+    const double rho_bw = K.tr_rho_vw + rho_gw;
+    const double chi_vw = K.tr_rho_vw * rcp64(rho_bw);
+    // D rho_bw / (1 - chi_vw) = D rho_bw^2 / rho_gw;  dchi/dr = beta_c (chi_vw - chi_mean) / R
+    const double mdot = K.tr_Dc * rho_bw * rho_bw * rcp64(rho_gw) * (chi_vw - chi_mean) * iR;
+    // (gamma - 1)/gamma k_bw dT/dr with dT/dr = beta_T (T_w - T_mean) / R
+    const double heat = K.tr_kT * (K.tr_Tw - T_mean) * iR;
+    dpb = K.three_gamma * iR * (fma(K.tr_RvTw, mdot, heat) - s.V * s.pb);
+    dmv = (4.0 * kPi) * s.R * s.R * mdot;
+}
+
+// Keller-Miksis, Eq. (keller_miksis), with the state p_b: the Rddot inside
+// d/dt p_bw moves to the left-hand side as in accel64.
+__device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double p_inf, const State4 &s)
+{
+    const double icV = s.V * K.inv_c;
+    const double den = fma(s.R, 1.0 - icV, K.fmu_ic_rho);
+    const double inv = rcp64(s.R * den);
+    const double iR = den * inv;
+    const double iden = s.R * inv;
+    double dpb, dmv;
+    transfer_rates(K, mRg, s, iR, dpb, dmv);
+    const double swR = fma(K.four_mu, s.V, K.two_sigma) * iR;   // (4 mu Rdot + 2 sigma)/R
+    const double pbw = s.pb - swR;
+    const double dpbw = fma(swR * iR, s.V, dpb);                 // dp_b/dt + s Rdot/R^2
+    const double num = (pbw - p_inf) * K.inv_rho * (1.0 + icV) + s.R * K.ic_rho * dpbw
+                     - 1.5 * s.V * s.V * (1.0 - icV * (1.0 / 3.0));
+    return State4{s.V, num * iden, dpb, dmv};
+}
+
+__device__ __forceinline__ State4 axpy(double h, const State4 &f, const State4 &y)
+{
+    return State4{fma(h, f.R, y.R), fma(h, f.V, y.V), fma(h, f.pb, y.pb), fma(h, f.mv, y.mv)};
+}
+
+// Shu-Osher SSP-RK3 with the embedded Heun member (as trial64), on four components.
+__device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double p_inf, const State4 &y,
+                                         double h)
+{
+    const State4 y1 = axpy(h, rhs4(K, mRg, p_inf, y), y);
+    const State4 u = axpy(h, rhs4(K, mRg, p_inf, y1), y1);
+    const double zR = 0.5 * (y.R + u.R), zV = 0.5 * (y.V + u.V);
+    const State4 y2{fma(0.75, y.R, 0.25 * u.R), fma(0.75, y.V, 0.25 * u.V), fma(0.75, y.pb, 0.25 * u.pb),
+                    fma(0.75, y.mv, 0.25 * u.mv)};
+    const State4 w = axpy(h, rhs4(K, mRg, p_inf, y2), y2);
+    Trial4 t;
+    t.y = State4{fma(2.0 / 3.0, w.R, y.R * (1.0 / 3.0)), fma(2.0 / 3.0, w.V, y.V * (1.0 / 3.0)),
+                 fma(2.0 / 3.0, w.pb, y.pb * (1.0 / 3.0)), fma(2.0 / 3.0, w.mv, y.mv * (1.0 / 3.0))};
+    t.eR = t.y.R - zR;
+    t.eV = t.y.V - zV;
+    t.ok = gt0(y1.R) && gt0(y2.R) && gt0(t.y.R) && finite64(t.y.V);
+    return t;
+}
+
+// The controller of advance_adaptive (or n equal sub-steps in fixed mode);
+// the error norm reads R and Rdot.
+__device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, double p_inf, double dt,
+                                             State4 &y, float &hc, int &n_att)
+{
+    if (K.n_fixed > 0) {
+        const double hf = dt / (double)K.n_fixed;
+        for (int i = 0; i < K.n_fixed; ++i)
+            y = trial4(K, mRg, p_inf, y, hf).y;
+        n_att = K.n_fixed;
+        return 0;
+    }
+    double h = f2d(hc);
+    if (!gt0(h) || !le(h, dt))
+        h = dt;
+    double t = 0.0;
+    uint32_t flags = 0;
+    int n = 0;
+    for (;;) {
+        if (n >= K.max_attempts) {
+            flags |= PAB_FLAG_STEP_LIMIT;
+            break;
+        }
+        const double rem = dt - t;
+        const bool last = le(rem, h);
+        const double ht = last ? rem : h;
+        const Trial4 tr = trial4(K, mRg, p_inf, y, ht);
+        ++n;
+        const Trial t2{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok};
+        const double err = error_norm(K, t2);
+        const double fac = step_factor(K, err, tr.ok);
+        if (tr.ok && le(err, K.tol)) {
+            y = tr.y;
+            if (last) {
+                const bool clipped = !le(h, rem);
+                h = (clipped && le(1.0, fac)) ? h : ht * fac;
+                break;
+            }
+            t += ht;
+            h = ht * fac;
+        } else {
+            h = ht * fac;
+        }
+    }
+    hc = d2f(h);
+    n_att = n;
+    return flags;
+}
+
+// Quadrature terms with p_bw = p_b - (4 mu Rdot + 2 sigma)/R, the pressure sum over rho.
+__device__ __forceinline__ void accumulate_transfer(const StepConst &K, const BinConst &bc,
+                                                    const State4 &y, MomAcc<false> &acc)
+{
+    const double wr2 = bc.w * y.R * y.R;
+    const double wr3 = wr2 * y.R;
+    const double pbw_rho = (y.pb - fma(K.four_mu, y.V, K.two_sigma) * rcp64(y.R)) * K.inv_rho;
+    acc.add_m3(wr3);
+    acc.m2v += wr2 * y.V;
+    acc.m3p += wr3 * pbw_rho;
+    acc.m3v2 += wr3 * y.V * y.V;
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    transfer_step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
+    const bool valid = c < K.C;
+    const double p_inf = valid ? a.p_inf[c] : K.p0;
+    const bool p_ok = finite64(p_inf);
+    const double nb = valid ? (a.nb ? a.nb[c] : K.nb_default) : 0.0;
+    MomAcc<false> acc;
+    uint32_t fl_or = 0, n_flag = 0, n_att = 0;
+    for (int b = warp; b < K.B; b += nw) {
+        if (!valid)
+            continue;
+        const BinConst &bc = K.bins[b];
+        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
+        State4 y{a.R[k], a.V[k], a.pb[k], a.mv[k]};
+        uint32_t fl = 0;
+        int na = 0;
+        if (!p_ok || !finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv)) {
+            fl = PAB_FLAG_NONFINITE;
+        } else {
+            float hc = a.h[k];
+            fl = advance4(K, gas_mRg(K, bc), p_inf, a.dt, y, hc, na);
+            if (K.n_fixed == 0)
+                a.h[k] = hc;
+            if (!finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv))
+                fl |= PAB_FLAG_NONFINITE;
+            else if (!gt0(y.R))
+                fl |= PAB_FLAG_NONPOS;
+            if (abs_ge(y.V, K.c))
+                fl |= PAB_FLAG_SUPERSONIC;
+            a.R[k] = y.R;
+            a.V[k] = y.V;
+            a.pb[k] = y.pb;
+            a.mv[k] = y.mv;
+        }
+        if (a.attempts)
+            a.attempts[k] = na;
+        fl_or |= fl;
+        n_flag += (fl != 0);
+        n_att += na;
+        if (a.out)
+            accumulate_transfer(K, bc, y, acc);
+    }
+    if (a.out)
+        reduce_and_store<false>(K, acc, nb, c, valid, a.out);
+    flush_counters(fl_or, n_flag, n_att, 0u, a.counters);
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    transfer_moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
+                            const double *__restrict__ Rp, const double *__restrict__ Vp,
+                            const double *__restrict__ pbp, double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
+    const bool valid = c < K.C;
+    const double nb = valid ? (nbp ? nbp[c] : K.nb_default) : 0.0;
+    MomAcc<false> acc;
+    for (int b = warp; b < K.B; b += nw) {
+        if (!valid)
+            continue;
+        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
+        accumulate_transfer(K, K.bins[b], State4{Rp[k], Vp[k], pbp[k], 0.0}, acc);
+    }
+    reduce_and_store<false>(K, acc, nb, c, valid, out);
+}
+
+// Equilibrium contents: p_b = p0 + 2 sigma/R0, m_v = (pv/(R_v T_w)) V0.
+__global__ void transfer_init_kernel(const __grid_constant__ StepConst K, double *pb, double *mv)
+{
+    const size_t n = (size_t)K.B * (size_t)K.C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const BinConst &bc = K.bins[(int)(i / (size_t)K.C)];
+        pb[i] = K.p0 + K.two_sigma * bc.invR0;
+        mv[i] = K.tr_rho_vw * ((4.0 / 3.0 * kPi) * bc.R0 * bc.R0 * bc.R0);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_transfer_step(const StepConst &K, const StepArgs &a, int block_warps, cudaStream_t s)
+{
+    if (!a.pb || !a.mv || !a.h)
+        return cudaErrorInvalidValue;
+    const int nw = clamp_warps(block_warps, K.B);
+    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
+    transfer_step_kernel<<<grid, nw * 32, 0, s>>>(K, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_moments(const StepConst &K, const double *nb, const double *R,
+                                    const double *V, const double *pb, double *out, int block_warps,
+                                    cudaStream_t s)
+{
+    const int nw = clamp_warps(block_warps, K.B);
+    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
+    transfer_moments_kernel<<<grid, nw * 32, 0, s>>>(K, nb, R, V, pb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_init(const StepConst &K, double *pb, double *mv, cudaStream_t s)
+{
+    transfer_init_kernel<<<152 * 8, 256, 0, s>>>(K, pb, mv);
+    return cudaGetLastError();
+}
+
+}  // namespace pab

@@ -17,7 +17,7 @@ from . import _build
 PAB_OK, PAB_EINVAL, PAB_ENOMEM, PAB_ECUDA, PAB_ESTEP_LIMIT, PAB_ENONFINITE, PAB_ESTATE = range(7)
 PAB_FP64, PAB_MIXED = 0, 1
 PAB_ADAPTIVE, PAB_FIXED = 0, 1
-PAB_GAS_POLYTROPIC, PAB_GAS_EMPTY = 0, 1
+PAB_GAS_POLYTROPIC, PAB_GAS_EMPTY, PAB_GAS_TRANSFER = 0, 1, 2
 FLAG_STEP_LIMIT, FLAG_NONFINITE, FLAG_SUPERSONIC, FLAG_NONPOS = 1, 2, 4, 8
 MAX_BINS = 63
 N_MOMENTS = 7
@@ -28,7 +28,8 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
-           "pab_stiffened_gas", "pab_math_check", "pab_bits_check")
+           "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_get_contents",
+           "pab_set_contents")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -48,7 +49,10 @@ class pab_config(ctypes.Structure):
                 ("stepper", ctypes.c_int32), ("n_fixed_sub", ctypes.c_int32),
                 ("max_attempts", ctypes.c_int32), ("tol", ctypes.c_double), ("v_floor", ctypes.c_double),
                 ("alpha0", ctypes.c_double), ("Rdot0_ref", ctypes.c_double),
-                ("record_attempts", ctypes.c_int32), ("block_warps", ctypes.c_int32)]
+                ("record_attempts", ctypes.c_int32), ("block_warps", ctypes.c_int32),
+                ("R_g", ctypes.c_double), ("R_v", ctypes.c_double), ("T_w", ctypes.c_double),
+                ("k_bw", ctypes.c_double), ("D_vg", ctypes.c_double), ("beta_T", ctypes.c_double),
+                ("beta_c", ctypes.c_double)]
 
 
 _LIB = None
@@ -80,6 +84,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_status_flags": (i32, [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i64),
                                    ctypes.POINTER(i64), ctypes.POINTER(i64), vp]),
         "pab_get_state": (i32, [vp, vp, vp, vp, vp]),
+        "pab_get_contents": (i32, [vp, vp, vp, vp]),
+        "pab_set_contents": (i32, [vp, vp, vp, vp]),
         "pab_set_state": (i32, [vp, vp, vp, vp, vp]),
         "pab_get_attempts": (i32, [vp, vp, vp]),
         "pab_get_bins": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
@@ -361,6 +367,23 @@ class Solver:
         pab_set_state(self.handle, self._dev(R, shp, torch.float64, "R"),
                       self._dev(V, shp, torch.float64, "Rdot"),
                       self._dev(h, shp, torch.float32, "h"), _stream_handle(stream))
+
+    def get_contents(self, stream=None):
+        """(p_b, m_v) [Nb][C] of a PAB_GAS_TRANSFER handle."""
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        pb = torch.empty(shp, dtype=torch.float64, device=self.device)
+        mv = torch.empty_like(pb)
+        _check(self.handle, load().pab_get_contents(self.handle, pb.data_ptr(), mv.data_ptr(),
+                                                    _stream_handle(stream) or None), "pab_get_contents")
+        return pb, mv
+
+    def set_contents(self, pb=None, mv=None, stream=None):
+        import torch
+        shp = (self.n_bins, self.n_cells)
+        _check(self.handle, load().pab_set_contents(self.handle, self._dev(pb, shp, torch.float64, "pb") or None,
+                                                    self._dev(mv, shp, torch.float64, "mv") or None,
+                                                    _stream_handle(stream) or None), "pab_set_contents")
 
     def attempts(self, stream=None):
         import torch

@@ -2,6 +2,7 @@
 include/pab.h declares, the ctypes config matches the C layout, and invalid
 calls are refused before any device work (no GPU needed)."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -12,7 +13,7 @@ import pytest
 from paper_2511_21031_gb300 import pab
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", f) for f in ("pab.h", "pab_measure.h", "pab_batch.h", "pab_closure.h", "pab_el.h")]
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def _declared():
