@@ -269,6 +269,62 @@ def _mixed_error_sample(wl, n_steps, n_cells=256):
     return out
 
 
+TRANSFER_PV = 2338.0  # saturated vapour pressure of water at 20 C
+
+
+def _bench_transfer(args, stream, dev, fp64_value):
+    """The 128^3 x 31 FP64 workload with the contents of pab_transfer.h (gas and
+    vapour with heat and mass transfer at the wall, p_v of water at 20 C), and
+    its error against the oracle on 64 seeded cells (outside the timed region)."""
+    import torch
+
+    import oracle
+    from paper_2511_21031_gb300 import pab
+    wl = make_workload("grid128", 0, args.edge)
+    total = args.warmup + args.steps
+    sol = pab.Solver(wl.n_cells, wl.n_bins, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K,
+                     alpha0=wl.alpha0, gas_mode=pab.PAB_GAS_TRANSFER, pv=TRANSFER_PV)
+    with torch.cuda.stream(stream):
+        ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
+    torch.cuda.synchronize()
+    r = _time_steps(sol, wl, ps, args, stream)
+    sol.close()
+    del ps
+    torch.cuda.synchronize()
+    bs = wl.n_cells * wl.n_bins * args.steps
+    # error sample
+    cells = np.sort(np.random.default_rng(13).choice(wl.n_cells, 64, replace=False))
+    sub = wl.subset(cells)
+    n_err = min(total, 20)
+    sv = pab.Solver(sub.n_cells, sub.n_bins, s_lognormal=sub.s, R0ref=sub.R0ref, span_K=sub.span_K,
+                    alpha0=sub.alpha0, gas_mode=pab.PAB_GAS_TRANSFER, pv=TRANSFER_PV)
+    P = oracle.Params(**dict(sub.fluid, pv=TRANSFER_PV))
+    T = oracle.Transfer()
+    R0 = np.array(sv.R0)
+    y0 = np.array([oracle.transfer_init(P, T, x) for x in R0])
+    R, V, pb, mv = (np.repeat(y0[:, i:i + 1], sub.n_cells, 1).copy() for i in range(4))
+    h = np.zeros(R.shape, np.float32)
+    for n in range(n_err):
+        p = sub.pressure_step(n)
+        sv.step(torch.as_tensor(p, device="cuda"), sub.dt)
+        oracle.transfer_step(P, T, R0, p, sub.dt, R, V, pb, mv, h)
+    Rg = sv.get_state()[0].cpu().numpy()
+    pbg, mvg = (x.cpu().numpy() for x in sv.get_contents())
+    sv.close()
+    err = {"R": float(np.max(np.abs(Rg - R) / R)), "p_b": float(np.max(np.abs(pbg - pb) / pb)),
+           "m_v": float(np.max(np.abs(mvg - mv) / np.abs(mv))),
+           "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {n_err} steps, adaptive"}
+    return {"workload": wl.name.replace("fp64", "transfer"),
+            "label": "contents with heat and mass transfer (FP64)", "precision": "fp64",
+            "value": bs / (r["ms_total"] * 1e-3), "unit": "bin-steps/s",
+            "ms_per_step": r["ms_total"] / args.steps,
+            "latency_ms": {"p50": float(np.percentile(r["launch_ms"], 50)),
+                           "p99": float(np.percentile(r["launch_ms"], 99))},
+            "trials_per_bin_step": r["status"]["n_attempts"] / bs, "status_flags": r["status"]["flags"],
+            "vs_polytropic_fp64": (bs / (r["ms_total"] * 1e-3)) / fp64_value,
+            "error_vs_oracle": err}
+
+
 def _bench_batched(args, stream, dev, n_instances=512):
     """512 independent instances (edge U{16..96}, Nb in {11,21,31,51}, amplitude
     U(0.3,1.5) p0, s U(0.2,0.7)) in one persistent mixed-precision launch per
@@ -518,6 +574,9 @@ def run_ours(args):
             del vps
             torch.cuda.synchronize()
 
+    if args.variants and args.transfer and ws == 1:
+        variants.append(_bench_transfer(args, stream, dev, value))
+
     if args.variants and args.batched and ws == 1:
         bv = _bench_batched(args, stream, dev, n_instances=args.batch_instances)
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
@@ -588,6 +647,8 @@ def main():
                     help="skip the 512-instance batched line")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the continuous-batching serving line")
+    ap.add_argument("--no-transfer", dest="transfer", action="store_false",
+                    help="skip the heat-and-mass-transfer contents line")
     ap.add_argument("--no-el", dest="el", action="store_false",
                     help="skip the volume-averaged (EL) line")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
