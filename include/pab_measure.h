@@ -38,14 +38,12 @@ pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int3
  *                    when |d| is beyond the series' range);
  *   gas_tab_dev[i] = the same value from the node table a handle uses (nearest
  *                    node x_j = q^j of R[i], node value times the series);
- *   exact_dev[i]   = exp(a log(1/R[i])) with CUDA's exp and log;
- *   rcbrt_dev[i]   = the library's R[i]^(-1/3) (FP32 seed, one FP64 Newton step).
+ *   exact_dev[i]   = exp(a log(1/R[i])) with CUDA's exp and log.
  * All arrays [n] FP64 on the device; a = 3 gamma > 0.  Allocates and frees a
  * small table.  Errors: PAB_EINVAL, PAB_ECUDA.
  */
 pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
-                          double *gas_dev, double *gas_tab_dev, double *exact_dev, double *rcbrt_dev,
-                          void *stream);
+                          double *gas_dev, double *gas_tab_dev, double *exact_dev, void *stream);
 
 /*
  * Values of the helpers that take work off the FP64 pipe, for the tests to

@@ -70,14 +70,6 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
     return G;
 }
 
-// x^(-1/3) for x > 0: FP32 seed rcbrtf, then one Newton step for y^-3 = x in
-// FP64, y <- y + y (1 - x y^3)/3 (relative error ~1e-14; the seed's ~1e-7 squared).
-__device__ __forceinline__ double rcbrt_newton(double x)
-{
-    const double y = f2d(rcbrtf(d2f(x)));
-    const double e = fma(-x, y * y * y, 1.0);
-    return fma(y * (1.0 / 3.0), e, y);
-}
 
 struct Trial {
     double R, V;    // third-order result y3
@@ -240,15 +232,35 @@ __device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
     return max_nn(fabs(t.eR) * vs, fabs(t.eV) * fabs(t.R)) * rcp64(fabs(t.R) * vs);
 }
 
-// Step-size factor clamp(0.9 (tol/err)^(1/3), 0.2, 5); 0.2 after a failed trial.
-// Below err = 1e-30 the clamp gives 5 for any tol >= 1e-18; past FP32 range, 0.2.
-__device__ __forceinline__ double step_factor(const StepConst &K, double err, bool ok)
+// Growth factor of the controller, clamp(0.9 (tol/err)^(1/3), 0.2, 5), in FP32
+// (a heuristic whose product is stored in FP32 between calls): 0.2 after a
+// failed trial or an error past the FP32 range, 5 for a zero error.
+__device__ __forceinline__ float growth_factor(const StepConst &K, float errf, bool ok)
 {
-    if (!ok || !le(err, 3.0e38))
-        return 0.2;
-    if (le(err, 1e-30))
-        return 5.0;
-    return min_nn(max_nn(0.9 * K.cbrt_tol * rcbrt_newton(err), 0.2), 5.0);
+    if (!ok || !(errf <= FLT_MAX))
+        return 0.2f;
+    if (errf == 0.0f)
+        return 5.0f;
+    return fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf(errf), 0.2f), 5.0f);
+}
+
+// Accept test and growth factor of an FP64 trial.  err <= tol is written
+// without a division, |eR| <= tol |R3| and |eRdot| <= tol max(|Rdot3|, v_floor)
+// (two FP64 products and integer compares; when ok holds R3 is positive and
+// finite).  The factor takes err from the FP32 images of the same quantities.
+struct Verdict {
+    bool accept;
+    float fac;
+};
+__device__ __forceinline__ Verdict judge64(const StepConst &K, const Trial &t)
+{
+    const double aR = abs_nn(t.R);
+    const double vs = max_nn(abs_nn(t.V), K.v_floor);
+    Verdict v;
+    v.accept = t.ok && le(abs_nn(t.eR), K.tol * aR) && le(abs_nn(t.eV), K.tol * vs);
+    const float errf = fmaxf(__fdividef(d2f(abs_nn(t.eR)), d2f(aR)), __fdividef(d2f(abs_nn(t.eV)), d2f(vs)));
+    v.fac = growth_factor(K, errf, t.ok);
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -295,14 +307,14 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
             tr = trial64(K, bc, B0, R, V, ht, g);
         }
         ++n;
-        const double err = error_norm(K, tr);
-        const double fac = step_factor(K, err, tr.ok);
-        if (tr.ok && le(err, K.tol)) {
+        const Verdict vd = judge64(K, tr);
+        const double fac = f2d(vd.fac);
+        if (vd.accept) {
             R = tr.R;
             V = tr.V;
             if (last) {
                 const bool clipped = !le(h, rem);
-                h = (clipped && le(1.0, fac)) ? h : ht * fac;
+                h = (clipped && vd.fac >= 1.0f) ? h : ht * fac;
                 break;
             }
             t += ht;
@@ -389,14 +401,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             full64 = false;
         }
         ++n;
-        const float errf = d2f(err);
-        float fac;
-        if (!ok || !(errf <= FLT_MAX))
-            fac = 0.2f;
-        else if (errf == 0.0f)
-            fac = 5.0f;
-        else
-            fac = fminf(fmaxf(0.9f * K.cbrt_tolf * rcbrtf(errf), 0.2f), 5.0f);
+        const float fac = growth_factor(K, d2f(err), ok);
         if (ok && le(err, K.tol)) {
             if (full64) {
                 R = nR;

@@ -30,7 +30,7 @@ __global__ void fma_streams(int iters, double *sink)
 
 __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, const double *tab,
                                   long long n, const double *R, const double *Rb, double *gas,
-                                  double *gas_tab, double *exact, double *rc)
+                                  double *gas_tab, double *exact)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -45,7 +45,6 @@ __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, cons
         g2.reset();
         gas_tab[i] = pab::gas_factor(Kt, Kt.bins[0], R[i], g2);
         exact[i] = exp(K.three_gamma * log(1.0 / R[i]));
-        rc[i] = pab::rcbrt_newton(R[i]);
     }
 }
 
@@ -118,10 +117,9 @@ extern "C" pab_status pab_bits_check(int64_t n, const float *f_dev, const double
 
 extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
                                      double *gas_dev, double *gas_tab_dev, double *exact_dev,
-                                     double *rcbrt_dev, void *stream)
+                                     void *stream)
 {
-    if (n < 0 || !(a > 0.0) ||
-        (n > 0 && (!R_dev || !Rb_dev || !gas_dev || !gas_tab_dev || !exact_dev || !rcbrt_dev)))
+    if (n < 0 || !(a > 0.0) || (n > 0 && (!R_dev || !Rb_dev || !gas_dev || !gas_tab_dev || !exact_dev)))
         return PAB_EINVAL;
     if (n == 0)
         return PAB_OK;
@@ -148,7 +146,7 @@ extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const doubl
         e = cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         math_check_kernel<<<152 * 4, 256, 0, s>>>(K, tab_dev, n, R_dev, Rb_dev, gas_dev, gas_tab_dev,
-                                                   exact_dev, rcbrt_dev);
+                                                   exact_dev);
         e = cudaGetLastError();
     }
     if (tab_dev)

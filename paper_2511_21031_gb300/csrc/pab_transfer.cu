@@ -123,14 +123,13 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
         const double ht = last ? rem : h;
         const Trial4 tr = trial4(K, mRg, p_inf, y, ht);
         ++n;
-        const Trial t2{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok};
-        const double err = error_norm(K, t2);
-        const double fac = step_factor(K, err, tr.ok);
-        if (tr.ok && le(err, K.tol)) {
+        const Verdict vd = judge64(K, Trial{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok});
+        const double fac = f2d(vd.fac);
+        if (vd.accept) {
             y = tr.y;
             if (last) {
                 const bool clipped = !le(h, rem);
-                h = (clipped && le(1.0, fac)) ? h : ht * fac;
+                h = (clipped && vd.fac >= 1.0f) ? h : ht * fac;
                 break;
             }
             t += ht;

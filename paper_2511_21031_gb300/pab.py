@@ -101,7 +101,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_set_conservative": (i32, [vp, vp, vp, vp, vp, vp]),
         "pab_mixture_pressure": (i32, [vp, vp, vp, vp, vp, vp]),
         "pab_stiffened_gas": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
-        "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp, vp]),
+        "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp]),
         "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -248,17 +248,16 @@ def pab_bits_check(f, x, y, stream=None):
 
 
 def pab_math_check(R, Rb, a: float, stream=None):
-    """(base-series value, table value, exp/log value, x^(-1/3)) of the library's device helpers."""
+    """(base-series value, table value, exp/log value) of the library's gas-term helpers."""
     import torch
     g = torch.empty_like(R)
     gt = torch.empty_like(R)
     e = torch.empty_like(R)
-    r = torch.empty_like(R)
     st = load().pab_math_check(R.numel(), R.data_ptr(), Rb.data_ptr(), float(a), g.data_ptr(),
-                               gt.data_ptr(), e.data_ptr(), r.data_ptr(), _stream_handle(stream) or None)
+                               gt.data_ptr(), e.data_ptr(), _stream_handle(stream) or None)
     if st != PAB_OK:
         raise PabError(st, "pab_math_check")
-    return g, gt, e, r
+    return g, gt, e
 
 
 def pab_destroy(h):

@@ -2,8 +2,7 @@
 double on the host): the binomial series of the gas term, around an exact base
 or around the nearest node of the handle's table (degree 11, used only where
 its truncation is below half an ulp), must be no less accurate than CUDA's
-exp(a log(x)) it replaces, and x^(-1/3) from an FP32 seed plus one FP64 Newton
-step must be accurate to 1e-13."""
+exp(a log(x)) it replaces."""
 import numpy as np
 import pytest
 
@@ -22,7 +21,7 @@ def test_gas_series_as_accurate_as_exp_log(a):
     Rb = np.exp(g.uniform(np.log(0.05), np.log(20.0), size=n))
     d = g.uniform(-0.05, 0.05, size=n)                 # beyond the series range too
     R = Rb * (1.0 + d)
-    gas, gtab, exact, _ = pab.pab_math_check(torch.as_tensor(R, device="cuda"),
+    gas, gtab, exact = pab.pab_math_check(torch.as_tensor(R, device="cuda"),
                                              torch.as_tensor(Rb, device="cuda"), a)
     ref = np.power(1.0 / R.astype(np.longdouble), np.longdouble(a))
     e_series = np.abs(gas.cpu().numpy().astype(np.longdouble) - ref) / ref
@@ -39,14 +38,3 @@ def test_gas_series_as_accurate_as_exp_log(a):
     ref_b = np.power(1.0 / Rb.astype(np.longdouble), np.longdouble(a))
     assert float(np.median(e_series[small])) <= 4 * ULP
     del ref_b
-
-
-def test_newton_rcbrt_relative_error():
-    import torch
-    g = np.random.default_rng(61)
-    x = np.exp(g.uniform(np.log(1e-30), np.log(1e30), size=200_000))
-    xt = torch.as_tensor(x, device="cuda")
-    _, _, _, rc = pab.pab_math_check(xt, xt, 4.2)
-    ref = np.power(x.astype(np.longdouble), np.longdouble(-1.0) / 3)
-    err = np.abs(rc.cpu().numpy().astype(np.longdouble) - ref) / ref
-    assert float(err.max()) <= 1e-13
