@@ -49,8 +49,8 @@ SM_MAX_MHZ = 2070.0
 # pressure and quadrature sums): least-squares fit of ncu's
 # smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over six launches
 # of the 64^3 x 31 grid with traced trial counts (residual 3e-4).
-FP64_FLOPS_PER_TRIAL = 172.5
-FP64_FLOPS_PER_BINSTEP = 50.8
+FP64_FLOPS_PER_TRIAL = 162.5
+FP64_FLOPS_PER_BINSTEP = 48.8
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
 # on the 64^3 x 31 grid, 283.5 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 34.9

@@ -173,6 +173,7 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->pv_rho = c->pv / c->rho;
     K->m05_inv_c = -0.5 * K->inv_c;
     K->tol = c->tol;
+    K->tol3 = 3.0 * c->tol;
     K->cbrt_tol = std::cbrt(c->tol);
     K->v_floor = c->v_floor >= 0.0 ? c->v_floor : 1e-3 * std::sqrt(c->p0 / c->rho);
     K->v_collapse = c->c / 20.0;

@@ -73,8 +73,8 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
 
 struct Trial {
     double R, V;    // third-order result y3
-    double eR, eV;  // y3 - z per component (embedded second-order difference; its sign is dropped
-                    // where error_norm multiplies it)
+    double eR, eV;  // 3 (y3 - z) = 2 k3 - (k1 + k2) per component: three times the embedded
+                    // second-order difference (its sign is dropped where it is multiplied)
     bool ok;        // every stage radius positive and y3 finite
 };
 
@@ -156,23 +156,26 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc,
 //   y1 = y + h f(y);  u = y1 + h f(y1)
 //   y2 = 3/4 y + 1/4 u;  z = 1/2 (y + u)      (z: second order)
 //   y3 = 1/3 y + 2/3 (y2 + h f(y2))           (third order, the one kept)
+// written with the increments k1 = h f(y), k2 = h f(y1), k3 = h f(y2):
+//   y1 = y + k1,  y2 = y + (k1 + k2)/4,  y3 = y + (k1 + k2)/6 + 2/3 k3,
+//   3 (y3 - z) = 2 k3 - (k1 + k2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
                                          double R, double V, double h, GasBase &g)
 {
     const double a1 = accel64(K, bc, B0, R, V, g);
-    const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
+    const double k1R = h * V, k1V = h * a1;
+    const double y1R = R + k1R, y1V = V + k1V;
     const double a2 = accel64(K, bc, B0, y1R, y1V, g);
-    const double uR = fma(h, y1V, y1R), uV = fma(h, a2, y1V);
-    const double zR = 0.5 * (R + uR), zV = 0.5 * (V + uV);
-    const double y2R = fma(0.75, R, 0.25 * uR), y2V = fma(0.75, V, 0.25 * uV);
+    const double sR = fma(h, y1V, k1R), sV = fma(h, a2, k1V);   // k1 + k2
+    const double y2R = fma(0.25, sR, R), y2V = fma(0.25, sV, V);
     const double a3 = accel64(K, bc, B0, y2R, y2V, g);
-    const double wR = fma(h, y2V, y2R), wV = fma(h, a3, y2V);
+    const double k3R = h * y2V, k3V = h * a3;
     Trial t;
-    t.R = fma(2.0 / 3.0, wR, R * (1.0 / 3.0));
-    t.V = fma(2.0 / 3.0, wV, V * (1.0 / 3.0));
-    t.eR = t.R - zR;
-    t.eV = t.V - zV;
+    t.R = fma(1.0 / 6.0, sR, fma(2.0 / 3.0, k3R, R));
+    t.V = fma(1.0 / 6.0, sV, fma(2.0 / 3.0, k3V, V));
+    t.eR = fma(2.0, k3R, -sR);
+    t.eV = fma(2.0, k3V, -sV);
     t.ok = gt0(y1R) && gt0(y2R) && gt0(t.R) && finite64(t.V);
     return t;
 }
@@ -216,8 +219,8 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
     Trial t;
     t.R = R + f2d(d3R);
     t.V = V + f2d(d3V);
-    t.eR = embedded_diff(k1R, k2R, k3R) * (1.0 / 3.0);
-    t.eV = embedded_diff(k1V, k2V, k3V) * (1.0 / 3.0);
+    t.eR = embedded_diff(k1R, k2R, k3R);
+    t.eV = embedded_diff(k1V, k2V, k3V);
     const float r1 = bc.R0f + (xi0 + k1R), r2 = bc.R0f + (xi0 + e2R);
     t.ok = (r1 > 0.0f) && (r2 > 0.0f) && gt0(t.R) && finite64(t.V) && isfinite(a1 + a2 + a3);
     return t;
@@ -229,7 +232,7 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
 __device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
 {
     const double vs = max_nn(abs_nn(t.V), K.v_floor);
-    return max_nn(fabs(t.eR) * vs, fabs(t.eV) * fabs(t.R)) * rcp64(fabs(t.R) * vs);
+    return max_nn(fabs(t.eR) * vs, fabs(t.eV) * fabs(t.R)) * rcp64((3.0 * fabs(t.R)) * vs);
 }
 
 // Growth factor of the controller, clamp(0.9 (tol/err)^(1/3), 0.2, 5), in FP32
@@ -246,8 +249,9 @@ __device__ __forceinline__ float growth_factor(const StepConst &K, float errf, b
 
 // Accept test and growth factor of an FP64 trial.  err <= tol is written
 // without a division, |eR| <= tol |R3| and |eRdot| <= tol max(|Rdot3|, v_floor)
-// (two FP64 products and integer compares; when ok holds R3 is positive and
-// finite).  The factor takes err from the FP32 images of the same quantities.
+// (two FP64 products and integer compares on the threefold differences the
+// trial carries, against 3 tol; when ok holds R3 is positive and finite).  The
+// factor takes err from the FP32 images of the same quantities.
 struct Verdict {
     bool accept;
     float fac;
@@ -257,8 +261,9 @@ __device__ __forceinline__ Verdict judge64(const StepConst &K, const Trial &t)
     const double aR = abs_nn(t.R);
     const double vs = max_nn(abs_nn(t.V), K.v_floor);
     Verdict v;
-    v.accept = t.ok && le(abs_nn(t.eR), K.tol * aR) && le(abs_nn(t.eV), K.tol * vs);
-    const float errf = fmaxf(__fdividef(d2f(abs_nn(t.eR)), d2f(aR)), __fdividef(d2f(abs_nn(t.eV)), d2f(vs)));
+    v.accept = t.ok && le(abs_nn(t.eR), K.tol3 * aR) && le(abs_nn(t.eV), K.tol3 * vs);
+    const float errf = (1.0f / 3.0f) * fmaxf(__fdividef(d2f(abs_nn(t.eR)), d2f(aR)),
+                                             __fdividef(d2f(abs_nn(t.eV)), d2f(vs)));
     v.fac = growth_factor(K, errf, t.ok);
     return v;
 }

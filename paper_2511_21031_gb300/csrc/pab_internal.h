@@ -29,7 +29,7 @@ struct BinConst {
 };
 
 constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
-constexpr int kGasTabTerms = 8;  // degree 7 around the nodes of a gas table
+constexpr int kGasTabTerms = 7;  // degree 6 around the nodes of a gas table
 
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
 // so warp-uniform reads come from the constant bank.
@@ -50,6 +50,7 @@ struct StepConst {
     double pv_rho;        // pv / rho
     double m05_inv_c;     // -0.5 / c
     double tol;
+    double tol3;          // 3 tol (Trial carries three times the embedded difference)
     double cbrt_tol;      // tol^(1/3)
     double v_floor;
     double v_collapse;    // mixed: |Rdot| above this takes the FP64 path (c/20)

@@ -21,7 +21,7 @@ struct State4 {
 
 struct Trial4 {
     State4 y;        // third-order result
-    double eR, eV;   // y3 - z of R and Rdot (the embedded second-order difference)
+    double eR, eV;   // 3 (y3 - z) of R and Rdot (three times the embedded difference)
     bool ok;         // stage radii positive and Rdot finite
 };
 
@@ -71,26 +71,29 @@ __device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double p_
     return State4{s.V, num * iden, dpb, dmv};
 }
 
-__device__ __forceinline__ State4 axpy(double h, const State4 &f, const State4 &y)
+__device__ __forceinline__ State4 scale(double h, const State4 &f)
 {
-    return State4{fma(h, f.R, y.R), fma(h, f.V, y.V), fma(h, f.pb, y.pb), fma(h, f.mv, y.mv)};
+    return State4{h * f.R, h * f.V, h * f.pb, h * f.mv};
 }
 
-// Shu-Osher SSP-RK3 with the embedded Heun member (as trial64), on four components.
+// Shu-Osher SSP-RK3 with the embedded Heun member in increment form (as trial64),
+// on four components: k1 = h f(y), y1 = y + k1, s = k1 + k2, y2 = y + s/4,
+// y3 = y + s/6 + 2/3 k3, 3 (y3 - z) = 2 k3 - s.
 __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double p_inf, const State4 &y,
                                          double h)
 {
-    const State4 y1 = axpy(h, rhs4(K, mRg, p_inf, y), y);
-    const State4 u = axpy(h, rhs4(K, mRg, p_inf, y1), y1);
-    const double zR = 0.5 * (y.R + u.R), zV = 0.5 * (y.V + u.V);
-    const State4 y2{fma(0.75, y.R, 0.25 * u.R), fma(0.75, y.V, 0.25 * u.V), fma(0.75, y.pb, 0.25 * u.pb),
-                    fma(0.75, y.mv, 0.25 * u.mv)};
-    const State4 w = axpy(h, rhs4(K, mRg, p_inf, y2), y2);
+    const State4 k1 = scale(h, rhs4(K, mRg, p_inf, y));
+    const State4 y1{y.R + k1.R, y.V + k1.V, y.pb + k1.pb, y.mv + k1.mv};
+    const State4 f2 = rhs4(K, mRg, p_inf, y1);
+    const State4 s{fma(h, f2.R, k1.R), fma(h, f2.V, k1.V), fma(h, f2.pb, k1.pb), fma(h, f2.mv, k1.mv)};
+    const State4 y2{fma(0.25, s.R, y.R), fma(0.25, s.V, y.V), fma(0.25, s.pb, y.pb), fma(0.25, s.mv, y.mv)};
+    const State4 k3 = scale(h, rhs4(K, mRg, p_inf, y2));
     Trial4 t;
-    t.y = State4{fma(2.0 / 3.0, w.R, y.R * (1.0 / 3.0)), fma(2.0 / 3.0, w.V, y.V * (1.0 / 3.0)),
-                 fma(2.0 / 3.0, w.pb, y.pb * (1.0 / 3.0)), fma(2.0 / 3.0, w.mv, y.mv * (1.0 / 3.0))};
-    t.eR = t.y.R - zR;
-    t.eV = t.y.V - zV;
+    t.y = State4{fma(1.0 / 6.0, s.R, fma(2.0 / 3.0, k3.R, y.R)), fma(1.0 / 6.0, s.V, fma(2.0 / 3.0, k3.V, y.V)),
+                 fma(1.0 / 6.0, s.pb, fma(2.0 / 3.0, k3.pb, y.pb)),
+                 fma(1.0 / 6.0, s.mv, fma(2.0 / 3.0, k3.mv, y.mv))};
+    t.eR = fma(2.0, k3.R, -s.R);
+    t.eV = fma(2.0, k3.V, -s.V);
     t.ok = gt0(y1.R) && gt0(y2.R) && gt0(t.y.R) && finite64(t.y.V);
     return t;
 }
