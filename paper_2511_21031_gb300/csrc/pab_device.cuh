@@ -41,7 +41,7 @@ __device__ __forceinline__ double gas_series(const StepConst &K, double d)
 // G = (R0/R)^(3 gamma) for R > 0.
 //  - With a node table (a handle's gas_tab): x = R/R0 goes to the nearest node
 //    x_j = q^j (picked in FP32: log2(x)/log2(q) rounded), and G = T_j (1 + d)^(-3 gamma)
-//    with d = (x - x_j)/x_j, |d| < gas_dmax_tab (degree-7 series). A pure
+//    with d = (x - x_j)/x_j, |d| < gas_dmax_tab (degree-6 series). A pure
 //    function of R: no exp or log while R/R0 stays within the table.
 //  - Otherwise (or outside the table): the radii of one step stay close to the
 //    last exact evaluation R_b in g, reached by the degree-11 series in
