@@ -151,6 +151,26 @@ pab_status pab_bubble_step_host(pab_t *h, const double *p_inf_host, const double
                                 double dt, double *moments_host, void *stream);
 
 /*
+ * Pipelined form of pab_bubble_step_host: enqueues the copy of p_inf_host (and
+ * nb_host) to the device, the step on `stream`, and the copy of the moments
+ * to moments_host, and returns without waiting.  The copies run on two streams
+ * the handle owns, through two sets of device staging buffers, so the input
+ * copy of one call and the output copy of the previous call overlap the
+ * steps; the steps themselves stay in call order on `stream`.  At most two
+ * calls are in flight: a call first waits until the call two before it has
+ * finished.  A call's host buffers must stay valid and unchanged, and its
+ * moments_host is not ready, until pab_host_wait returns (or until the second
+ * call after it has returned).  Pinned host memory is required for overlap.
+ * Errors: as pab_bubble_step_host.
+ */
+pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_host, const double *nb_host,
+                                      double dt, double *moments_host, void *stream);
+
+/* Wait until every pipelined call of the handle has finished (its moments are
+ * on the host and its host buffers are free).  Errors: PAB_EINVAL, PAB_ECUDA. */
+pab_status pab_host_wait(pab_t *h);
+
+/*
  * Synchronise `stream`, return the status accumulated since the last call
  * and reset it: *flags = OR of per-bin PAB_FLAG_* bits, *n_flagged = number
  * of bin-steps that set any bit, *n_attempts = total trials, *n_fp64 = trials

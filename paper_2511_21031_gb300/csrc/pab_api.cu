@@ -33,6 +33,14 @@ struct pab_s {
     double *stage_p = nullptr;                // host entry point staging [C]
     double *stage_nb = nullptr;               // [C]
     double *stage_out = nullptr;              // [7][C]
+    // pipelined host entry point: two staging sets, an input and an output copy stream
+    double *pipe_p[2] = {nullptr, nullptr};
+    double *pipe_nb[2] = {nullptr, nullptr};
+    double *pipe_out[2] = {nullptr, nullptr};
+    cudaStream_t pipe_in = nullptr, pipe_outs = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_step[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    bool pipe_busy[2] = {false, false};
+    int pipe_next = 0;
     int block_warps = 8;
     char err[512] = {0};
 };
@@ -444,12 +452,27 @@ void pab_destroy(pab_t *h)
     cudaGetDevice(&cur);
     if (cur != h->device)
         cudaSetDevice(h->device);
+    for (int i = 0; i < 2; ++i) {
+        if (h->ev_out[i])
+            cudaEventSynchronize(h->ev_out[i]);
+    }
     void *bufs[] = {h->R, h->V, h->h, h->attempts, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
-                    h->stage_nb, h->stage_out};
+                    h->stage_nb, h->stage_out, h->pipe_p[0], h->pipe_p[1], h->pipe_nb[0], h->pipe_nb[1],
+                    h->pipe_out[0], h->pipe_out[1]};
     for (void *b : bufs)
         if (b)
             cudaFreeAsync(b, s);
     cudaStreamSynchronize(s);
+    for (int i = 0; i < 2; ++i) {
+        cudaEvent_t evs[] = {h->ev_in[i], h->ev_step[i], h->ev_out[i]};
+        for (cudaEvent_t ev : evs)
+            if (ev)
+                cudaEventDestroy(ev);
+    }
+    if (h->pipe_in)
+        cudaStreamDestroy(h->pipe_in);
+    if (h->pipe_outs)
+        cudaStreamDestroy(h->pipe_outs);
     if (h->counters_host)
         cudaFreeHost(h->counters_host);
     if (cur != h->device)
@@ -839,4 +862,85 @@ extern "C" pab_status pab_set_contents(pab_t *h, const double *pb_dev, const dou
     if (e == cudaSuccess && mv_dev)
         e = cudaMemcpyAsync(h->mv, mv_dev, n, cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_set_contents");
+}
+
+extern "C" pab_status pab_host_wait(pab_t *h)
+{
+    if (!h)
+        return PAB_EINVAL;
+    for (int i = 0; i < 2; ++i) {
+        if (!h->pipe_busy[i])
+            continue;
+        cudaError_t e = cudaEventSynchronize(h->ev_out[i]);
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, "pab_host_wait");
+        h->pipe_busy[i] = false;
+    }
+    return PAB_OK;
+}
+
+extern "C" pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_host, const double *nb_host,
+                                                 double dt, double *moments_host, void *stream)
+{
+    if (!h)
+        return PAB_EINVAL;
+    if (!p_inf_host)
+        return fail(h, PAB_EINVAL, "pab_bubble_step_host_async: p_inf_host is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(h, PAB_EINVAL, "pab_bubble_step_host_async: dt must be positive and finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t C = (size_t)h->cfg.n_cells;
+    const int k = h->pipe_next;
+    cudaError_t e = cudaSuccess;
+    if (!h->pipe_in)
+        e = cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->pipe_outs)
+        e = cudaStreamCreateWithFlags(&h->pipe_outs, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (!h->ev_in[i])
+            e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_step[i])
+            e = cudaEventCreateWithFlags(&h->ev_step[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_out[i])
+            e = cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming);
+    }
+    // the call two before this one used the same staging set and host-side slot
+    if (e == cudaSuccess && h->pipe_busy[k]) {
+        e = cudaEventSynchronize(h->ev_out[k]);
+        h->pipe_busy[k] = false;
+    }
+    if (e == cudaSuccess && !h->pipe_p[k])
+        e = cudaMalloc((void **)&h->pipe_p[k], C * sizeof(double));
+    if (e == cudaSuccess && nb_host && !h->pipe_nb[k])
+        e = cudaMalloc((void **)&h->pipe_nb[k], C * sizeof(double));
+    if (e == cudaSuccess && moments_host && !h->pipe_out[k])
+        e = cudaMalloc((void **)&h->pipe_out[k], 7 * C * sizeof(double));
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host_async setup");
+    e = cudaMemcpyAsync(h->pipe_p[k], p_inf_host, C * sizeof(double), cudaMemcpyHostToDevice, h->pipe_in);
+    if (e == cudaSuccess && nb_host)
+        e = cudaMemcpyAsync(h->pipe_nb[k], nb_host, C * sizeof(double), cudaMemcpyHostToDevice, h->pipe_in);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(h->ev_in[k], h->pipe_in);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(s, h->ev_in[k], 0);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host_async H2D");
+    pab_status st = pab_bubble_step(h, h->pipe_p[k], nb_host ? h->pipe_nb[k] : nullptr, dt,
+                                    moments_host ? h->pipe_out[k] : nullptr, stream);
+    if (st != PAB_OK)
+        return st;
+    e = cudaEventRecord(h->ev_step[k], s);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(h->pipe_outs, h->ev_step[k], 0);
+    if (e == cudaSuccess && moments_host)
+        e = cudaMemcpyAsync(moments_host, h->pipe_out[k], 7 * C * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->pipe_outs);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(h->ev_out[k], h->pipe_outs);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "pab_bubble_step_host_async D2H");
+    h->pipe_busy[k] = true;
+    h->pipe_next = 1 - k;
+    return PAB_OK;
 }

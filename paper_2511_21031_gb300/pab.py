@@ -24,7 +24,7 @@ N_MOMENTS = 7
 MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3Rdot2_over_R3")
 
 EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
-           "pab_bubble_step_host", "pab_status_flags", "pab_get_state", "pab_set_state",
+           "pab_bubble_step_host", "pab_bubble_step_host_async", "pab_host_wait", "pab_status_flags", "pab_get_state", "pab_set_state",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
@@ -85,6 +85,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                    ctypes.POINTER(i64), ctypes.POINTER(i64), vp]),
         "pab_get_state": (i32, [vp, vp, vp, vp, vp]),
         "pab_get_contents": (i32, [vp, vp, vp, vp]),
+        "pab_bubble_step_host_async": (i32, [vp, vp, vp, dbl, vp, vp]),
+        "pab_host_wait": (i32, [vp]),
         "pab_set_contents": (i32, [vp, vp, vp, vp]),
         "pab_set_state": (i32, [vp, vp, vp, vp, vp]),
         "pab_get_attempts": (i32, [vp, vp, vp]),
@@ -347,6 +349,24 @@ class Solver:
                              hp(moments_host, (N_MOMENTS, self.n_cells), "moments_host"),
                              _stream_handle(stream))
         return moments_host
+
+    def step_host_async(self, p_inf_host, dt: float, moments_host=None, nb_host=None, stream=None):
+        """Pipelined end-to-end form: returns at once; moments_host is ready (and the host
+        tensors free) after host_wait() or after the second call after this one."""
+        import torch
+        for t, shape, name in ((p_inf_host, (self.n_cells,), "p_inf_host"), (nb_host, (self.n_cells,), "nb_host"),
+                               (moments_host, (N_MOMENTS, self.n_cells), "moments_host")):
+            if t is not None and (t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous()
+                                  or tuple(t.shape) != shape):
+                raise ValueError(f"{name} must be a contiguous float64 CPU tensor of shape {shape}")
+        _check(self.handle, load().pab_bubble_step_host_async(
+            self.handle, p_inf_host.data_ptr(), nb_host.data_ptr() if nb_host is not None else None, float(dt),
+            moments_host.data_ptr() if moments_host is not None else None, _stream_handle(stream) or None),
+            "pab_bubble_step_host_async")
+        return moments_host
+
+    def host_wait(self):
+        _check(self.handle, load().pab_host_wait(self.handle), "pab_host_wait")
 
     def status(self, stream=None, raise_on_error=False):
         return pab_status_flags(self.handle, _stream_handle(stream), raise_on_error)
