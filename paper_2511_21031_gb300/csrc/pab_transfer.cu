@@ -33,7 +33,13 @@ __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc
 }
 
 // dp_b/dt and dm_v/dt (Ando's pressure equation and Eq. massVaporRate with
-// constant-coefficient wall gradients), iR = 1/R.
+// constant-coefficient wall gradients), iR = 1/R.  With chi_vw = rho_vw/rho_bw
+// and 1 - chi_vw = rho_gw/rho_bw the vapour flux is
+//   mdot = D beta_c rho_bw (rho_vw - chi_mean rho_bw) / (rho_gw R) = X / R,
+// so the wall fraction needs no reciprocal, and the heat term
+// (gamma - 1)/gamma k_bw beta_T (T_w - T_mean)/R shares the factor 1/R:
+//   dp_b/dt = 3 gamma/R ((R_v T_w X + kT (T_w - T_mean))/R - Rdot p_b),
+//   dm_v/dt = 4 pi R^2 mdot = 4 pi R X.
 __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, const State4 &s,
                                                double iR, double &dpb, double &dmv)
 {
@@ -43,32 +49,29 @@ __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, c
     const double chi_mean = mvRg * rcp64(mvRg + mRg);      // m_v / (m_v + m_g)
     const double rho_gw = (s.pb - K.pv) * K.tr_inv_RgTw;   // gas density at the wall
     const double rho_bw = K.tr_rho_vw + rho_gw;
-    const double chi_vw = K.tr_rho_vw * rcp64(rho_bw);
-    // D rho_bw / (1 - chi_vw) = D rho_bw^2 / rho_gw;  dchi/dr = beta_c (chi_vw - chi_mean) / R
-    const double mdot = K.tr_Dc * rho_bw * rho_bw * rcp64(rho_gw) * (chi_vw - chi_mean) * iR;
-    // (gamma - 1)/gamma k_bw dT/dr with dT/dr = beta_T (T_w - T_mean) / R
-    const double heat = K.tr_kT * (K.tr_Tw - T_mean) * iR;
-    dpb = K.three_gamma * iR * (fma(K.tr_RvTw, mdot, heat) - s.V * s.pb);
-    dmv = (4.0 * kPi) * s.R * s.R * mdot;
+    const double X = K.tr_Dc * rho_bw * rcp64(rho_gw) * fma(-chi_mean, rho_bw, K.tr_rho_vw);
+    const double q = fma(K.tr_RvTw, X, K.tr_kT * (K.tr_Tw - T_mean));
+    dpb = K.three_gamma * iR * fma(q, iR, -s.V * s.pb);
+    dmv = (4.0 * kPi) * s.R * X;
 }
 
-// Keller-Miksis, Eq. (keller_miksis), with the state p_b: the Rddot inside
-// d/dt p_bw moves to the left-hand side as in accel64.
-__device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double p_inf, const State4 &s)
+// Keller-Miksis, Eq. (keller_miksis), with the state p_b, regrouped as in
+// accel64: the s/R terms (s = 4 mu Rdot + 2 sigma) of (p_bw - p_inf)(1 + Rdot/c)/rho
+// and of (R/(rho c)) d/dt p_bw add up to -s/(rho R), which leaves
+//   Rddot = (N0 R - s/rho) / (R den),
+//   N0 = (p_b - p_inf)/rho (1 + Rdot/c) + R dp_b/dt /(rho c) - Rdot^2 (3/2 - Rdot/(2c)).
+__device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double pinf_rho, const State4 &s)
 {
-    const double icV = s.V * K.inv_c;
-    const double den = fma(s.R, 1.0 - icV, K.fmu_ic_rho);
+    const double den = fma(s.R, fma(s.V, -K.inv_c, 1.0), K.fmu_ic_rho);
     const double inv = rcp64(s.R * den);
     const double iR = den * inv;
-    const double iden = s.R * inv;
     double dpb, dmv;
     transfer_rates(K, mRg, s, iR, dpb, dmv);
-    const double swR = fma(K.four_mu, s.V, K.two_sigma) * iR;   // (4 mu Rdot + 2 sigma)/R
-    const double pbw = s.pb - swR;
-    const double dpbw = fma(swR * iR, s.V, dpb);                 // dp_b/dt + s Rdot/R^2
-    const double num = (pbw - p_inf) * K.inv_rho * (1.0 + icV) + s.R * K.ic_rho * dpbw
-                     - 1.5 * s.V * s.V * (1.0 - icV * (1.0 / 3.0));
-    return State4{s.V, num * iden, dpb, dmv};
+    const double P = fma(s.pb, K.inv_rho, -pinf_rho);
+    const double w = fma(s.R * K.ic_rho, dpb, -s.V * (s.V * fma(s.V, K.m05_inv_c, 1.5)));
+    const double N0 = fma(P, fma(s.V, K.inv_c, 1.0), w);
+    const double s_rho = fma(K.fmu_rho, s.V, K.tsig_rho);
+    return State4{s.V, fma(N0, s.R, -s_rho) * inv, dpb, dmv};
 }
 
 __device__ __forceinline__ State4 scale(double h, const State4 &f)
@@ -79,15 +82,15 @@ __device__ __forceinline__ State4 scale(double h, const State4 &f)
 // Shu-Osher SSP-RK3 with the embedded Heun member in increment form (as trial64),
 // on four components: k1 = h f(y), y1 = y + k1, s = k1 + k2, y2 = y + s/4,
 // y3 = y + s/6 + 2/3 k3, 3 (y3 - z) = 2 k3 - s.
-__device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double p_inf, const State4 &y,
+__device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double pinf_rho, const State4 &y,
                                          double h)
 {
-    const State4 k1 = scale(h, rhs4(K, mRg, p_inf, y));
+    const State4 k1 = scale(h, rhs4(K, mRg, pinf_rho, y));
     const State4 y1{y.R + k1.R, y.V + k1.V, y.pb + k1.pb, y.mv + k1.mv};
-    const State4 f2 = rhs4(K, mRg, p_inf, y1);
+    const State4 f2 = rhs4(K, mRg, pinf_rho, y1);
     const State4 s{fma(h, f2.R, k1.R), fma(h, f2.V, k1.V), fma(h, f2.pb, k1.pb), fma(h, f2.mv, k1.mv)};
     const State4 y2{fma(0.25, s.R, y.R), fma(0.25, s.V, y.V), fma(0.25, s.pb, y.pb), fma(0.25, s.mv, y.mv)};
-    const State4 k3 = scale(h, rhs4(K, mRg, p_inf, y2));
+    const State4 k3 = scale(h, rhs4(K, mRg, pinf_rho, y2));
     Trial4 t;
     t.y = State4{fma(1.0 / 6.0, s.R, fma(2.0 / 3.0, k3.R, y.R)), fma(1.0 / 6.0, s.V, fma(2.0 / 3.0, k3.V, y.V)),
                  fma(1.0 / 6.0, s.pb, fma(2.0 / 3.0, k3.pb, y.pb)),
@@ -103,10 +106,11 @@ __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double 
 __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, double p_inf, double dt,
                                              State4 &y, float &hc, int &n_att)
 {
+    const double pinf_rho = p_inf * K.inv_rho;
     if (K.n_fixed > 0) {
         const double hf = dt / (double)K.n_fixed;
         for (int i = 0; i < K.n_fixed; ++i)
-            y = trial4(K, mRg, p_inf, y, hf).y;
+            y = trial4(K, mRg, pinf_rho, y, hf).y;
         n_att = K.n_fixed;
         return 0;
     }
@@ -124,7 +128,7 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
         const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
-        const Trial4 tr = trial4(K, mRg, p_inf, y, ht);
+        const Trial4 tr = trial4(K, mRg, pinf_rho, y, ht);
         ++n;
         const Verdict vd = judge64(K, Trial{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok});
         const double fac = f2d(vd.fac);
