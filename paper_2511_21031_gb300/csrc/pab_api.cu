@@ -47,6 +47,9 @@ struct pab_s {
 
 namespace {
 
+// Sub-step size of fixed mode (0 in adaptive mode).
+double sub_step(const pab::StepConst &K, double dt) { return K.n_fixed > 0 ? dt / (double)K.n_fixed : 0.0; }
+
 pab_status fail(pab_t *h, pab_status s, const char *fmt, ...)
 {
     if (h) {
@@ -493,6 +496,7 @@ pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_d
     a.p_inf = p_inf_dev;
     a.nb = nb_dev;
     a.dt = dt;
+    a.dt_sub = sub_step(h->K, dt);
     a.R = h->R;
     a.V = h->V;
     a.h = h->h;
@@ -814,6 +818,7 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
     a.p_inf = p_inf_dev;
     a.nb = nb_dev;
     a.dt = dt;
+    a.dt_sub = sub_step(K, dt);
     a.R = R_dev;
     a.V = Rdot_dev;
     a.h = h_dev;

@@ -47,6 +47,7 @@ struct SlotDesc {
     float *h;
     double *out;
     double dt;
+    double dt_sub;       // dt / n_fixed in fixed mode (formed on the host)
     long long C;
     long long n_tiles;
     int B;
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(512)
                 int na = 0, nd = 0;
                 GasBase g;
                 g.reset();
-                const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, R, V, hc, na, nd, g);
+                const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
                 d.R[k] = R;  // unchanged when the input was not finite
                 d.V[k] = V;
                 d.h[k] = hc;
@@ -659,6 +660,7 @@ pab_status pab_batch_bind(pab_batch_t *b, int32_t slot, const double *p_inf_dev,
     d.nb = nb_dev;
     d.out = moments_dev;
     d.dt = dt;
+    d.dt_sub = b->K_host[slot].n_fixed > 0 ? dt / (double)b->K_host[slot].n_fixed : 0.0;
     d.active = 1;
     return PAB_OK;
 }

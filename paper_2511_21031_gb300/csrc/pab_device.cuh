@@ -338,9 +338,11 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
 // the trial's three right-hand sides in FP32 (deviation form) on increments
 // k_j = h f(stage j) from the accepted state:
 //   y3 - y = (k1 + k2)/6 + 2/3 k3,   y3 - z = (2 k3 - k1 - k2)/3.
-// FP64 holds the state, the embedded error estimate (the k's promoted and
-// combined in FP64), its norm and the accept decision, and the controller's
-// time bookkeeping (t, dt - t, landing on dt).  The growth factor is formed in
+// FP64 holds the state (inside the loop the radius as its offset R - R0 from
+// the bin's equilibrium, so the FP32 image needs no subtraction per step), the
+// embedded error estimate (exact parts combined in FP64), its norm and the
+// accept decision, and the controller's time bookkeeping (the time left of
+// the flow step, counted down, and landing on dt).  The growth factor is formed in
 // FP32: the proposal it scales is stored in FP32 between calls anyway.  The
 // FP32 images of the state (xi = R - R0, Rdot) are refreshed only when a trial
 // is accepted.  Bins near collapse (R < r_collapse R0 or |Rdot| > v_collapse)
@@ -354,10 +356,11 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
     double h = f2d(hc);
     if (!gt0(h) || !le(h, dt))
         h = dt;
-    double t = 0.0;
+    double rem = dt;  // time left of the flow step
     uint32_t flags = 0;
     int n = 0;
-    xi = d2f(R - bc.R0);
+    double xi64 = R - bc.R0;  // the radius offset is the FP64 state inside the loop
+    xi = d2f(xi64);
     v = d2f(V);
     const float xi_collapse = (K.r_collapsef - 1.0f) * bc.R0f;
     for (;;) {
@@ -365,7 +368,6 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             flags |= PAB_FLAG_STEP_LIMIT;
             break;
         }
-        const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
         double err, nR = 0.0, nV = 0.0;
@@ -375,7 +377,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             GasBase g;
             g.reset();
             const double B0 = (K.pv - p_inf) * K.inv_rho;
-            const Trial tr = trial64(K, bc, B0, R, V, ht, g);
+            const Trial tr = trial64(K, bc, B0, bc.R0 + xi64, V, ht, g);
             ++n64;
             err = error_norm(K, tr);
             ok = tr.ok;
@@ -409,25 +411,26 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
         const float fac = growth_factor(K, d2f(err), ok);
         if (ok && le(err, K.tol)) {
             if (full64) {
-                R = nR;
+                xi64 = nR - bc.R0;
                 V = nV;
             } else {
-                R += f2d(d3R);
+                xi64 += f2d(d3R);
                 V += f2d(d3V);
             }
-            xi = d2f(R - bc.R0);
+            xi = d2f(xi64);
             v = d2f(V);
             if (last) {
                 const bool clipped = !le(h, rem);
                 h = (clipped && fac >= 1.0f) ? h : ht * f2d(fac);
                 break;
             }
-            t += ht;
+            rem -= ht;
             h = ht * f2d(fac);
         } else {
             h = ht * f2d(fac);
         }
     }
+    R = bc.R0 + xi64;
     hc = d2f(h);
     n_att = n;
     return flags;
@@ -435,11 +438,12 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
 
 // Fixed mode: n equal trials of dt/n, no error estimate (MIXED: FP64 trials
 // only for bins near collapse, as in the adaptive mode).
+// h = dt / n_fixed comes from the host (a division here would be hoisted out
+// of the bin loop and run in every thread, adaptive mode included).
 template <bool MIXED>
 __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst &bc, double p_inf,
-                                              float A, double dt, double &R, double &V, GasBase &g)
+                                              float A, double h, double &R, double &V, GasBase &g)
 {
-    const double h = dt / (double)K.n_fixed;
     const double B0 = (K.pv - p_inf) * K.inv_rho;
     for (int i = 0; i < K.n_fixed; ++i) {
         Trial tr;
@@ -458,8 +462,8 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
 // ---------------------------------------------------------------------------
 template <bool MIXED>
 __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinConst &bc, double p_inf,
-                                                bool p_ok, double dt, double &R, double &V, float &hc,
-                                                int &na, int &n64, GasBase &g)
+                                                bool p_ok, double dt, double dt_sub, double &R, double &V,
+                                                float &hc, int &na, int &n64, GasBase &g)
 {
     na = 0;
     n64 = 0;
@@ -468,7 +472,7 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
     uint32_t fl = 0;
     const float A = MIXED ? bc.dpeqf + d2f(K.p0 - p_inf) : 0.0f;
     if (K.n_fixed > 0) {
-        advance_fixed<MIXED>(K, bc, p_inf, A, dt, R, V, g);
+        advance_fixed<MIXED>(K, bc, p_inf, A, dt_sub, R, V, g);
         na = K.n_fixed;
     } else if (MIXED) {
         float xi, v;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256)
         int nd = 0;
         GasBase g;
         g.reset();
-        fl = advance_bin<false>(K, bc, p_inf, isfinite(p_inf), dt, r, v, hc, na, nd, g);
+        fl = advance_bin<false>(K, bc, p_inf, isfinite(p_inf), dt, 0.0, r, v, hc, na, nd, g);  // adaptive
         R[n] = r;  // unchanged when the input was not finite
         V[n] = v;
         h[n] = hc;

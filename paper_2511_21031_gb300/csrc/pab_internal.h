@@ -101,6 +101,7 @@ struct StepArgs {
     int32_t *attempts;     // [B][C] or nullptr
     double *out;           // [7][C] or nullptr
     Counters *counters;
+    double dt_sub = 0.0;   // dt / n_fixed in fixed mode (formed on the host)
     double *pb = nullptr;  // [B][C] bubble pressure (PAB_GAS_TRANSFER)
     double *mv = nullptr;  // [B][C] vapour mass (PAB_GAS_TRANSFER)
 };

@@ -113,12 +113,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                 fl |= PAB_FLAG_SUPERSONIC;
             a.R[k] = R;
             a.V[k] = V;
-            if (a.out) {
-                if (!isfinite(xi) || !isfinite(v))
-                    accumulate<MIXED>(K, bc, R, V, acc, g);
-                else
-                    accumulate_mixed<MIXED>(K, bc, R, xi, v, acc);
-            }
+            // a finite state has finite FP32 images (|R - R0| and |Rdot| are far below the
+            // FP32 range) and a non-finite one gives NaN moments either way
+            if (a.out)
+                accumulate_mixed<MIXED>(K, bc, R, xi, v, acc);
             if (a.attempts)
                 a.attempts[k] = na;
             fl_or |= fl;
@@ -128,7 +126,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         } else {
             const float A = MIXED ? bc.dpeqf + dp_cell : 0.0f;
             if (K.n_fixed > 0) {
-                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt, R, V, g);
+                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt_sub, R, V, g);
                 na = K.n_fixed;
             } else {
                 float hc = a.h[k];

@@ -29,7 +29,7 @@ struct Trial4 {
 __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc)
 {
     const double V0 = (4.0 / 3.0 * kPi) * bc.R0 * bc.R0 * bc.R0;
-    return (K.p0 + K.two_sigma * bc.invR0 - K.pv) * V0 / K.tr_Tw;
+    return (K.p0 + K.two_sigma * bc.invR0 - K.pv) * V0 * (K.tr_Rg * K.tr_inv_RgTw);  // ... / T_w
 }
 
 // dp_b/dt and dm_v/dt (Ando's pressure equation and Eq. massVaporRate with
@@ -104,13 +104,12 @@ __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double 
 // The controller of advance_adaptive (or n equal sub-steps in fixed mode);
 // the error norm reads R and Rdot.
 __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, double p_inf, double dt,
-                                             State4 &y, float &hc, int &n_att)
+                                             double dt_sub, State4 &y, float &hc, int &n_att)
 {
     const double pinf_rho = p_inf * K.inv_rho;
     if (K.n_fixed > 0) {
-        const double hf = dt / (double)K.n_fixed;
         for (int i = 0; i < K.n_fixed; ++i)
-            y = trial4(K, mRg, pinf_rho, y, hf).y;
+            y = trial4(K, mRg, pinf_rho, y, dt_sub).y;
         n_att = K.n_fixed;
         return 0;
     }
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             fl = PAB_FLAG_NONFINITE;
         } else {
             float hc = a.h[k];
-            fl = advance4(K, gas_mRg(K, bc), p_inf, a.dt, y, hc, na);
+            fl = advance4(K, gas_mRg(K, bc), p_inf, a.dt, a.dt_sub, y, hc, na);
             if (K.n_fixed == 0)
                 a.h[k] = hc;
             if (!finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv))
