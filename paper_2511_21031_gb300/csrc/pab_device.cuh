@@ -402,7 +402,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const float R3f = bc.R0f + (xi + d3R);
             const float rR = 1.0f / (3.0f * fabsf(R3f));
             const float rV = 1.0f / (3.0f * fmaxf(fabsf(v + d3V), K.v_floorf));
-            err = max_nn(fabs(eR) * f2d(rR), fabs(eV) * f2d(rV));
+            err = max_nn(abs_nn(eR) * f2d(rR), abs_nn(eV) * f2d(rV));
             ok = (bc.R0f + (xi + k1R) > 0.0f) && (bc.R0f + (xi + e2R) > 0.0f) && (R3f > 0.0f)
               && isfinite(a1 + a2 + a3);
             full64 = false;
