@@ -10,9 +10,11 @@
 //                      separable: the warp evaluates the 3 x (2m+1) one-
 //                      dimensional factors once (for stencil half-widths m up to
 //                      24 cells; wider kernels evaluate every point), then its
-//                      lanes walk the (2m+1)^3 stencil cube, keep the cells with
-//                      d/h < 3 and add V delta and Vdot delta with FP64 atomics
-//                      (nearby bubbles overlap, Listing 1's "atomic update").
+//                      lanes walk the (2m+1)^3 stencil cube in FP32, queue the
+//                      cells with d/h < 3 (about a sixth of the cube) and add
+//                      V delta and Vdot delta for 32 of them at a time with FP64
+//                      atomics (nearby bubbles overlap, Listing 1's "atomic
+//                      update").
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -85,6 +87,21 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Whether stencil point (oi, oj, ok) of the cached factors lies inside the
+// truncated kernel: FP32 sum of the squared offsets against 9 h^2, and within
+// 1e-5 of the cut the FP64 decision d/h < 3.
+__device__ __forceinline__ bool smear_inside(const double (*sq)[kSide], const float (*sqf)[kSide], int oi,
+                                             int oj, int ok, float lim2f, double h)
+{
+    const float d2f = sqf[0][oi] + sqf[1][oj] + sqf[2][ok];
+    bool inside = d2f < lim2f;
+    if (fabsf(d2f - lim2f) <= 1e-5f * lim2f) {
+        const double d2 = sq[0][oi] + sq[1][oj] + sq[2][ok];
+        inside = sqrt(d2) / h < 3.0;
+    }
+    return inside;
+}
+
 __global__ void __launch_bounds__(kSmearWarps * 32)
     el_smear_kernel(long long N, const double *__restrict__ px, const double *__restrict__ py,
                     const double *__restrict__ pz, const double *__restrict__ R,
@@ -97,8 +114,11 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
     __shared__ double fac[kSmearWarps][3][kSide];
     __shared__ double sq[kSmearWarps][3][kSide];
     __shared__ float sqf[kSmearWarps][3][kSide];
+    // inside points waiting for a full warp (ring of 64 stencil indices per warp)
+    __shared__ int ring[kSmearWarps][64];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const double norm = 15.749609945722419;  // (2 pi)^{3/2}
     for (long long n = (long long)blockIdx.x * kSmearWarps + warp; n < N;
          n += (long long)gridDim.x * kSmearWarps) {
@@ -109,11 +129,13 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
         const bool cached = m <= kCacheHalf;
         const double x0 = px[n], y0 = py[n], z0 = pz[n];
         const int bx = (int)floor(x0 / dx) - m, by = (int)floor(y0 / dx) - m, bz = (int)floor(z0 / dx) - m;
-        const double inv2h2 = 1.0 / (2.0 * h * h);
+        const double inv2h2 = rcp64(2.0 * h * h);
         const double Vb = 4.0 / 3.0 * 3.14159265358979323846 * r * r * r;
         const double Vd = 4.0 * 3.14159265358979323846 * r * r * V[n];
-        const double amp = Vb / (h * h * h * norm);  // V times the kernel's normalisation
-        const double rate = Vd / Vb;                  // alpha_dot / alpha of this bubble
+        const double amp = Vb * rcp64(h * h * h * norm);  // V times the kernel's normalisation
+        const double rate = Vd * rcp64(Vb);                // alpha_dot / alpha of this bubble
+        const double lim2 = 9.0 * h * h;
+        const long long count = (long long)side * side * side;
         if (cached) {
             for (int t = lane; t < 3 * side; t += 32) {
                 const int a = t / side, o = t % side;
@@ -126,40 +148,61 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                 const double f = exp(-c2 * inv2h2);
                 fac[warp][a][o] = a == 0 ? f * amp : f;
             }
-        }
-        __syncwarp();
-        const double lim2 = 9.0 * h * h;
-        const float lim2f = (float)lim2;
-        const long long count = (long long)side * side * side;
-        for (long long t = lane; t < count; t += 32) {
-            const int oi = (int)(t % side), oj = (int)((t / side) % side), ok = (int)(t / ((long long)side * side));
-            const int i = bx + oi, j = by + oj, k = bz + ok;
-            if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz)
-                continue;
-            double a;
-            if (cached) {
-                const float d2f = sqf[warp][0][oi] + sqf[warp][1][oj] + sqf[warp][2][ok];
-                bool inside = d2f < lim2f;
-                if (fabsf(d2f - lim2f) <= 1e-5f * lim2f) {  // near the cut: decide as d/h < 3
-                    const double d2 = sq[warp][0][oi] + sq[warp][1][oj] + sq[warp][2][ok];
-                    inside = sqrt(d2) / h < 3.0;
+            __syncwarp();
+            const float lim2f = (float)lim2;
+            // the lanes test 32 stencil points at a time; the inside ones (about 16 % of the
+            // cube) queue up, and every 32 of them are added by the whole warp at once
+            int queued = 0, tail = 0;
+            for (long long base = 0; base < count; base += 32) {
+                const long long t = base + lane;
+                bool in = false;
+                if (t < count) {
+                    const int oi = (int)(t % side), oj = (int)((t / side) % side),
+                              ok = (int)(t / ((long long)side * side));
+                    const int i = bx + oi, j = by + oj, k = bz + ok;
+                    in = i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz &&
+                         smear_inside(sq[warp], sqf[warp], oi, oj, ok, lim2f, h);
                 }
-                if (!inside)
+                const unsigned mask = __ballot_sync(0xffffffffu, in);
+                if (in)
+                    ring[warp][(tail + queued + __popc(mask & lt_mask)) & 63] = (int)t;
+                queued += __popc(mask);
+                __syncwarp();
+                const bool flush_all = base + 32 >= count;
+                while (queued >= 32 || (flush_all && queued > 0)) {
+                    if (lane < queued) {
+                        const int tq = ring[warp][(tail + lane) & 63];
+                        const int oi = tq % side, oj = (tq / side) % side, ok = tq / (side * side);
+                        const double a = fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok];
+                        const long long c = ((long long)(bz + ok) * ny + (by + oj)) * nx + (bx + oi);
+                        atomicAdd(&alpha[c], a);
+                        if (alpha_dot)
+                            atomicAdd(&alpha_dot[c], a * rate);
+                    }
+                    const int done = queued < 32 ? queued : 32;
+                    tail = (tail + done) & 63;
+                    queued -= done;
+                    __syncwarp();
+                }
+            }
+        } else {
+            for (long long t = lane; t < count; t += 32) {
+                const int oi = (int)(t % side), oj = (int)((t / side) % side), ok = (int)(t / ((long long)side * side));
+                const int i = bx + oi, j = by + oj, k = bz + ok;
+                if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz)
                     continue;
-                a = fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok];
-            } else {
                 const double cx = ((double)i + 0.5) * dx - x0;
                 const double cy = ((double)j + 0.5) * dx - y0;
                 const double cz = ((double)k + 0.5) * dx - z0;
                 const double d2 = cx * cx + cy * cy + cz * cz;
                 if (!(sqrt(d2) / h < 3.0))
                     continue;
-                a = amp * exp(-d2 * inv2h2);
+                const double a = amp * exp(-d2 * inv2h2);
+                const long long c = ((long long)k * ny + j) * nx + i;
+                atomicAdd(&alpha[c], a);
+                if (alpha_dot)
+                    atomicAdd(&alpha_dot[c], a * rate);
             }
-            const long long c = ((long long)k * ny + j) * nx + i;
-            atomicAdd(&alpha[c], a);
-            if (alpha_dot)
-                atomicAdd(&alpha_dot[c], a * rate);
         }
         __syncwarp();
     }
