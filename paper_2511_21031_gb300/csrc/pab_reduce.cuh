@@ -127,7 +127,7 @@ __device__ __forceinline__ void flush_counters(uint32_t fl_or, uint32_t n_flag, 
 __host__ __device__ inline int clamp_warps(int w, int B)
 {
     if (w <= 0)
-        w = 8;
+        w = kDefaultWarps;
     if (w > kMaxWarps)
         w = kMaxWarps;
     if (w > B)
