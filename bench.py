@@ -402,7 +402,8 @@ def _bench_batched(args, stream, dev, n_instances=512):
             "fp64_trial_fraction": n64 / max(1, n_att), "status_flags": flags,
             "launch": {"block_warps": tune["block_warps"], "ctas_per_sm": tune["ctas_per_sm"],
                        "bins_per_grab": tune["bins_per_grab"], "autotuned": True,
-                       "cached": tune.get("cached", False)},
+                       "cached": tune.get("cached", False), "candidates": tune.get("candidates"),
+                       "sample_best_ms": tune.get("ms"), "sample_worst_ms": tune.get("worst_ms")},
             "warmup_attempts": attempts0}
 
 

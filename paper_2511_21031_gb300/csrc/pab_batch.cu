@@ -143,14 +143,20 @@ __global__ void __launch_bounds__(kOrderThreads)
 // Persistent batch kernel.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
-__global__ void __launch_bounds__(512)
+// 64 registers (512 threads x 2 CTAs): twice the resident warps of the
+// unbounded build for some spills.
+__global__ void __launch_bounds__(512, 2)
     batch_kernel(const SlotDesc *__restrict__ slots, const int *__restrict__ order,
                  const long long *__restrict__ start, Queue *q, SlotCounters *cnt,
                  int bins_per_grab, int max_bins)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     StepConst &K = *reinterpret_cast<StepConst *>(smem);
-    double *terms = reinterpret_cast<double *>(smem + const_bytes());  // [4][max_bins][32]
+    // per-bin quadrature terms in bin order: [max_bins][32] FP64 w R^3, then the other
+    // three as [3][max_bins][32], FP32 in MIXED (their sums are FP32 there) and FP64 otherwise
+    double *terms = reinterpret_cast<double *>(smem + const_bytes());
+    float *terms_f = reinterpret_cast<float *>(terms + (size_t)max_bins * kTile);
+    double *terms_d = terms + (size_t)max_bins * kTile;
     __shared__ long long s_item;
     __shared__ int s_j;
     __shared__ int s_next;
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(512)
         const long long c = tile * kTile + lane;
         const bool valid = c < d.C;
         const double p_inf = valid ? d.p_inf[c] : K.p0;
-        const bool p_ok = isfinite(p_inf);
+        const bool p_ok = finite64(p_inf);
         uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
 
         for (;;) {
@@ -229,10 +235,18 @@ __global__ void __launch_bounds__(512)
                 n_att += na;
                 n64 += nd;
                 if (d.out) {
-                    double t[4];
-                    quad_terms<MIXED>(K, bc, R, V, t, g);
-                    for (int m = 0; m < 4; ++m)
-                        terms[((size_t)m * max_bins + b) * kTile + lane] = t[m];
+                    if (MIXED) {
+                        float tf[3];
+                        terms[(size_t)b * kTile + lane] = quad_terms_mixed(K, bc, R, V, tf);
+                        for (int m = 0; m < 3; ++m)
+                            terms_f[((size_t)m * max_bins + b) * kTile + lane] = tf[m];
+                    } else {
+                        double t[4];
+                        quad_terms64(K, bc, R, V, t, g);
+                        terms[(size_t)b * kTile + lane] = t[0];
+                        for (int m = 0; m < 3; ++m)
+                            terms_d[((size_t)m * max_bins + b) * kTile + lane] = t[m + 1];
+                    }
                 }
             }
         }
@@ -249,18 +263,27 @@ __global__ void __launch_bounds__(512)
         __syncthreads();
         if (warp == 0 && d.out && valid) {
             double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
+            float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
             for (int b = 0; b < d.B; ++b) {
-                const double x = terms[((size_t)0 * max_bins + b) * kTile + lane];
+                const double x = terms[(size_t)b * kTile + lane];
                 if (MIXED) {
                     neumaier_add(m3, m3c, x);
+                    m2vf += terms_f[((size_t)0 * max_bins + b) * kTile + lane];
+                    m3pf += terms_f[((size_t)1 * max_bins + b) * kTile + lane];
+                    m3v2f += terms_f[((size_t)2 * max_bins + b) * kTile + lane];
                 } else {
                     m3 += x;
+                    m2v += terms_d[((size_t)0 * max_bins + b) * kTile + lane];
+                    m3p += terms_d[((size_t)1 * max_bins + b) * kTile + lane];
+                    m3v2 += terms_d[((size_t)2 * max_bins + b) * kTile + lane];
                 }
-                m2v += terms[((size_t)1 * max_bins + b) * kTile + lane];
-                m3p += terms[((size_t)2 * max_bins + b) * kTile + lane];
-                m3v2 += terms[((size_t)3 * max_bins + b) * kTile + lane];
             }
             m3 += m3c;
+            if (MIXED) {
+                m2v = f2d(m2vf);
+                m3p = fma(K.p0, m3, f2d(m3pf));  // p0 sum w R^3 + sum w R^3 (p_bw - p0)
+                m3v2 = f2d(m3v2f);
+            }
             const double nb = d.nb ? d.nb[c] : K.nb_default;
             const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
             const double inv_m3 = 1.0 / m3;
@@ -545,7 +568,9 @@ pab_status pab_batch_create(const pab_batch_config *cfg, void *stream, pab_batch
     if (e == cudaSuccess) {
         std::memset(b->desc_host, 0, sizeof(pab::SlotDesc) * ms);
         b->free_ranges[0] = cap;
-        b->smem_bytes = pab::const_bytes() + (size_t)4 * b->cfg.max_bins * pab::kTile * sizeof(double);
+        b->smem_bytes = pab::const_bytes() + (size_t)b->cfg.max_bins * pab::kTile * sizeof(double) +
+                        (size_t)3 * b->cfg.max_bins * pab::kTile *
+                            (cfg->precision == PAB_MIXED ? sizeof(float) : sizeof(double));
         e = cfg->precision == PAB_MIXED ? pab::set_smem_limit<true>(b->smem_bytes)
                                         : pab::set_smem_limit<false>(b->smem_bytes);
     }

@@ -123,30 +123,38 @@ __device__ __forceinline__ double wall_pressure_rho64(const StepConst &K, const 
 // (for the polytropic gas A = p0 - p_inf).  Each term is then accurate
 // relative to itself rather than to p0.
 // ---------------------------------------------------------------------------
+//
+// The FP32 arithmetic of the mixed trial is written with explicit roundings
+// (__fadd_rn, __fmul_rn, __fmaf_rn: never fused or split by the compiler), so
+// every kernel that inlines it computes the same bits whatever its register
+// budget; the divisions are IEEE (correctly rounded) divisions.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ float gas_dev32(const StepConst &K, const BinConst &bc, float u)
 {
-    return bc.pg0f * expm1f(-K.three_gammaf * log1pf(u));
+    return __fmul_rn(bc.pg0f, expm1f(__fmul_rn(-K.three_gammaf, log1pf(u))));
 }
 
 __device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc, float A, float xi,
                                          float V)
 {
-    const float R = bc.R0f + xi;
+    const float R = __fadd_rn(bc.R0f, xi);
     const float iR = 1.0f / R;
-    const float u = xi * bc.invR0f;
+    const float u = __fmul_rn(xi, bc.invR0f);
     float pgdev = 0.0f, pg = 0.0f;
     if (K.gas_mode == PAB_GAS_POLYTROPIC) {
         pgdev = gas_dev32(K, bc, u);
-        pg = bc.pg0f + pgdev;
+        pg = __fadd_rn(bc.pg0f, pgdev);
     }
-    const float VR = V * iR;
-    const float s = fmaf(K.four_muf, V, K.two_sigmaf);
-    const float dp = A + pgdev + (K.two_sigmaf * u - K.four_muf * V) * iR;
-    const float dpbw = (s * iR - K.three_gammaf * pg) * VR;
-    const float icV = V * K.inv_cf;
-    const float num = dp * K.inv_rhof * (1.0f + icV) + R * K.ic_rhof * dpbw
-                    - 1.5f * V * V * (1.0f - icV * (1.0f / 3.0f));
-    const float den = fmaf(R, 1.0f - icV, K.fmu_ic_rhof);
+    const float VR = __fmul_rn(V, iR);
+    const float s = __fmaf_rn(K.four_muf, V, K.two_sigmaf);                  // 2 sigma + 4 mu Rdot
+    const float st = __fmaf_rn(K.two_sigmaf, u, __fmul_rn(-K.four_muf, V));  // 2 sigma u - 4 mu Rdot
+    const float dp = __fmaf_rn(st, iR, __fadd_rn(A, pgdev));
+    const float dpbw = __fmul_rn(__fmaf_rn(s, iR, __fmul_rn(-K.three_gammaf, pg)), VR);
+    const float icV = __fmul_rn(V, K.inv_cf);
+    const float lin = __fmul_rn(__fmul_rn(dp, K.inv_rhof), __fadd_rn(1.0f, icV));
+    const float kin = __fmul_rn(__fmul_rn(1.5f, __fmul_rn(V, V)), __fmaf_rn(-1.0f / 3.0f, icV, 1.0f));
+    const float num = __fmaf_rn(__fmul_rn(R, K.ic_rhof), dpbw, __fsub_rn(lin, kin));
+    const float den = __fmaf_rn(R, __fsub_rn(1.0f, icV), K.fmu_ic_rhof);
     return num / den;
 }
 
@@ -190,39 +198,56 @@ __device__ __forceinline__ double embedded_diff(float k1, float k2, float k3)
 {
     float s, es, d, ed;
     two_sum(k1, k2, s, es);
-    two_sum(2.0f * k3, -s, d, ed);
+    two_sum(__fmul_rn(2.0f, k3), -s, d, ed);
     return f2d(d) + (f2d(ed) - f2d(es));
 }
 
-// The same trial with the three right-hand sides in FP32 on increments from
-// y: k_j = h f(stage j).  y3 - y = (k1 + k2)/6 + 2/3 k3 and the embedded
-// difference y3 - z = (2 k3 - k1 - k2)/3 is formed in FP64 from the k's, so
-// the error estimate suffers no FP32 cancellation.  The new state is y plus
-// the FP32 increment, added in FP64.
+// The three FP32 right-hand sides of one trial, on increments from the state
+// (xi = R - R0, v) with k_j = h f(stage j):
+//   stage 2 = y + k1,  stage 3 = y + (k1 + k2)/4,  y3 - y = (k1 + k2)/6 + 2/3 k3.
+// ok: both inner stage radii positive and every right-hand side finite.
+struct Incr32 {
+    float k1R, k2R, k3R, k1V, k2V, k3V;
+    float d3R, d3V;  // y3 - y
+    bool ok;
+};
+__device__ __forceinline__ Incr32 incr32(const StepConst &K, const BinConst &bc, float A, float xi,
+                                         float v, float hf)
+{
+    Incr32 t;
+    const float a1 = accel32(K, bc, A, xi, v);
+    t.k1R = __fmul_rn(hf, v);
+    t.k1V = __fmul_rn(hf, a1);
+    const float x1 = __fadd_rn(xi, t.k1R), v1 = __fadd_rn(v, t.k1V);
+    const float a2 = accel32(K, bc, A, x1, v1);
+    t.k2R = __fmul_rn(hf, v1);
+    t.k2V = __fmul_rn(hf, a2);
+    const float sR = __fadd_rn(t.k1R, t.k2R), sV = __fadd_rn(t.k1V, t.k2V);
+    const float x2 = __fmaf_rn(0.25f, sR, xi), v2 = __fmaf_rn(0.25f, sV, v);
+    const float a3 = accel32(K, bc, A, x2, v2);
+    t.k3R = __fmul_rn(hf, v2);
+    t.k3V = __fmul_rn(hf, a3);
+    t.d3R = __fmaf_rn(2.0f / 3.0f, t.k3R, __fmul_rn(1.0f / 6.0f, sR));
+    t.d3V = __fmaf_rn(2.0f / 3.0f, t.k3V, __fmul_rn(1.0f / 6.0f, sV));
+    t.ok = (__fadd_rn(bc.R0f, x1) > 0.0f) && (__fadd_rn(bc.R0f, x2) > 0.0f)
+        && isfinite(__fadd_rn(__fadd_rn(a1, a2), a3));
+    return t;
+}
+
+// The trial with the three right-hand sides in FP32.  The embedded difference
+// y3 - z = (2 k3 - k1 - k2)/3 is formed in FP64 from the k's, so the error
+// estimate suffers no FP32 cancellation.  The new state is y plus the FP32
+// increment, added in FP64.
 __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc, float A, double R,
                                          double V, double h)
 {
-    const float xi0 = d2f(R - bc.R0);
-    const float v0 = d2f(V);
-    const float hf = d2f(h);
-    const float a1 = accel32(K, bc, A, xi0, v0);
-    const float k1R = hf * v0, k1V = hf * a1;
-    const float v1 = v0 + k1V;
-    const float a2 = accel32(K, bc, A, xi0 + k1R, v1);
-    const float k2R = hf * v1, k2V = hf * a2;
-    const float e2R = 0.25f * (k1R + k2R), e2V = 0.25f * (k1V + k2V);
-    const float v2 = v0 + e2V;
-    const float a3 = accel32(K, bc, A, xi0 + e2R, v2);
-    const float k3R = hf * v2, k3V = hf * a3;
-    const float d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
-    const float d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
+    const Incr32 in = incr32(K, bc, A, d2f(R - bc.R0), d2f(V), d2f(h));
     Trial t;
-    t.R = R + f2d(d3R);
-    t.V = V + f2d(d3V);
-    t.eR = embedded_diff(k1R, k2R, k3R);
-    t.eV = embedded_diff(k1V, k2V, k3V);
-    const float r1 = bc.R0f + (xi0 + k1R), r2 = bc.R0f + (xi0 + e2R);
-    t.ok = (r1 > 0.0f) && (r2 > 0.0f) && gt0(t.R) && finite64(t.V) && isfinite(a1 + a2 + a3);
+    t.R = R + f2d(in.d3R);
+    t.V = V + f2d(in.d3V);
+    t.eR = embedded_diff(in.k1R, in.k2R, in.k3R);
+    t.eV = embedded_diff(in.k1V, in.k2V, in.k3V);
+    t.ok = in.ok && gt0(t.R) && finite64(t.V);
     return t;
 }
 
@@ -275,14 +300,11 @@ __device__ __forceinline__ Verdict judge64(const StepConst &K, const Trial &t)
 //   ends exactly at dt; accepted: t += h_try, proposal h_try * fac (on the
 //   last trial the unclipped h is kept when it was clipped and fac >= 1);
 //   rejected: h = h_try * fac; at most max_attempts trials.
-// MIXED selects the FP64 trial only where R < r_collapse R0 or
-// |Rdot| > v_collapse, else the FP32 trial.
+// FP64 trials throughout (the mixed mode has its own loop, advance_mixed).
 // ---------------------------------------------------------------------------
-template <bool MIXED>
 __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
-                                                     double p_inf, float A, double dt, double &R,
-                                                     double &V, float &hc, int &n_att, int &n64,
-                                                     GasBase &g)
+                                                     double p_inf, double dt, double &R, double &V,
+                                                     float &hc, int &n_att, GasBase &g)
 {
     const double B0 = (K.pv - p_inf) * K.inv_rho;
     double h = f2d(hc);
@@ -299,18 +321,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
         const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
-        Trial tr;
-        if (MIXED) {
-            const bool stiff = (R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse);
-            if (stiff) {
-                tr = trial64(K, bc, B0, R, V, ht, g);
-                ++n64;
-            } else {
-                tr = trial32(K, bc, A, R, V, ht);
-            }
-        } else {
-            tr = trial64(K, bc, B0, R, V, ht, g);
-        }
+        const Trial tr = trial64(K, bc, B0, R, V, ht, g);
         ++n;
         const Verdict vd = judge64(K, tr);
         const double fac = f2d(vd.fac);
@@ -385,26 +396,16 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             nV = tr.V;
             full64 = true;
         } else {
-            const float hf = d2f(ht);
-            const float a1 = accel32(K, bc, A, xi, v);
-            const float k1R = hf * v, k1V = hf * a1;
-            const float v1 = v + k1V;
-            const float a2 = accel32(K, bc, A, xi + k1R, v1);
-            const float k2R = hf * v1, k2V = hf * a2;
-            const float e2R = 0.25f * (k1R + k2R), e2V = 0.25f * (k1V + k2V);
-            const float v2 = v + e2V;
-            const float a3 = accel32(K, bc, A, xi + e2R, v2);
-            const float k3R = hf * v2, k3V = hf * a3;
-            d3R = (k1R + k2R) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3R;
-            d3V = (k1V + k2V) * (1.0f / 6.0f) + (2.0f / 3.0f) * k3V;
-            const double eR = embedded_diff(k1R, k2R, k3R);
-            const double eV = embedded_diff(k1V, k2V, k3V);
-            const float R3f = bc.R0f + (xi + d3R);
-            const float rR = 1.0f / (3.0f * fabsf(R3f));
-            const float rV = 1.0f / (3.0f * fmaxf(fabsf(v + d3V), K.v_floorf));
+            const Incr32 in = incr32(K, bc, A, xi, v, d2f(ht));
+            d3R = in.d3R;
+            d3V = in.d3V;
+            const double eR = embedded_diff(in.k1R, in.k2R, in.k3R);
+            const double eV = embedded_diff(in.k1V, in.k2V, in.k3V);
+            const float R3f = __fadd_rn(bc.R0f, __fadd_rn(xi, d3R));
+            const float rR = 1.0f / __fmul_rn(3.0f, fabsf(R3f));
+            const float rV = 1.0f / __fmul_rn(3.0f, fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf));
             err = max_nn(abs_nn(eR) * f2d(rR), abs_nn(eV) * f2d(rV));
-            ok = (bc.R0f + (xi + k1R) > 0.0f) && (bc.R0f + (xi + e2R) > 0.0f) && (R3f > 0.0f)
-              && isfinite(a1 + a2 + a3);
+            ok = in.ok && (R3f > 0.0f);
             full64 = false;
         }
         ++n;
@@ -478,7 +479,7 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
         float xi, v;
         fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64, xi, v);
     } else {
-        fl = advance_adaptive<false>(K, bc, p_inf, A, dt, R, V, hc, na, n64, g);
+        fl = advance_adaptive(K, bc, p_inf, dt, R, V, hc, na, g);
     }
     if (!finite64(R) || !finite64(V))
         fl |= PAB_FLAG_NONFINITE;
@@ -489,27 +490,38 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
     return fl;
 }
 
-// Quadrature terms of one bin at (R, Rdot): w R^3, w R^2 Rdot, w R^3 p_bw,
-// w R^3 Rdot^2 (the wall pressure in FP64, or in FP32 deviation form in MIXED).
-template <bool MIXED>
-__device__ __forceinline__ void quad_terms(const StepConst &K, const BinConst &bc, double R, double V,
-                                           double t[4], GasBase &g)
+// Quadrature terms of one bin at (R, Rdot), FP64: w R^3, w R^2 Rdot,
+// w R^3 p_bw, w R^3 Rdot^2.
+__device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
+                                             double t[4], GasBase &g)
 {
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
-    double pbw;
-    if (MIXED) {
-        const float xi = d2f(R - bc.R0);
-        const float u = xi * bc.invR0f;
-        const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-        pbw = K.p0 + f2d(bc.dpeqf + (pgdev + (K.two_sigmaf * u - K.four_muf * d2f(V)) / d2f(R)));
-    } else {
-        pbw = K.rho * wall_pressure_rho64(K, bc, R, V, g);
-    }
+    const double pbw = K.rho * wall_pressure_rho64(K, bc, R, V, g);
     t[0] = wr3;
     t[1] = wr2 * V;
     t[2] = wr3 * pbw;
     t[3] = wr3 * V * V;
+}
+
+// The same terms in mixed precision: w R^3 in FP64 (for the compensated alpha
+// sum), and in FP32 w R^2 Rdot, w R^3 (p_bw - p0) (the wall pressure in
+// deviation form; p0 sum w R^3 is added once per cell) and w R^3 Rdot^2.
+__device__ __forceinline__ double quad_terms_mixed(const StepConst &K, const BinConst &bc, double R,
+                                                   double V, float tf[3])
+{
+    const double wr2 = bc.w * R * R;
+    const double wr3 = wr2 * R;
+    const float xi = d2f(R - bc.R0);
+    const float u = xi * bc.invR0f;
+    const float Rf = bc.R0f + xi, Vf = d2f(V);
+    const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
+    const float dev = bc.dpeqf + pgdev + (K.two_sigmaf * u - K.four_muf * Vf) / Rf;
+    const float wr2f = d2f(wr2), wr3f = d2f(wr3);
+    tf[0] = wr2f * Vf;
+    tf[1] = wr3f * dev;
+    tf[2] = wr3f * Vf * Vf;
+    return wr3;
 }
 
 }  // namespace pab

@@ -130,10 +130,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                 na = K.n_fixed;
             } else {
                 float hc = a.h[k];
-                int nd = 0;
-                fl = advance_adaptive<false>(K, bc, p_inf, A, a.dt, R, V, hc, na, nd, g);
+                fl = advance_adaptive(K, bc, p_inf, a.dt, R, V, hc, na, g);
                 a.h[k] = hc;
-                n64 += nd;
             }
             if (!finite64(R) || !finite64(V))
                 fl |= PAB_FLAG_NONFINITE;
