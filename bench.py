@@ -45,16 +45,16 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel executes per trial
 # (one sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination,
-# error norm, controller) and per bin-step outside the trial loop (load, wall
+# error norm, controller) and per bin-step outside the trial loop (load, bubble
 # pressure and quadrature sums): least-squares fit of ncu's
 # smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over six launches
-# of the 64^3 x 31 grid with traced trial counts (residual 3e-4).
-FP64_FLOPS_PER_TRIAL = 162.5
-FP64_FLOPS_PER_BINSTEP = 48.8
+# of the 64^3 x 31 grid with traced trial counts (residual 5e-4).
+FP64_FLOPS_PER_TRIAL = 148.45
+FP64_FLOPS_PER_BINSTEP = 32.1
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
-# on the 64^3 x 31 grid, 283.5 MB / 8.13M bin-steps); scaled by bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 34.9
-FP64_PIPE_ACTIVE_NCU = 0.880
+# on the 64^3 x 31 grid, 295.3 MB / 8.13M bin-steps); scaled by bin-steps.
+FP64_DRAM_BYTES_PER_BINSTEP = 36.3
+FP64_PIPE_ACTIVE_NCU = 0.916
 
 
 def _dist():

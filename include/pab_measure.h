@@ -60,14 +60,16 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
  *                 6 (float)x (bit patterns, with subnormal float results
  *                 flushed to a signed zero; NaN for NaN), 7 the embedded
  *                 difference 2 k3 - (k1 + k2) of k1 = f, k2 = (float)x,
- *                 k3 = (float)y against FP64 within 4 ulp of its terms;
+ *                 k3 = (float)y against FP64 within 4 ulp of its terms,
+ *                 8 2|x| and 2s (s the subnormal or zero with the bits of |x|
+ *                 shifted right by 12) against the FP64 additions;
  *                 y_dev[i] must be a finite number >= +0.
- * f_dev [n] float; the others [n] double (cmp_dev [n] uint8), all on the device.
+ * f_dev [n] float; the others [n] double (cmp_dev [n] uint16), all on the device.
  * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.
  */
 pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, const double *y_dev,
                           double *f2d_dev, double *f2d_hw, double *rcp_dev, double *div_dev,
-                          double *seed_dev, uint8_t *cmp_dev, void *stream);
+                          double *seed_dev, uint16_t *cmp_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -223,7 +223,7 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
         b.dpeqf = (float)(peq - c->p0);
         b.invR0 = 1.0 / R0[i];
         b.A1 = pg0 / c->rho;
-        b.A2 = 3.0 * c->gamma * pg0 / c->rho * K->inv_c;
+        b.A3 = (1.0 - 3.0 * c->gamma) * pg0 / c->rho * K->inv_c;
         m3 += w[i] * R0[i] * R0[i] * R0[i];
     }
     K->nb_default = m3 > 0.0 ? c->alpha0 / (4.0 / 3.0 * M_PI * m3) : 0.0;
@@ -278,14 +278,17 @@ void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *
     const double lq = std::log(q);
     *J = (int)std::ceil(std::log(25.0) / lq);
     *inv_log2q = 1.0 / std::log2(q);
-    tab->resize((size_t)4 * (2 * *J + 1));
+    tab->resize((size_t)kGasTabStride * (2 * *J + 1));
     for (int j = -*J; j <= *J; ++j) {
         const double x = std::exp((double)j * lq);
-        double *e = tab->data() + 4 * (size_t)(j + *J);
+        double *e = tab->data() + kGasTabStride * (size_t)(j + *J);
         e[0] = x;
-        e[1] = 1.0 / x;
-        e[2] = std::pow(x, -a);
-        e[3] = 0.0;
+        // c_k = x^(-a) C(-a, k) x^(-k): the binomial series of (x + delta)^(-a) in delta
+        double ck = std::pow(x, -a);
+        for (int k = 0; k < kGasTabTerms; ++k) {
+            e[1 + k] = ck;
+            ck *= (-a - (double)k) / ((double)(k + 1) * x);
+        }
     }
 }
 

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(512, 2)
             d.out[2 * C + c] = m3;
             d.out[3 * C + c] = m2v;
             d.out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
-            d.out[5 * C + c] = m3p * inv_m3;
+            d.out[5 * C + c] = (MIXED ? m3p : K.rho * m3p) * inv_m3;  // FP64 terms are over rho
             d.out[6 * C + c] = m3v2 * inv_m3;
         }
         if (threadIdx.x == 0) {

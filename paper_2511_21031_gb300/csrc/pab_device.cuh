@@ -40,13 +40,15 @@ __device__ __forceinline__ double gas_series(const StepConst &K, double d)
 
 // G = (R0/R)^(3 gamma) for R > 0.
 //  - With a node table (a handle's gas_tab): x = R/R0 goes to the nearest node
-//    x_j = q^j (picked in FP32: log2(x)/log2(q) rounded), and G = T_j (1 + d)^(-3 gamma)
-//    with d = (x - x_j)/x_j, |d| < gas_dmax_tab (degree-6 series). A pure
-//    function of R: no exp or log while R/R0 stays within the table.
+//    x_j = q^j (picked in FP32: log2(x)/log2(q) rounded), and G is the node's
+//    binomial series in delta = x - x_j, sum_k c_k delta^k (degree 6,
+//    |delta| < x_j gas_dmax_tab). A pure function of R: no exp or log while R/R0
+//    stays within the table.
 //  - Otherwise (or outside the table): the radii of one step stay close to the
 //    last exact evaluation R_b in g, reached by the degree-11 series in
 //    d = (R - R_b)/R_b; farther away the value is exact, exp(-3 gamma log(R/R0)),
 //    and becomes the new base.
+static_assert(kGasTabStride == 8 && kGasTabTerms == 7, "gas table node layout");
 __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst &bc, double R,
                                              GasBase &g)
 {
@@ -54,10 +56,16 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
         const float xf = d2f(R) * bc.invR0f;
         const int j = __float2int_rn(__log2f(xf) * K.gas_inv_log2q);
         if (j >= -K.gas_J && j <= K.gas_J) {
-            const double2 *e = reinterpret_cast<const double2 *>(K.gas_tab) + 2 * (j + K.gas_J);
-            const double2 n0 = __ldg(e), n1 = __ldg(e + 1);  // {x_j, 1/x_j}, {T_j, 0}
-            const double d = fma(R, bc.invR0, -n0.x) * n0.y;
-            return n1.x * gas_series<kGasTabTerms>(K, d);
+            // {x_j, c_0}, {c_1, c_2}, {c_3, c_4}, {c_5, c_6}
+            const double2 *e = reinterpret_cast<const double2 *>(K.gas_tab) + 4 * (j + K.gas_J);
+            const double2 n0 = __ldg(e), n1 = __ldg(e + 1), n2 = __ldg(e + 2), n3 = __ldg(e + 3);
+            const double d = fma(R, bc.invR0, -n0.x);
+            double s = fma(n3.y, d, n3.x);
+            s = fma(s, d, n2.y);
+            s = fma(s, d, n2.x);
+            s = fma(s, d, n1.y);
+            s = fma(s, d, n1.x);
+            return fma(s, d, n0.y);
         }
     }
     const double d = (R - g.Rb) * g.invRb;
@@ -88,30 +96,32 @@ struct Trial {
 // over rho, the s/R terms of (p_bw - p_inf)(1 + Rdot/c)/rho and of
 // (R/(rho c)) d/dt p_bw add up to -s/(rho R), which leaves
 //   Rddot = (N0 R - s/rho) / (R den),
-//   N0 = (B0 + A1 G)(1 + Rdot/c) - Rdot (A2 G + Rdot (3/2 - Rdot/(2c))),
-// with B0 = (pv - p_inf)/rho per cell, A1 = p_g0/rho and A2 = 3 gamma p_g0/(rho c)
-// per bin: one reciprocal and no other division.  1/c = 0 gives Rayleigh-Plesset.
+//   N0 = P (1 + Rdot/c) - Rdot (3 gamma A1 G/c + Rdot (3/2 - Rdot/(2c))),  P = B0 + A1 G,
+// with B0 = (pv - p_inf)/rho per cell and A1 = p_g0/rho per bin.  Regrouped on
+// Rdot: N0 = P + Rdot (A3 G + B0/c - Rdot (3/2 - Rdot/(2c))) with the per-bin
+// A3 = (1 - 3 gamma) A1/c and the per-cell B0/c: one reciprocal and no other
+// division.  1/c = 0 gives Rayleigh-Plesset.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
-                                          double R, double V, GasBase &g)
+                                          double B0c, double R, double V, GasBase &g)
 {
     const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
     const double den = fma(R, fma(V, -K.inv_c, 1.0), K.fmu_ic_rho);
     const double inv = rcp64(R * den);
     const double P = fma(bc.A1, G, B0);
-    const double q = fma(V, fma(V, K.m05_inv_c, 1.5), bc.A2 * G);
-    const double N0 = fma(P, fma(V, K.inv_c, 1.0), -V * q);
+    const double t = fma(-V, fma(V, K.m05_inv_c, 1.5), fma(bc.A3, G, B0c));
+    const double N0 = fma(V, t, P);
     const double s_rho = fma(K.fmu_rho, V, K.tsig_rho);
     return fma(N0, R, -s_rho) * inv;
 }
 
-// Wall pressure over rho, p_bw/rho = pv/rho + A1 G - s/(rho R), in FP64 (for
-// the <R^3 p_bw> moment; the sums are scaled by rho once per cell).
-__device__ __forceinline__ double wall_pressure_rho64(const StepConst &K, const BinConst &bc,
-                                                      double R, double V, GasBase &g)
+// The bubble pressure over rho, p_b/rho = pv/rho + A1 G, FP64.  With it the
+// <R^3 p_bw> term needs no division: w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho.
+__device__ __forceinline__ double bubble_pressure_rho64(const StepConst &K, const BinConst &bc,
+                                                        double R, GasBase &g)
 {
     const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
-    return fma(-fma(K.fmu_rho, V, K.tsig_rho), rcp64(R), fma(bc.A1, G, K.pv_rho));
+    return fma(bc.A1, G, K.pv_rho);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,21 +179,23 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc,
 //   3 (y3 - z) = 2 k3 - (k1 + k2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
-                                         double R, double V, double h, GasBase &g)
+                                         double B0c, double R, double V, double h, GasBase &g)
 {
-    const double a1 = accel64(K, bc, B0, R, V, g);
+    const double a1 = accel64(K, bc, B0, B0c, R, V, g);
     const double k1R = h * V, k1V = h * a1;
     const double y1R = R + k1R, y1V = V + k1V;
-    const double a2 = accel64(K, bc, B0, y1R, y1V, g);
+    const double a2 = accel64(K, bc, B0, B0c, y1R, y1V, g);
     const double sR = fma(h, y1V, k1R), sV = fma(h, a2, k1V);   // k1 + k2
     const double y2R = fma(0.25, sR, R), y2V = fma(0.25, sV, V);
-    const double a3 = accel64(K, bc, B0, y2R, y2V, g);
-    const double k3R = h * y2V, k3V = h * a3;
+    const double a3 = accel64(K, bc, B0, B0c, y2R, y2V, g);
+    // 2 k3 = (2h) f(y2) with 2h exact; y3 = y + (k1 + k2)/6 + 2/3 k3 written as
+    // y + (k1 + k2)/2 + (2 k3 - (k1 + k2))/3
+    const double h2 = twice_nn(h);
     Trial t;
-    t.R = fma(1.0 / 6.0, sR, fma(2.0 / 3.0, k3R, R));
-    t.V = fma(1.0 / 6.0, sV, fma(2.0 / 3.0, k3V, V));
-    t.eR = fma(2.0, k3R, -sR);
-    t.eV = fma(2.0, k3V, -sV);
+    t.eR = fma(h2, y2V, -sR);
+    t.eV = fma(h2, a3, -sV);
+    t.R = fma(1.0 / 3.0, t.eR, fma(0.5, sR, R));
+    t.V = fma(1.0 / 3.0, t.eV, fma(0.5, sV, V));
     t.ok = gt0(y1R) && gt0(y2R) && gt0(t.R) && finite64(t.V);
     return t;
 }
@@ -307,6 +319,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
                                                      float &hc, int &n_att, GasBase &g)
 {
     const double B0 = (K.pv - p_inf) * K.inv_rho;
+    const double B0c = B0 * K.inv_c;
     double h = f2d(hc);
     if (!gt0(h) || !le(h, dt))
         h = dt;
@@ -321,7 +334,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
         const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
-        const Trial tr = trial64(K, bc, B0, R, V, ht, g);
+        const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g);
         ++n;
         const Verdict vd = judge64(K, tr);
         const double fac = f2d(vd.fac);
@@ -388,7 +401,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             GasBase g;
             g.reset();
             const double B0 = (K.pv - p_inf) * K.inv_rho;
-            const Trial tr = trial64(K, bc, B0, bc.R0 + xi64, V, ht, g);
+            const Trial tr = trial64(K, bc, B0, B0 * K.inv_c, bc.R0 + xi64, V, ht, g);
             ++n64;
             err = error_norm(K, tr);
             ok = tr.ok;
@@ -446,12 +459,13 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
                                               float A, double h, double &R, double &V, GasBase &g)
 {
     const double B0 = (K.pv - p_inf) * K.inv_rho;
+    const double B0c = B0 * K.inv_c;
     for (int i = 0; i < K.n_fixed; ++i) {
         Trial tr;
         if (MIXED && !((R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse)))
             tr = trial32(K, bc, A, R, V, h);
         else
-            tr = trial64(K, bc, B0, R, V, h, g);
+            tr = trial64(K, bc, B0, B0c, R, V, h, g);
         R = tr.R;
         V = tr.V;
     }
@@ -491,16 +505,15 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 }
 
 // Quadrature terms of one bin at (R, Rdot), FP64: w R^3, w R^2 Rdot,
-// w R^3 p_bw, w R^3 Rdot^2.
+// w R^3 p_bw / rho (= w R^3 p_b/rho - w R^2 s/rho), w R^3 Rdot^2.
 __device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
                                              double t[4], GasBase &g)
 {
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
-    const double pbw = K.rho * wall_pressure_rho64(K, bc, R, V, g);
     t[0] = wr3;
     t[1] = wr2 * V;
-    t[2] = wr3 * pbw;
+    t[2] = fma(wr3, bubble_pressure_rho64(K, bc, R, g), -wr2 * fma(K.fmu_rho, V, K.tsig_rho));
     t[3] = wr3 * V * V;
 }
 

@@ -21,7 +21,7 @@ struct BinConst {
     double w;      // quadrature weight w_i (sums to one over the bins)
     double invR0;  // 1/R0
     double A1;     // pg0 / rho
-    double A2;     // 3 gamma pg0 / (rho c)
+    double A3;     // (1 - 3 gamma) pg0 / (rho c)
     float R0f;     // R0 in FP32 (mixed path)
     float invR0f;  // 1/R0 in FP32
     float pg0f;    // pg0 in FP32
@@ -35,6 +35,7 @@ constexpr int kDefaultWarps = 4;
 
 constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
 constexpr int kGasTabTerms = 7;  // degree 6 around the nodes of a gas table
+constexpr int kGasTabStride = kGasTabTerms + 1;  // doubles per node: x_j and the coefficients
 
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
 // so warp-uniform reads come from the constant bank.
@@ -73,8 +74,10 @@ struct StepConst {
     double gas_c[kGasTerms];
     double gas_dmax;
     double gas_dmax_tab;  // the same bound for the degree kGasTabTerms-1 of the table path
-    // optional table of nodes x_j = q^j, j = -gas_J..gas_J, as {x_j, 1/x_j, x_j^(-3 gamma), 0}:
-    // (R/R0)^(-3 gamma) = T_j (1 + d)^(-3 gamma) with d = (R/R0 - x_j)/x_j (nullptr: no table)
+    // optional table of nodes x_j = q^j, j = -gas_J..gas_J, kGasTabStride doubles each,
+    // {x_j, c_0 .. c_6}: (R/R0)^(-3 gamma) = sum_k c_k (R/R0 - x_j)^k with
+    // c_k = x_j^(-3 gamma) C(-3 gamma, k) x_j^(-k), the binomial series about the node
+    // (nullptr: no table)
     const double *gas_tab;
     float gas_inv_log2q;  // 1/log2(q)
     int32_t gas_J;
@@ -117,7 +120,8 @@ pab_status validate_config(const pab_config *c, char *msg, size_t n);
 bool bin_table(const pab_config *c, double *R0, double *w);
 void make_const(const pab_config *c, const double *R0, const double *w, StepConst *K);
 BinConst make_bin(const pab_config *c, double R0, double w);  // constants of one radius
-// Host values of the gas-term table for a = 3 gamma (4 * (2 J + 1) doubles) and its spacing.
+// Host values of the gas-term table for a = 3 gamma (kGasTabStride * (2 J + 1) doubles) and its
+// spacing.
 void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *inv_log2q);
 
 // Launchers (pab_kernels.cu).  Return the launch error.

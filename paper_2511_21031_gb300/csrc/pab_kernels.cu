@@ -39,11 +39,12 @@ __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &b
         acc.m2vf = fmaf(d2f(wr2), Vf, acc.m2vf);
         acc.m3v2f = fmaf(wr3f * Vf, Vf, acc.m3v2f);
     } else {
-        const double pbw_rho = wall_pressure_rho64(K, bc, R, V, g);
+        // w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho, s = 4 mu Rdot + 2 sigma
         acc.add_m3(wr3);
-        acc.m2v += wr2 * V;
-        acc.m3p += wr3 * pbw_rho;
-        acc.m3v2 += wr3 * V * V;
+        acc.m2v = fma(wr2, V, acc.m2v);
+        acc.m3p = fma(wr3, bubble_pressure_rho64(K, bc, R, g), acc.m3p);
+        acc.m3p = fma(-wr2, fma(K.fmu_rho, V, K.tsig_rho), acc.m3p);
+        acc.m3v2 = fma(wr3 * V, V, acc.m3v2);
     }
 }
 

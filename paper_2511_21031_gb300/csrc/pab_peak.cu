@@ -50,7 +50,7 @@ __global__ void math_check_kernel(const __grid_constant__ pab::StepConst K, cons
 
 __global__ void bits_check_kernel(long long n, const float *f, const double *x, const double *y,
                                   double *f2d, double *f2d_hw, double *rcp, double *dv, double *seed,
-                                  uint8_t *cmp)
+                                  uint16_t *cmp)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -76,6 +76,11 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
             if (fabsf(hw) < FLT_MIN)
                 hw = copysignf(0.0f, hw);
             bad |= (__float_as_uint(pab::d2f(xi)) != __float_as_uint(hw)) << 6;
+            // 2x on the integer units, for |x| and for a subnormal made from its bits
+            const double sub = pab::from_bits(pab::ubits(ax) >> 12);
+            if (ax < 0x1p1023)
+                bad |= (pab::ubits(pab::twice_nn(ax)) != pab::ubits(__dadd_rn(ax, ax))) << 8;
+            bad |= (pab::ubits(pab::twice_nn(sub)) != pab::ubits(__dadd_rn(sub, sub))) << 8;
         } else {
             bad |= (!isnan(pab::d2f(xi))) << 6;
         }
@@ -90,7 +95,7 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
                                                     fabs((double)k2));
             bad |= (!(fabs(got - ref) <= tol)) << 7;
         }
-        cmp[i] = (uint8_t)bad;
+        cmp[i] = (uint16_t)bad;
     }
 }
 
@@ -99,7 +104,7 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
 extern "C" pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev,
                                      const double *y_dev, double *f2d_dev, double *f2d_hw,
                                      double *rcp_dev, double *div_dev, double *seed_dev,
-                                     uint8_t *cmp_dev, void *stream)
+                                     uint16_t *cmp_dev, void *stream)
 {
     if (n < 0 || (n > 0 && (!f_dev || !x_dev || !y_dev || !f2d_dev || !f2d_hw || !rcp_dev ||
                             !div_dev || !seed_dev || !cmp_dev)))

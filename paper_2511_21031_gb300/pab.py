@@ -239,7 +239,7 @@ def pab_bits_check(f, x, y, stream=None):
     """Library helpers against the hardware: dict of f2d, f2d_hw, rcp, div, seed, cmp."""
     import torch
     out = {k: torch.empty_like(x) for k in ("f2d", "f2d_hw", "rcp", "div", "seed")}
-    out["cmp"] = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    out["cmp"] = torch.empty(x.shape, dtype=torch.int16, device=x.device)  # uint16 bit masks
     st = load().pab_bits_check(x.numel(), f.data_ptr(), x.data_ptr(), y.data_ptr(),
                                out["f2d"].data_ptr(), out["f2d_hw"].data_ptr(),
                                out["rcp"].data_ptr(), out["div"].data_ptr(), out["seed"].data_ptr(),
