@@ -62,7 +62,10 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
  *                 difference 2 k3 - (k1 + k2) of k1 = f, k2 = (float)x,
  *                 k3 = (float)y against FP64 within 4 ulp of its terms,
  *                 8 2|x| and 2s (s the subnormal or zero with the bits of |x|
- *                 shifted right by 12) against the FP64 additions;
+ *                 shifted right by 12) against the FP64 additions, 9 the
+ *                 library's FP32 quotient f / (float)x and 10 its reciprocal
+ *                 1 / (float)x, each within an ulp of the IEEE operation
+ *                 where operands and result lie between 2^-100 and 2^100;
  *                 y_dev[i] must be a finite number >= +0.
  * f_dev [n] float; the others [n] double (cmp_dev [n] uint16), all on the device.
  * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.

@@ -195,6 +195,7 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->two_sigmaf = (float)K->two_sigma;
     K->three_gammaf = (float)K->three_gamma;
     K->ic_rhof = (float)K->ic_rho;
+    K->tg_ic_rhof = (float)(K->three_gamma * K->ic_rho);
     K->fmu_ic_rhof = (float)K->fmu_ic_rho;
     K->v_floorf = (float)K->v_floor;
     K->cbrt_tolf = (float)K->cbrt_tol;

@@ -83,6 +83,7 @@ struct StepConst {
     int32_t gas_J;
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
     float cbrt_tolf, v_collapsef, r_collapsef, cf;
+    float tg_ic_rhof;     // 3 gamma (1/c)/rho
     BinConst bins[PAB_MAX_BINS];
 };
 

@@ -32,7 +32,7 @@ __device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &b
         const float Vf = d2f(V);
         const float u = xi * bc.invR0f;
         const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-        const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * Vf) / Rf;
+        const float dev = pgdev + div32(K.two_sigmaf * u - K.four_muf * Vf, Rf);
         const float wr3f = d2f(wr3);
         acc.add_m3(wr3);
         acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
@@ -57,7 +57,7 @@ __device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinCo
     const float Rf = bc.R0f + xi;
     const float u = xi * bc.invR0f;
     const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-    const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * v) / Rf;
+    const float dev = pgdev + div32(K.two_sigmaf * u - K.four_muf * v, Rf);
     const double wr2 = bc.w * R * R;
     const double wr3 = wr2 * R;
     const float wr2f = d2f(wr2);
@@ -69,8 +69,7 @@ __device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinCo
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kMaxWarps * 32)
-    step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
+__device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -154,6 +153,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     if (a.out)
         reduce_and_store<MIXED>(K, acc, nb, c, valid, a.out);
     flush_counters(fl_or, n_flag, n_att, n64, a.counters);
+}
+
+// One kernel per precision with its own register bound.  MIXED: 64 registers
+// (kMaxWarps x 32 threads x 2 CTAs), so 8 CTAs of the default 4 warps fit on an
+// SM; left to itself the compiler takes 110 and 4 CTAs fit (13.2e9 against
+// 17.5e9 bin-steps/s on the 128^3 x 31 line).  FP64: no minimum, where the
+// compiler settles on 64 registers itself (3 % faster than 64 under the bound).
+template <bool MIXED>
+__global__ void step_kernel(const __grid_constant__ StepConst K, const StepArgs a);
+template <>
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    step_kernel<false>(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    step_body<false>(K, a);
+}
+template <>
+__global__ void __launch_bounds__(kMaxWarps * 32, 2)
+    step_kernel<true>(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    step_body<true>(K, a);
 }
 
 template <bool MIXED>

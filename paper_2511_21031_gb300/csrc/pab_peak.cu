@@ -95,6 +95,19 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
                                                     fabs((double)k2));
             bad |= (!(fabs(got - ref) <= tol)) << 7;
         }
+        // FP32 quotient and reciprocal from the approximate seed, within an ulp of
+        // the IEEE operations on their domain (normal operands and results between
+        // 2^-100 and 2^100 in magnitude)
+        const float qa = f[i], qb = __double2float_rn(xi);
+        const auto in_dom = [](float z) { return fabsf(z) >= 0x1p-100f && fabsf(z) <= 0x1p100f; };
+        if (in_dom(qa) && in_dom(qb) && in_dom(qa / qb)) {
+            const float q = pab::div32(qa, qb), qr = __fdiv_rn(qa, qb);
+            const float r = pab::rcp32(qb), rr = __frcp_rn(qb);
+            const int dq = abs((int)__float_as_uint(q) - (int)__float_as_uint(qr));
+            const int dr = abs((int)__float_as_uint(r) - (int)__float_as_uint(rr));
+            bad |= (dq > 1) << 9;
+            bad |= (dr > 1) << 10;
+        }
         cmp[i] = (uint16_t)bad;
     }
 }
