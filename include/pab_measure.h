@@ -60,12 +60,15 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
  *                 6 (float)x (bit patterns, with subnormal float results
  *                 flushed to a signed zero; NaN for NaN), 7 the embedded
  *                 difference 2 k3 - (k1 + k2) of k1 = f, k2 = (float)x,
- *                 k3 = (float)y against FP64 within 4 ulp of its terms,
+ *                 k3 = (float)y against FP64 within 4 ulp of its terms
+ *                 (where |k1|, |k2|, |k3| < 2^100),
  *                 8 2|x| and 2s (s the subnormal or zero with the bits of |x|
  *                 shifted right by 12) against the FP64 additions, 9 the
  *                 library's FP32 quotient f / (float)x and 10 its reciprocal
  *                 1 / (float)x, each within an ulp of the IEEE operation
- *                 where operands and result lie between 2^-100 and 2^100;
+ *                 where operands and result lie between 2^-100 and 2^100,
+ *                 11 the library's short float -> double of a finite f with
+ *                 |f| < 2^104 (bit patterns);
  *                 y_dev[i] must be a finite number >= +0.
  * f_dev [n] float; the others [n] double (cmp_dev [n] uint16), all on the device.
  * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.

@@ -207,13 +207,15 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
 // exact), so the difference is d + (e_d - e_s) exactly.  The three parts are
 // combined in FP64 (e_d - e_s is exact there whenever their exponents differ
 // by less than 29), so the result is the exact difference rounded once to
-// FP64, at two FP64 additions where the direct FP64 form takes three.
+// FP64, at two FP64 additions where the direct FP64 form takes three.  For
+// finite |k| < 2^100 (the parts then stay inside f2d_fin's range); a trial's
+// increments are many orders below that, and a non-finite one fails the trial.
 __device__ __forceinline__ double embedded_diff(float k1, float k2, float k3)
 {
     float s, es, d, ed;
     two_sum(k1, k2, s, es);
     two_sum(__fmul_rn(2.0f, k3), -s, d, ed);
-    return f2d(d) + (f2d(ed) - f2d(es));
+    return f2d_fin(d) + (f2d_fin(ed) - f2d_fin(es));
 }
 
 // The three FP32 right-hand sides of one trial, on increments from the state
@@ -257,8 +259,8 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
 {
     const Incr32 in = incr32(K, bc, A, d2f(R - bc.R0), d2f(V), d2f(h));
     Trial t;
-    t.R = R + f2d(in.d3R);
-    t.V = V + f2d(in.d3V);
+    t.R = R + f2d_fin(in.d3R);
+    t.V = V + f2d_fin(in.d3V);
     t.eR = embedded_diff(in.k1R, in.k2R, in.k3R);
     t.eV = embedded_diff(in.k1V, in.k2V, in.k3V);
     t.ok = in.ok && gt0(t.R) && finite64(t.V);
@@ -339,7 +341,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
         const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g);
         ++n;
         const Verdict vd = judge64(K, tr);
-        const double fac = f2d(vd.fac);
+        const double fac = f2d_fin(vd.fac);
         if (vd.accept) {
             R = tr.R;
             V = tr.V;
@@ -433,7 +435,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const float R3f = __fadd_rn(bc.R0f, __fadd_rn(xi, d3R));
             const float rR = rcp32(__fmul_rn(3.0f, fabsf(R3f)));
             const float rV = rcp32(__fmul_rn(3.0f, fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf)));
-            err = max_nn(abs_nn(eR) * f2d(rR), abs_nn(eV) * f2d(rV));
+            err = max_nn(abs_nn(eR) * f2d_fin(rR), abs_nn(eV) * f2d_fin(rV));
             ok = in.ok && (R3f > 0.0f);
             full64 = false;
         }
@@ -444,20 +446,20 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
                 xi64 = nR - bc.R0;
                 V = nV;
             } else {
-                xi64 += f2d(d3R);
-                V += f2d(d3V);
+                xi64 += f2d_fin(d3R);
+                V += f2d_fin(d3V);
             }
             xi = d2f(xi64);
             v = d2f(V);
             if (last) {
                 const bool clipped = !le(h, rem);
-                h = (clipped && fac >= 1.0f) ? h : ht * f2d(fac);
+                h = (clipped && fac >= 1.0f) ? h : ht * f2d_fin(fac);
                 break;
             }
             rem -= ht;
-            h = ht * f2d(fac);
+            h = ht * f2d_fin(fac);
         } else {
-            h = ht * f2d(fac);
+            h = ht * f2d_fin(fac);
         }
     }
     R = bc.R0 + xi64;

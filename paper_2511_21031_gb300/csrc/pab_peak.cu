@@ -87,14 +87,17 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
         // the embedded difference against the same quantity in FP64 (two
         // roundings there, about one in the library)
         const float k1 = f[i], k2 = __double2float_rn(xi), k3 = __double2float_rn(yi);
-        if (isfinite(k1) && isfinite(k2) && isfinite(k3) && fabsf(k1) < 1e38f && fabsf(k2) < 1e38f &&
-            fabsf(k3) < 1e38f) {
+        if (isfinite(k1) && isfinite(k2) && isfinite(k3) && fabsf(k1) < 0x1p100f &&
+            fabsf(k2) < 0x1p100f && fabsf(k3) < 0x1p100f) {  // the helper's domain
             const double ref = 2.0 * (double)k3 - ((double)k1 + (double)k2);
             const double got = pab::embedded_diff(k1, k2, k3);
             const double tol = 4.0 * DBL_EPSILON * (fabs(2.0 * (double)k3) + fabs((double)k1) +
                                                     fabs((double)k2));
             bad |= (!(fabs(got - ref) <= tol)) << 7;
         }
+        // the short float -> double on its domain (finite, |f| < 2^104)
+        if (isfinite(f[i]) && fabsf(f[i]) < 0x1p104f)
+            bad |= (pab::ubits(pab::f2d_fin(f[i])) != pab::ubits((double)f[i])) << 11;
         // FP32 quotient and reciprocal from the approximate seed, within an ulp of
         // the IEEE operations on their domain (normal operands and results between
         // 2^-100 and 2^100 in magnitude)
