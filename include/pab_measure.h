@@ -30,6 +30,17 @@ pab_status pab_peak_fma(int32_t precision, int32_t blocks, int32_t threads, int3
                         double *sink_dev, float *ms_out, double *fma_out, void *stream);
 
 /*
+ * The FP32 gas term of the mixed right-hand side, (1 + u)^(-a) - 1, for the
+ * tests to compare with FP64 references (no counterpart in the paper): for
+ * i < n, out_dev[i] = the library's branch-free evaluation at u_dev[i] and
+ * lib_dev[i] = expm1f(-a log1pf(u_dev[i])) with CUDA's functions.  All arrays
+ * [n] FP32 on the device; 1 + u > 0, a = 3 gamma > 0.
+ * Errors: PAB_EINVAL (n < 0, a <= 0 or NULL pointers with n > 0), PAB_ECUDA.
+ */
+pab_status pab_gas32_check(int64_t n, const float *u_dev, float a, float *out_dev, float *lib_dev,
+                           void *stream);
+
+/*
  * Values of the FP64 device helpers, for the tests to compare with
  * high-precision references (no counterpart in the paper):
  *   gas_dev[i]     = the library's (1/R[i])^a reached from the base radius Rb[i]

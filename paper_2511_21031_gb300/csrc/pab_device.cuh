@@ -139,9 +139,52 @@ __device__ __forceinline__ double bubble_pressure_rho64(const StepConst &K, cons
 // every kernel that inlines it computes the same bits whatever its register
 // budget; the divisions are IEEE (correctly rounded) divisions.
 // ---------------------------------------------------------------------------
+// (1 + u)^(-a) - 1 in FP32 for 1 + u > 0, accurate relative to itself near
+// u = 0.  w = 1 + u = 2^k f with f in [sqrt(1/2), sqrt(2)), and
+//   log2(1 + u) = k + t P(t) + c/(w ln 2),  t = f - 1,  c = u - (w - 1)
+// (c the rounding of w, divided by w from the reciprocal seed: it is below an
+// ulp of w); y = -a log2(1 + u), clamped to [-125, 125], splits as n + r with
+// n an integer and |r| <= 1/2, and
+//   (1 + u)^(-a) - 1 = 2^n (2^r - 1) + (2^n - 1),  2^r - 1 = r Q(r),
+// with 2^n formed in the exponent field.  P (degree 8) and Q (degree 5) are
+// minimax fits in relative error on those intervals (csrc/fit_gas32.py).
+// Within 6 ulp for |u| < 1/2 and 11 ulp for u in (-0.8, 1000] at a = 4.2, as
+// the composition expm1f(-a log1pf(u)) is; no branches and no library call.
+__device__ __forceinline__ float pow_m1_32(float u, float a)
+{
+    const float w = __fadd_rn(1.0f, u);
+    const float c = __fsub_rn(u, __fsub_rn(w, 1.0f));
+    const uint32_t wb = __float_as_uint(w);
+    const int k = (int)(wb - 0x3f3504f3u) >> 23;
+    const float t = __fsub_rn(__uint_as_float(wb - ((uint32_t)k << 23)), 1.0f);
+    float p = 0x1.01b48cp-3f;
+    p = __fmaf_rn(p, t, -0x1.a87c04p-3f);
+    p = __fmaf_rn(p, t, 0x1.b9c97ap-3f);
+    p = __fmaf_rn(p, t, -0x1.e95c12p-3f);
+    p = __fmaf_rn(p, t, 0x1.26d382p-2f);
+    p = __fmaf_rn(p, t, -0x1.715c4ep-2f);
+    p = __fmaf_rn(p, t, 0x1.ec73d6p-2f);
+    p = __fmaf_rn(p, t, -0x1.71547p-1f);
+    p = __fmaf_rn(p, t, 0x1.715476p+0f);
+    const float cw = __fmul_rn(__fmul_rn(c, rcp_seed32(w)), 0x1.715476p+0f);  // c / (w ln 2)
+    const float l2 = __fadd_rn(__int2float_rn(k), __fmaf_rn(t, p, cw));
+    const float y = fminf(fmaxf(__fmul_rn(-a, l2), -125.0f), 125.0f);
+    const float mg = __fadd_rn(y, 0x1.8p23f);  // y rounded to an integer in the low bits
+    const float r = __fsub_rn(y, __fsub_rn(mg, 0x1.8p23f));
+    const int n = (int)(__float_as_uint(mg) - 0x4b400000u);
+    float q = 0x1.4308eap-13f;
+    q = __fmaf_rn(q, r, 0x1.5f07b6p-10f);
+    q = __fmaf_rn(q, r, 0x1.3b2ba0p-7f);
+    q = __fmaf_rn(q, r, 0x1.c6af6ep-5f);
+    q = __fmaf_rn(q, r, 0x1.ebfbdep-3f);
+    q = __fmaf_rn(q, r, 0x1.62e430p-1f);
+    const float sc = __uint_as_float((uint32_t)(n + 127) << 23);
+    return __fmaf_rn(sc, __fmul_rn(r, q), __fsub_rn(sc, 1.0f));
+}
+
 __device__ __forceinline__ float gas_dev32(const StepConst &K, const BinConst &bc, float u)
 {
-    return __fmul_rn(bc.pg0f, expm1f(__fmul_rn(-K.three_gammaf, log1pf(u))));
+    return __fmul_rn(bc.pg0f, pow_m1_32(u, K.three_gammaf));
 }
 
 // With iR = 1/R the numerator of the deviation form is P + Q iR,

@@ -136,6 +136,32 @@ extern "C" pab_status pab_bits_check(int64_t n, const float *f_dev, const double
     return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
 }
 
+namespace {
+__global__ void gas32_check_kernel(long long n, const float *u, float a, float *out, float *lib)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        out[i] = pab::pow_m1_32(u[i], a);
+        lib[i] = expm1f(-a * log1pf(u[i]));
+    }
+}
+}  // namespace
+
+extern "C" pab_status pab_gas32_check(int64_t n, const float *u_dev, float a, float *out_dev,
+                                      float *lib_dev, void *stream)
+{
+    if (n < 0 || !(a > 0.0f) || (n > 0 && (!u_dev || !out_dev || !lib_dev)))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    gas32_check_kernel<<<152 * 4, 256, 0, s>>>(n, u_dev, a, out_dev, lib_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
+
 extern "C" pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, double a,
                                      double *gas_dev, double *gas_tab_dev, double *exact_dev,
                                      void *stream)

@@ -28,8 +28,8 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
-           "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_get_contents",
-           "pab_set_contents")
+           "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check",
+           "pab_get_contents", "pab_set_contents")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_stiffened_gas": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
         "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp]),
         "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +261,18 @@ def pab_math_check(R, Rb, a: float, stream=None):
     if st != PAB_OK:
         raise PabError(st, "pab_math_check")
     return g, gt, e
+
+
+def pab_gas32_check(u, a: float, stream=None):
+    """(library value, CUDA expm1f/log1pf value) of the FP32 gas term (1 + u)^(-a) - 1."""
+    import torch
+    out = torch.empty_like(u)
+    lib = torch.empty_like(u)
+    st = load().pab_gas32_check(u.numel(), u.data_ptr(), float(a), out.data_ptr(), lib.data_ptr(),
+                                _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_gas32_check")
+    return out, lib
 
 
 def pab_destroy(h):

@@ -38,3 +38,30 @@ def test_gas_series_as_accurate_as_exp_log(a):
     ref_b = np.power(1.0 / Rb.astype(np.longdouble), np.longdouble(a))
     assert float(np.median(e_series[small])) <= 4 * ULP
     del ref_b
+
+
+@pytest.mark.parametrize("gamma", [1.0, 1.4, 5.0 / 3.0])
+def test_fp32_gas_term_within_its_bound(gamma):
+    """(1 + u)^(-3 gamma) - 1 in FP32 against FP64, in ulps of the FP32 result: the
+    branch-free evaluation of the mixed right-hand side stays within the bound its
+    header states, and near the library composition expm1f(-a log1pf(u))."""
+    import torch
+    a = np.float32(3.0 * gamma)
+    rng = np.random.default_rng(5)
+    near = np.concatenate([10.0 ** rng.uniform(-12, np.log10(0.5), 200000),
+                           -(10.0 ** rng.uniform(-12, np.log10(0.5), 200000))])
+    wide = np.concatenate([rng.uniform(-0.8, 0.0, 100000), 10.0 ** rng.uniform(-0.3, 3, 100000)])
+    for u, bound in ((near, 8.0), (wide, 16.0)):
+        u32 = np.concatenate([u, [0.0, -0.0]]).astype(np.float32)
+        out, lib = pab.pab_gas32_check(torch.as_tensor(u32, device="cuda"), float(a))
+        out, lib = out.cpu().numpy().astype(np.float64), lib.cpu().numpy().astype(np.float64)
+        exact = np.expm1(-float(a) * np.log1p(u32.astype(np.float64)))
+        ulp = np.spacing(np.abs(exact.astype(np.float32))).astype(np.float64)
+        ulp[exact == 0] = np.finfo(np.float32).smallest_subnormal
+        e_new = np.abs(out - exact) / ulp
+        e_lib = np.abs(lib - exact) / ulp
+        print(f"gamma {gamma}: max {e_new.max():.2f} ulp (CUDA expm1f/log1pf: {e_lib.max():.2f})")
+        assert np.all(np.isfinite(out))
+        assert e_new.max() <= bound
+        assert e_new.max() <= 1.5 * e_lib.max() + 2.0
+        assert np.all(out[u32 == 0] == 0)
