@@ -105,7 +105,7 @@ __device__ __forceinline__ bool smear_inside(const double (*sq)[kSide], const fl
 __global__ void __launch_bounds__(kSmearWarps * 32)
     el_smear_kernel(long long N, const double *__restrict__ px, const double *__restrict__ py,
                     const double *__restrict__ pz, const double *__restrict__ R,
-                    const double *__restrict__ V, int nx, int ny, int nz, double dx,
+                    const double *__restrict__ V, int nx, int ny, int nz, double dx, double inv_dx,
                     double *__restrict__ alpha, double *__restrict__ alpha_dot)
 {
     // per warp and axis offset: the squared distance (FP64 and FP32) and the 1-D
@@ -124,18 +124,43 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
          n += (long long)gridDim.x * kSmearWarps) {
         const double r = R[n];
         const double h = r < dx ? dx : r;
-        const int m = (int)floor(3.0 * h / dx) + 1;  // cells whose centre can lie within 3h
+        // cells whose centre can lie within 3h: m > 3h/dx (the 1e-9 keeps the product's
+        // rounding from taking m one too small); m >= 4 for every number r (h >= dx)
+        const int m = (int)floor(fma(3.0 * h, inv_dx, 1e-9)) + 1;
+        if (m < 4)
+            continue;  // r is NaN: the bubble adds nothing
         const int side = 2 * m + 1;
         const bool cached = m <= kCacheHalf;
         const double x0 = px[n], y0 = py[n], z0 = pz[n];
-        const int bx = (int)floor(x0 / dx) - m, by = (int)floor(y0 / dx) - m, bz = (int)floor(z0 / dx) - m;
-        const double inv2h2 = rcp64(2.0 * h * h);
-        const double Vb = 4.0 / 3.0 * 3.14159265358979323846 * r * r * r;
-        const double Vd = 4.0 * 3.14159265358979323846 * r * r * V[n];
-        const double amp = Vb * rcp64(h * h * h * norm);  // V times the kernel's normalisation
-        const double rate = Vd * rcp64(Vb);                // alpha_dot / alpha of this bubble
+        // the base cell may be off by one where x0/dx rounds across an integer: the window
+        // [f - m, f + m] still holds every centre within 3h of x0 then
+        const int bx = (int)floor(x0 * inv_dx) - m, by = (int)floor(y0 * inv_dx) - m,
+                  bz = (int)floor(z0 * inv_dx) - m;
+        const double ir = rcp64(r);
+        const double ih = r < dx ? inv_dx : ir;  // 1/h
+        const double inv2h2 = 0.5 * ih * ih;
+        const double rh = r * ih;
+        // V/(h^3 (2 pi)^{3/2}) = (4 pi/3) (r/h)^3 / (2 pi)^{3/2}, and alpha_dot/alpha = 3 Rdot/r
+        const double amp = (4.0 / 3.0 * 3.14159265358979323846 / norm) * (rh * rh * rh);
+        const double rate = 3.0 * V[n] * ir;
         const double lim2 = 9.0 * h * h;
-        const long long count = (long long)side * side * side;
+        // stencil point t = oi + side (oj + side ok); each lane walks t = lane, lane + 32,
+        // ... with its offsets carried forward (32 = q32 side + r32, side >= 9 since
+        // h >= dx), so the loops divide nothing
+        const int q32 = 32 / side, r32 = 32 - q32 * side;
+        int oi = lane % side, oj = lane / side, ok = 0;
+        const auto next32 = [&]() {
+            oi += r32;
+            oj += q32;
+            if (oi >= side) {
+                oi -= side;
+                ++oj;
+            }
+            if (oj >= side) {
+                oj -= side;
+                ++ok;
+            }
+        };
         if (cached) {
             for (int t = lane; t < 3 * side; t += 32) {
                 const int a = t / side, o = t % side;
@@ -152,29 +177,28 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
             const float lim2f = (float)lim2;
             // the lanes test 32 stencil points at a time; the inside ones (about 16 % of the
             // cube) queue up, and every 32 of them are added by the whole warp at once
+            // (queued points are kept as oi | oj << 8 | ok << 16, side <= 49 here)
             int queued = 0, tail = 0;
-            for (long long base = 0; base < count; base += 32) {
-                const long long t = base + lane;
+            for (int base = 0; base < side * side * side; base += 32) {
                 bool in = false;
-                if (t < count) {
-                    const int oi = (int)(t % side), oj = (int)((t / side) % side),
-                              ok = (int)(t / ((long long)side * side));
+                if (ok < side) {
                     const int i = bx + oi, j = by + oj, k = bz + ok;
                     in = i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz &&
                          smear_inside(sq[warp], sqf[warp], oi, oj, ok, lim2f, h);
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, in);
                 if (in)
-                    ring[warp][(tail + queued + __popc(mask & lt_mask)) & 63] = (int)t;
+                    ring[warp][(tail + queued + __popc(mask & lt_mask)) & 63] = oi | (oj << 8) | (ok << 16);
                 queued += __popc(mask);
+                next32();
                 __syncwarp();
-                const bool flush_all = base + 32 >= count;
+                const bool flush_all = base + 32 >= side * side * side;
                 while (queued >= 32 || (flush_all && queued > 0)) {
                     if (lane < queued) {
                         const int tq = ring[warp][(tail + lane) & 63];
-                        const int oi = tq % side, oj = (tq / side) % side, ok = tq / (side * side);
-                        const double a = fac[warp][0][oi] * fac[warp][1][oj] * fac[warp][2][ok];
-                        const long long c = ((long long)(bz + ok) * ny + (by + oj)) * nx + (bx + oi);
+                        const int qi = tq & 255, qj = (tq >> 8) & 255, qk = tq >> 16;
+                        const double a = fac[warp][0][qi] * fac[warp][1][qj] * fac[warp][2][qk];
+                        const long long c = ((long long)(bz + qk) * ny + (by + qj)) * nx + (bx + qi);
                         atomicAdd(&alpha[c], a);
                         if (alpha_dot)
                             atomicAdd(&alpha_dot[c], a * rate);
@@ -186,8 +210,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                 }
             }
         } else {
-            for (long long t = lane; t < count; t += 32) {
-                const int oi = (int)(t % side), oj = (int)((t / side) % side), ok = (int)(t / ((long long)side * side));
+            for (; ok < side; next32()) {
                 const int i = bx + oi, j = by + oj, k = bz + ok;
                 if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz)
                     continue;
@@ -260,8 +283,8 @@ cudaError_t launch_smear(pab_el_t *e, double *alpha, double *alpha_dot, cudaStre
     if (blocks > 152LL * 64)
         blocks = 152LL * 64;
     pab::el_smear_kernel<<<(unsigned)blocks, pab::kSmearWarps * 32, 0, s>>>(
-        e->N, e->pos, e->pos + e->N, e->pos + 2 * e->N, e->R, e->V, e->nx, e->ny, e->nz, e->dx, alpha,
-        alpha_dot);
+        e->N, e->pos, e->pos + e->N, e->pos + 2 * e->N, e->R, e->V, e->nx, e->ny, e->nz, e->dx,
+        1.0 / e->dx, alpha, alpha_dot);
     return cudaGetLastError();
 }
 
