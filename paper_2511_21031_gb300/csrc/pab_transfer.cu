@@ -36,8 +36,10 @@ __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc
 // constant-coefficient wall gradients), iR = 1/R.  With chi_vw = rho_vw/rho_bw
 // and 1 - chi_vw = rho_gw/rho_bw the vapour flux is
 //   mdot = D beta_c rho_bw (rho_vw - chi_mean rho_bw) / (rho_gw R) = X / R,
-// so the wall fraction needs no reciprocal, and the heat term
-// (gamma - 1)/gamma k_bw beta_T (T_w - T_mean)/R shares the factor 1/R:
+// so the wall fraction needs no reciprocal; with the mean mass fraction
+// chi_mean = m_v R_g / D2, D2 = m_v R_g + m_g R_g, the two remaining divisions
+// share one reciprocal: X = D beta_c rho_bw (rho_vw D2 - m_v R_g rho_bw) / (D2 rho_gw).
+// The heat term (gamma - 1)/gamma k_bw beta_T (T_w - T_mean)/R shares the factor 1/R:
 //   dp_b/dt = 3 gamma/R ((R_v T_w X + kT (T_w - T_mean))/R - Rdot p_b),
 //   dm_v/dt = 4 pi R^2 mdot = 4 pi R X.
 __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, const State4 &s,
@@ -46,10 +48,10 @@ __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, c
     const double Vb = (4.0 / 3.0 * kPi) * s.R * s.R * s.R;
     const double T_mean = s.pb * Vb * rcp64(fma(s.mv, K.tr_Rv, mRg));
     const double mvRg = s.mv * K.tr_Rg;
-    const double chi_mean = mvRg * rcp64(mvRg + mRg);      // m_v / (m_v + m_g)
+    const double D2 = mvRg + mRg;                          // (m_v + m_g) R_g
     const double rho_gw = (s.pb - K.pv) * K.tr_inv_RgTw;   // gas density at the wall
     const double rho_bw = K.tr_rho_vw + rho_gw;
-    const double X = K.tr_Dc * rho_bw * rcp64(rho_gw) * fma(-chi_mean, rho_bw, K.tr_rho_vw);
+    const double X = K.tr_Dc * rho_bw * fma(K.tr_rho_vw, D2, -mvRg * rho_bw) * rcp64(D2 * rho_gw);
     const double q = fma(K.tr_RvTw, X, K.tr_kT * (K.tr_Tw - T_mean));
     dpb = K.three_gamma * iR * fma(q, iR, -s.V * s.pb);
     dmv = (4.0 * kPi) * s.R * X;
@@ -59,7 +61,8 @@ __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, c
 // accel64: the s/R terms (s = 4 mu Rdot + 2 sigma) of (p_bw - p_inf)(1 + Rdot/c)/rho
 // and of (R/(rho c)) d/dt p_bw add up to -s/(rho R), which leaves
 //   Rddot = (N0 R - s/rho) / (R den),
-//   N0 = (p_b - p_inf)/rho (1 + Rdot/c) + R dp_b/dt /(rho c) - Rdot^2 (3/2 - Rdot/(2c)).
+//   N0 = P (1 + Rdot/c) + R dp_b/dt /(rho c) - Rdot^2 (3/2 - Rdot/(2c)),  P = (p_b - p_inf)/rho,
+// taken as N0 = P + R dp_b/dt /(rho c) + Rdot (P/c - Rdot (3/2 - Rdot/(2c))).
 __device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double pinf_rho, const State4 &s)
 {
     const double den = fma(s.R, fma(s.V, -K.inv_c, 1.0), K.fmu_ic_rho);
@@ -68,8 +71,8 @@ __device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double pi
     double dpb, dmv;
     transfer_rates(K, mRg, s, iR, dpb, dmv);
     const double P = fma(s.pb, K.inv_rho, -pinf_rho);
-    const double w = fma(s.R * K.ic_rho, dpb, -s.V * (s.V * fma(s.V, K.m05_inv_c, 1.5)));
-    const double N0 = fma(P, fma(s.V, K.inv_c, 1.0), w);
+    const double t = fma(-s.V, fma(s.V, K.m05_inv_c, 1.5), P * K.inv_c);
+    const double N0 = fma(s.V, t, fma(s.R * K.ic_rho, dpb, P));
     const double s_rho = fma(K.fmu_rho, s.V, K.tsig_rho);
     return State4{s.V, fma(N0, s.R, -s_rho) * inv, dpb, dmv};
 }
@@ -81,7 +84,7 @@ __device__ __forceinline__ State4 scale(double h, const State4 &f)
 
 // Shu-Osher SSP-RK3 with the embedded Heun member in increment form (as trial64),
 // on four components: k1 = h f(y), y1 = y + k1, s = k1 + k2, y2 = y + s/4,
-// y3 = y + s/6 + 2/3 k3, 3 (y3 - z) = 2 k3 - s.
+// e = 2 k3 - s = (2h) f(y2) - s = 3 (y3 - z) with 2h exact, y3 = y + s/2 + e/3.
 __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double pinf_rho, const State4 &y,
                                          double h)
 {
@@ -90,13 +93,14 @@ __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double 
     const State4 f2 = rhs4(K, mRg, pinf_rho, y1);
     const State4 s{fma(h, f2.R, k1.R), fma(h, f2.V, k1.V), fma(h, f2.pb, k1.pb), fma(h, f2.mv, k1.mv)};
     const State4 y2{fma(0.25, s.R, y.R), fma(0.25, s.V, y.V), fma(0.25, s.pb, y.pb), fma(0.25, s.mv, y.mv)};
-    const State4 k3 = scale(h, rhs4(K, mRg, pinf_rho, y2));
+    const State4 f3 = rhs4(K, mRg, pinf_rho, y2);
+    const double h2 = twice_nn(h);
+    const State4 e{fma(h2, f3.R, -s.R), fma(h2, f3.V, -s.V), fma(h2, f3.pb, -s.pb), fma(h2, f3.mv, -s.mv)};
     Trial4 t;
-    t.y = State4{fma(1.0 / 6.0, s.R, fma(2.0 / 3.0, k3.R, y.R)), fma(1.0 / 6.0, s.V, fma(2.0 / 3.0, k3.V, y.V)),
-                 fma(1.0 / 6.0, s.pb, fma(2.0 / 3.0, k3.pb, y.pb)),
-                 fma(1.0 / 6.0, s.mv, fma(2.0 / 3.0, k3.mv, y.mv))};
-    t.eR = fma(2.0, k3.R, -s.R);
-    t.eV = fma(2.0, k3.V, -s.V);
+    t.y = State4{fma(1.0 / 3.0, e.R, fma(0.5, s.R, y.R)), fma(1.0 / 3.0, e.V, fma(0.5, s.V, y.V)),
+                 fma(1.0 / 3.0, e.pb, fma(0.5, s.pb, y.pb)), fma(1.0 / 3.0, e.mv, fma(0.5, s.mv, y.mv))};
+    t.eR = e.R;
+    t.eV = e.V;
     t.ok = gt0(y1.R) && gt0(y2.R) && gt0(t.y.R) && finite64(t.y.V);
     return t;
 }
@@ -155,11 +159,12 @@ __device__ __forceinline__ void accumulate_transfer(const StepConst &K, const Bi
 {
     const double wr2 = bc.w * y.R * y.R;
     const double wr3 = wr2 * y.R;
-    const double pbw_rho = (y.pb - fma(K.four_mu, y.V, K.two_sigma) * rcp64(y.R)) * K.inv_rho;
+    // w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho
     acc.add_m3(wr3);
-    acc.m2v += wr2 * y.V;
-    acc.m3p += wr3 * pbw_rho;
-    acc.m3v2 += wr3 * y.V * y.V;
+    acc.m2v = fma(wr2, y.V, acc.m2v);
+    acc.m3p = fma(wr3, y.pb * K.inv_rho, acc.m3p);
+    acc.m3p = fma(-wr2, fma(K.fmu_rho, y.V, K.tsig_rho), acc.m3p);
+    acc.m3v2 = fma(wr3 * y.V, y.V, acc.m3v2);
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
