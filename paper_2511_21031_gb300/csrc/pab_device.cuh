@@ -79,6 +79,16 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
 }
 
 
+// The first trial size of a flow step from the carried FP32 proposal hc: hc
+// itself when it is a number in (0, dt], else dt.  hc > 0 is tested in FP32
+// (false for NaN); f2d_fin is exact below 2^104 and takes larger values, inf
+// included, to at least 2^104, above any dt, so they fall back to dt too.
+__device__ __forceinline__ double start_h(float hc, double dt)
+{
+    const double h = hc > 0.0f ? f2d_fin(hc) : dt;
+    return le(h, dt) ? h : dt;
+}
+
 struct Trial {
     double R, V;    // third-order result y3
     double eR, eV;  // 3 (y3 - z) = 2 k3 - (k1 + k2) per component: three times the embedded
@@ -367,9 +377,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
 {
     const double B0 = (K.pv - p_inf) * K.inv_rho;
     const double B0c = B0 * K.inv_c;
-    double h = f2d(hc);
-    if (!gt0(h) || !le(h, dt))
-        h = dt;
+    double h = start_h(hc, dt);
     double t = 0.0;
     uint32_t flags = 0;
     int n = 0;
@@ -432,8 +440,9 @@ __device__ __forceinline__ Trial64Out collapse_trial64(const StepConst &K, const
 // accept decision, and the controller's time bookkeeping (the time left of
 // the flow step, counted down, and landing on dt).  The growth factor is formed in
 // FP32: the proposal it scales is stored in FP32 between calls anyway.  The
-// FP32 images of the state (xi = R - R0, Rdot) are refreshed only when a trial
-// is accepted.  Bins near collapse (R < r_collapse R0 or |Rdot| > v_collapse)
+// FP32 images of the state (xi = R - R0, Rdot) change only when a trial is
+// accepted: by the same FP32 increments after an FP32 trial, from the state
+// after an FP64 one.  Bins near collapse (R < r_collapse R0 or |Rdot| > v_collapse)
 // take the FP64 trial.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinConst &bc,
@@ -441,9 +450,7 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
                                                   double &V, float &hc, int &n_att, int &n64,
                                                   float &xi, float &v)
 {
-    double h = f2d(hc);
-    if (!gt0(h) || !le(h, dt))
-        h = dt;
+    double h = start_h(hc, dt);
     double rem = dt;  // time left of the flow step
     uint32_t flags = 0;
     int n = 0;
@@ -488,12 +495,16 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             if (full64) {
                 xi64 = nR - bc.R0;
                 V = nV;
+                xi = d2f(xi64);
+                v = d2f(V);
             } else {
+                // the FP32 images move by the same increments: within an ulp or two of
+                // the state's own images until the next flow step derives them afresh
                 xi64 += f2d_fin(d3R);
                 V += f2d_fin(d3V);
+                xi = __fadd_rn(xi, d3R);
+                v = __fadd_rn(v, d3V);
             }
-            xi = d2f(xi64);
-            v = d2f(V);
             if (last) {
                 const bool clipped = !le(h, rem);
                 h = (clipped && fac >= 1.0f) ? h : ht * f2d_fin(fac);

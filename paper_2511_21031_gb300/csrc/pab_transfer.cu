@@ -117,9 +117,7 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
         n_att = K.n_fixed;
         return 0;
     }
-    double h = f2d(hc);
-    if (!gt0(h) || !le(h, dt))
-        h = dt;
+    double h = start_h(hc, dt);
     double t = 0.0;
     uint32_t flags = 0;
     int n = 0;
