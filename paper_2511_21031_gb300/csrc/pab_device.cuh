@@ -365,10 +365,11 @@ __device__ __forceinline__ Verdict judge64(const StepConst &K, const Trial &t)
 // ---------------------------------------------------------------------------
 // Adaptive advance of one bin over dt with the carried proposal hc:
 //   h = min(hc, dt) (dt when hc is not a positive number); the trial size is
-//   min(h, dt - t) and the trial that reaches dt is marked last, so the call
-//   ends exactly at dt; accepted: t += h_try, proposal h_try * fac (on the
-//   last trial the unclipped h is kept when it was clipped and fac >= 1);
-//   rejected: h = h_try * fac; at most max_attempts trials.
+//   min(h, rem) with rem the time left of the flow step, and the trial that
+//   reaches dt is marked last, so the call ends exactly at dt; accepted:
+//   rem -= h_try, proposal h_try * fac (on the last trial the unclipped h is
+//   kept when it was clipped and fac >= 1); rejected: h = h_try * fac; at most
+//   max_attempts trials.
 // FP64 trials throughout (the mixed mode has its own loop, advance_mixed).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
@@ -378,7 +379,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
     const double B0 = (K.pv - p_inf) * K.inv_rho;
     const double B0c = B0 * K.inv_c;
     double h = start_h(hc, dt);
-    double t = 0.0;
+    double rem = dt;  // time left of the flow step, counted down
     uint32_t flags = 0;
     int n = 0;
     for (;;) {
@@ -386,7 +387,6 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
             flags |= PAB_FLAG_STEP_LIMIT;
             break;
         }
-        const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
         const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g);
@@ -401,7 +401,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
                 h = (clipped && vd.fac >= 1.0f) ? h : ht * fac;
                 break;
             }
-            t += ht;
+            rem -= ht;
             h = ht * fac;
         } else {
             h = ht * fac;

@@ -118,7 +118,7 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
         return 0;
     }
     double h = start_h(hc, dt);
-    double t = 0.0;
+    double rem = dt;  // time left of the flow step, counted down
     uint32_t flags = 0;
     int n = 0;
     for (;;) {
@@ -126,7 +126,6 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
             flags |= PAB_FLAG_STEP_LIMIT;
             break;
         }
-        const double rem = dt - t;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
         const Trial4 tr = trial4(K, mRg, pinf_rho, y, ht);
@@ -140,7 +139,7 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
                 h = (clipped && vd.fac >= 1.0f) ? h : ht * fac;
                 break;
             }
-            t += ht;
+            rem -= ht;
             h = ht * fac;
         } else {
             h = ht * fac;
