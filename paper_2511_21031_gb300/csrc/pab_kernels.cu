@@ -222,9 +222,9 @@ cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, in
     const int nw = clamp_warps(block_warps, K.B);
     const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
     if (precision == PAB_MIXED)
-        step_kernel<true><<<grid, nw * 32, 0, s>>>(K, a);
+        step_kernel<true><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
     else
-        step_kernel<false><<<grid, nw * 32, 0, s>>>(K, a);
+        step_kernel<false><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
     return cudaGetLastError();
 }
 
@@ -234,9 +234,9 @@ cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, 
     const int nw = clamp_warps(block_warps, K.B);
     const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
     if (precision == PAB_MIXED)
-        moments_kernel<true><<<grid, nw * 32, 0, s>>>(K, nb, R, V, out);
+        moments_kernel<true><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, out);
     else
-        moments_kernel<false><<<grid, nw * 32, 0, s>>>(K, nb, R, V, out);
+        moments_kernel<false><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, out);
     return cudaGetLastError();
 }
 

@@ -40,35 +40,41 @@ struct MomAcc {
     __device__ __forceinline__ double M3V2() const { return MIXED ? f2d(m3v2f) : m3v2; }
 };
 
+// Dynamic shared memory of the kernels that call reduce_and_store: the five
+// partial sums of each warp and lane, sized by the launch's warps (a static
+// array for the largest CTA would hold L1 capacity that the gas table uses).
+constexpr size_t reduce_smem_bytes(int nw) { return (size_t)5 * nw * kTile * sizeof(double); }
+
 // Combine the warps' partial sums of one tile and write the moments.
 template <bool MIXED>
 __device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAcc<MIXED> &acc,
                                                  double nb, int64_t c, bool valid, double *out)
 {
-    __shared__ double red[5][kMaxWarps][kTile];
+    extern __shared__ double red[];  // [5][nw][kTile], reduce_smem_bytes(nw)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    red[0][warp][lane] = acc.m3;
-    red[1][warp][lane] = acc.m3c;
-    red[2][warp][lane] = acc.M2V();
-    red[3][warp][lane] = acc.M3P();
-    red[4][warp][lane] = acc.M3V2();
+    const auto at = [&](int m, int w) -> double & { return red[((size_t)m * nw + w) * kTile + lane]; };
+    at(0, warp) = acc.m3;
+    at(1, warp) = acc.m3c;
+    at(2, warp) = acc.M2V();
+    at(3, warp) = acc.M3P();
+    at(4, warp) = acc.M3V2();
     __syncthreads();
     if (warp == 0 && valid) {
-        double m3 = red[0][0][lane], m3c = red[1][0][lane];
-        double m2v = red[2][0][lane], m3p = red[3][0][lane], m3v2 = red[4][0][lane];
+        double m3 = at(0, 0), m3c = at(1, 0);
+        double m2v = at(2, 0), m3p = at(3, 0), m3v2 = at(4, 0);
         for (int w = 1; w < nw; ++w) {
-            const double x = red[0][w][lane];
+            const double x = at(0, w);
             if (MIXED) {
                 neumaier_add(m3, m3c, x);
-                m3c += red[1][w][lane];
+                m3c += at(1, w);
             } else {
                 m3 += x;
             }
-            m2v += red[2][w][lane];
-            m3p += red[3][w][lane];
-            m3v2 += red[4][w][lane];
+            m2v += at(2, w);
+            m3p += at(3, w);
+            m3v2 += at(4, w);
         }
         if (MIXED)
             m3 += m3c;

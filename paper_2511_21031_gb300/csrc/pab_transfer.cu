@@ -257,7 +257,7 @@ cudaError_t launch_transfer_step(const StepConst &K, const StepArgs &a, int bloc
         return cudaErrorInvalidValue;
     const int nw = clamp_warps(block_warps, K.B);
     const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    transfer_step_kernel<<<grid, nw * 32, 0, s>>>(K, a);
+    transfer_step_kernel<<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
     return cudaGetLastError();
 }
 
@@ -267,7 +267,7 @@ cudaError_t launch_transfer_moments(const StepConst &K, const double *nb, const 
 {
     const int nw = clamp_warps(block_warps, K.B);
     const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    transfer_moments_kernel<<<grid, nw * 32, 0, s>>>(K, nb, R, V, pb, out);
+    transfer_moments_kernel<<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, pb, out);
     return cudaGetLastError();
 }
 
