@@ -290,6 +290,8 @@ void gas_table(double a, double dmax, std::vector<double> *tab, int *J, double *
             e[1 + k] = ck;
             ck *= (-a - (double)k) / ((double)(k + 1) * x);
         }
+        for (int k = 1 + kGasTabTerms; k < kGasTabStride; ++k)
+            e[k] = 0.0;
     }
 }
 
