@@ -41,14 +41,14 @@ __device__ __forceinline__ double gas_series(const StepConst &K, double d)
 // G = (R0/R)^(3 gamma) for R > 0.
 //  - With a node table (a handle's gas_tab): x = R/R0 goes to the nearest node
 //    x_j = q^j (picked in FP32: log2(x)/log2(q) rounded), and G is the node's
-//    binomial series in delta = x - x_j, sum_k c_k delta^k (degree 4,
+//    binomial series in delta = x - x_j, sum_k c_k delta^k (degree 3,
 //    |delta| < x_j gas_dmax_tab). A pure function of R: no exp or log while R/R0
 //    stays within the table.
 //  - Otherwise (or outside the table): the radii of one step stay close to the
 //    last exact evaluation R_b in g, reached by the degree-11 series in
 //    d = (R - R_b)/R_b; farther away the value is exact, exp(-3 gamma log(R/R0)),
 //    and becomes the new base.
-static_assert(kGasTabStride == 6 && kGasTabTerms == 5, "gas table node layout");
+static_assert(kGasTabStride == 6 && kGasTabTerms == 4, "gas table node layout");
 __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst &bc, double R,
                                              GasBase &g)
 {
@@ -56,12 +56,12 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
         const float xf = d2f(R) * bc.invR0f;
         const int j = __float2int_rn(__log2f(xf) * K.gas_inv_log2q);
         if (j >= -K.gas_J && j <= K.gas_J) {
-            // {x_j, c_0}, {c_1, c_2}, {c_3, c_4}
+            // {x_j, c_0}, {c_1, c_2}, {c_3, 0}
             const double2 *e = reinterpret_cast<const double2 *>(K.gas_tab) + 3 * (j + K.gas_J);
-            const double2 n0 = __ldg(e), n1 = __ldg(e + 1), n2 = __ldg(e + 2);
+            const double2 n0 = __ldg(e), n1 = __ldg(e + 1);
+            const double c3 = __ldg(reinterpret_cast<const double *>(e + 2));
             const double d = fma(R, bc.invR0, -n0.x);
-            double s = fma(n2.y, d, n2.x);
-            s = fma(s, d, n1.y);
+            double s = fma(c3, d, n1.y);
             s = fma(s, d, n1.x);
             return fma(s, d, n0.y);
         }

@@ -34,8 +34,8 @@ struct BinConst {
 constexpr int kDefaultWarps = 4;
 
 constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
-constexpr int kGasTabTerms = 5;   // degree 4 around the nodes of a gas table
-constexpr int kGasTabStride = 6;  // doubles per node: x_j and the coefficients
+constexpr int kGasTabTerms = 4;   // degree 3 around the nodes of a gas table
+constexpr int kGasTabStride = 6;  // doubles per node: x_j, the coefficients and a pad
 
 // Liquid, gas and stepper constants.  Passed by value as a kernel parameter,
 // so warp-uniform reads come from the constant bank.
@@ -75,7 +75,7 @@ struct StepConst {
     double gas_dmax;
     double gas_dmax_tab;  // the same bound for the degree kGasTabTerms-1 of the table path
     // optional table of nodes x_j = q^j, j = -gas_J..gas_J, kGasTabStride doubles each,
-    // {x_j, c_0 .. c_4}: (R/R0)^(-3 gamma) = sum_k c_k (R/R0 - x_j)^k with
+    // {x_j, c_0 .. c_3, 0}: (R/R0)^(-3 gamma) = sum_k c_k (R/R0 - x_j)^k with
     // c_k = x_j^(-3 gamma) C(-3 gamma, k) x_j^(-k), the binomial series about the node
     // (nullptr: no table)
     const double *gas_tab;
