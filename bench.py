@@ -48,13 +48,13 @@ SM_MAX_MHZ = 2070.0
 # error norm, controller) and per bin-step outside the trial loop (load, bubble
 # pressure and quadrature sums): least-squares fit of ncu's
 # smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over six launches
-# of the 64^3 x 31 grid with traced trial counts (residual 5e-4).
-FP64_FLOPS_PER_TRIAL = 148.45
-FP64_FLOPS_PER_BINSTEP = 32.1
+# of the 64^3 x 31 grid with traced trial counts (residual 6e-4).
+FP64_FLOPS_PER_TRIAL = 129.45
+FP64_FLOPS_PER_BINSTEP = 26.1
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
-# on the 64^3 x 31 grid, 295.3 MB / 8.13M bin-steps); scaled by bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 36.3
-FP64_PIPE_ACTIVE_NCU = 0.916
+# on the 64^3 x 31 grid, 285.6 MB / 8.13M bin-steps); scaled by bin-steps.
+FP64_DRAM_BYTES_PER_BINSTEP = 35.1
+FP64_PIPE_ACTIVE_NCU = 0.910
 
 
 def _dist():
