@@ -52,7 +52,8 @@ pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const doub
 pab_status pab_el_step(pab_el_t *e, const double *p_cell_dev, double dt, double *alpha_dev,
                        double *alpha_dot_dev, void *stream);
 
-/* Smear the current state only (alpha_dev required, alpha_dot_dev optional). */
+/* Smear the current state only (alpha_dev required, alpha_dot_dev optional).  A
+ * bubble whose radius is NaN (one flagged non-finite by a step) adds nothing. */
 pab_status pab_el_smear(pab_el_t *e, double *alpha_dev, double *alpha_dot_dev, void *stream);
 
 /* Synchronise `stream`, read and reset the status as pab_status_flags does. */

@@ -35,6 +35,29 @@ def test_smear_matches_oracle_including_wide_kernels_and_edges():
     cl.close()
 
 
+def test_bubble_with_nan_radius_adds_nothing_to_the_smear():
+    import torch
+    wl = _cloud(seed=73)
+    g = np.random.default_rng(73)
+    R = wl.R0 * g.uniform(0.5, 3.0, size=wl.n_bubbles)
+    V = g.normal(size=wl.n_bubbles)
+    k = wl.n_bubbles // 2
+    Rn = R.copy()
+    Rn[k] = np.nan
+    cl = BubbleCloud(wl.pos, wl.R0, wl.edge, wl.edge, wl.edge, wl.dx)
+    cl.set_state(torch.as_tensor(Rn, device="cuda"), torch.as_tensor(V, device="cuda"))
+    a = torch.empty(wl.edge ** 3, dtype=torch.float64, device="cuda")
+    ad = torch.empty_like(a)
+    cl.smear(a, ad)
+    keep = np.arange(wl.n_bubbles) != k
+    oa, oad = oracle.el_smear(wl.pos[:, keep], R[keep], V[keep], wl.edge, wl.edge, wl.edge, wl.dx)
+    a, ad = a.cpu().numpy(), ad.cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(ad))
+    np.testing.assert_allclose(a, oa, rtol=1e-12, atol=1e-14 * oa.max())
+    np.testing.assert_allclose(ad, oad, rtol=1e-12, atol=1e-14 * np.abs(oad).max())
+    cl.close()
+
+
 def test_advance_and_smear_match_oracle_over_steps():
     import torch
     wl = _cloud(edge=16, alpha0=3e-3, seed=72)

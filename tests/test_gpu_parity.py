@@ -246,3 +246,50 @@ def test_external_nb_field_scales_alpha_linearly():
     # p_bw: gas series from the step's base (fused) against the exact value (reduce-only)
     torch.testing.assert_close(m2[5], m1[5], rtol=1e-14, atol=0)
     a.close()
+
+
+def _planted_proposals(wl):
+    """Carried step proposals [B][C] that the controller must fall back from (NaN, zeros,
+    negative, infinite, beyond 2^104, huge but exactly convertible, above dt) next to valid
+    ones (subnormal, a third of dt, dt itself); returns (h, the mask of the valid ones)."""
+    dt = np.float32(wl.dt)
+    special = np.array([np.nan, 0.0, -0.0, -1e-9, np.inf, 3e38, 1e31, 2.0 * dt,
+                        1e-40, dt / np.float32(3.0), dt], dtype=np.float32)
+    valid = np.array([False] * 8 + [True] * 3)
+    idx = np.arange(wl.n_bins * wl.n_cells).reshape(wl.n_bins, wl.n_cells) % special.size
+    return special[idx], valid[idx]
+
+
+def test_invalid_carried_step_size_falls_back_to_dt():
+    """The first trial of a flow step is min(h, dt) for a positive finite carried h and dt
+    otherwise: the FP64 path against the oracle from the same planted proposals, and the
+    mixed path bit for bit against the same run with every invalid proposal set to 0."""
+    import torch
+    wl = workloads.config_small()
+    R0, _ = oracle.bins(wl.n_bins, wl.R0ref, wl.s, wl.span_K)
+    R = np.repeat(R0[:, None], wl.n_cells, axis=1)
+    V = np.zeros_like(R)
+    h, valid = _planted_proposals(wl)
+    steps = 5
+    o = run_oracle(wl, steps, state=(R, V, h))
+    s = pab.Solver(wl.n_cells, wl.n_bins, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K,
+                   alpha0=wl.alpha0, record_attempts=1, **wl.fluid)
+    s.set_state(torch.as_tensor(R, device="cuda"), torch.as_tensor(V, device="cuda"),
+                torch.as_tensor(h, device="cuda"))
+    g = run_gpu(wl, steps, solver=s)
+    _check(g, o, wl.fluid, TOL_ADAPT)
+    assert g["status"]["flags"] == 0
+    s.close()
+
+    outs = []
+    for hh in (h, np.where(valid, h, np.float32(0.0))):
+        m = pab.Solver(wl.n_cells, wl.n_bins, precision="mixed", s_lognormal=wl.s, R0ref=wl.R0ref,
+                       span_K=wl.span_K, alpha0=wl.alpha0, **wl.fluid)
+        m.set_state(torch.as_tensor(R, device="cuda"), torch.as_tensor(V, device="cuda"),
+                    torch.as_tensor(hh, device="cuda"))
+        for n in range(steps):
+            m.step(torch.as_tensor(wl.pressure_step(n), device="cuda"), wl.dt)
+        outs.append([x.cpu() for x in m.get_state()])
+        m.close()
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
