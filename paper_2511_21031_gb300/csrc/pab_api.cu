@@ -169,13 +169,9 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->inv_rho = 1.0 / c->rho;
     K->c = c->c;
     K->inv_c = 1.0 / c->c;
-    K->mu = c->mu;
-    K->sigma = c->sigma;
-    K->gamma = c->gamma;
     K->pv = c->pv;
     K->p0 = c->p0;
     K->three_gamma = 3.0 * c->gamma;
-    K->four_mu = 4.0 * c->mu;
     K->two_sigma = 2.0 * c->sigma;
     K->ic_rho = K->inv_c / c->rho;
     K->fmu_ic_rho = 4.0 * c->mu * K->inv_c / c->rho;
@@ -185,20 +181,20 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->m05_inv_c = -0.5 * K->inv_c;
     K->tol = c->tol;
     K->tol3 = 3.0 * c->tol;
-    K->cbrt_tol = std::cbrt(c->tol);
     K->v_floor = c->v_floor >= 0.0 ? c->v_floor : 1e-3 * std::sqrt(c->p0 / c->rho);
     K->v_collapse = c->c / 20.0;
     K->r_collapse = 0.2;
     K->inv_rhof = (float)K->inv_rho;
     K->inv_cf = (float)K->inv_c;
-    K->four_muf = (float)K->four_mu;
+    K->four_muf = (float)(4.0 * c->mu);
     K->two_sigmaf = (float)K->two_sigma;
     K->three_gammaf = (float)K->three_gamma;
     K->ic_rhof = (float)K->ic_rho;
     K->tg_ic_rhof = (float)(K->three_gamma * K->ic_rho);
     K->fmu_ic_rhof = (float)K->fmu_ic_rho;
     K->v_floorf = (float)K->v_floor;
-    K->cbrt_tolf = (float)K->cbrt_tol;
+    K->cbrt_tolf = (float)std::cbrt(c->tol);
+    K->tol3f = (float)K->tol3;
     K->v_collapsef = (float)K->v_collapse;
     K->r_collapsef = (float)K->r_collapse;
     K->cf = (float)c->c;

@@ -143,9 +143,10 @@ __global__ void __launch_bounds__(kOrderThreads)
 // Persistent batch kernel.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
-// 64 registers (512 threads x 2 CTAs): twice the resident warps of the
-// unbounded build for some spills.
-__global__ void __launch_bounds__(512, 2)
+// At most 80 registers: the per-bin terms in shared memory (about 37 KB per CTA
+// at Nb = 51) leave room for 6 CTAs of 4 warps per SM, which 80 registers still
+// fit; the unbounded build takes 118 (4 CTAs), 64 would spill.
+__global__ void __maxnreg__(80)
     batch_kernel(const SlotDesc *__restrict__ slots, const int *__restrict__ order,
                  const long long *__restrict__ start, Queue *q, SlotCounters *cnt,
                  int bins_per_grab, int max_bins)

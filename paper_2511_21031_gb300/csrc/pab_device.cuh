@@ -463,33 +463,44 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
         }
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
-        double err, nR = 0.0, nV = 0.0;
-        float d3R = 0.0f, d3V = 0.0f;
-        bool ok, full64;
+        const float htf = d2f(ht);
+        double nR = 0.0, nV = 0.0;
+        float d3R = 0.0f, d3V = 0.0f, errf;
+        bool ok, accept, full64;
         if (xi < xi_collapse || fabsf(v) > K.v_collapsef) {
             const Trial64Out tr = collapse_trial64(K, bc, p_inf, bc.R0 + xi64, V, ht);
             ++n64;
-            err = tr.err;
             ok = tr.ok;
+            accept = ok && le(tr.err, K.tol);
+            errf = d2f(tr.err);
             nR = tr.R;
             nV = tr.V;
             full64 = true;
         } else {
-            const Incr32 in = incr32(K, bc, A, xi, v, d2f(ht));
+            const Incr32 in = incr32(K, bc, A, xi, v, htf);
             d3R = in.d3R;
             d3V = in.d3V;
-            const double eR = embedded_diff(in.k1R, in.k2R, in.k3R);
-            const double eV = embedded_diff(in.k1V, in.k2V, in.k3V);
+            const double aeR = abs_nn(embedded_diff(in.k1R, in.k2R, in.k3R));
+            const double aeV = abs_nn(embedded_diff(in.k1V, in.k2V, in.k3V));
             const float R3f = __fadd_rn(bc.R0f, __fadd_rn(xi, d3R));
-            const float rR = rcp32(__fmul_rn(3.0f, fabsf(R3f)));
-            const float rV = rcp32(__fmul_rn(3.0f, fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf)));
-            err = max_nn(abs_nn(eR) * f2d_fin(rR), abs_nn(eV) * f2d_fin(rV));
+            const float aRf = fabsf(R3f);
+            const float aVf = fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf);
             ok = in.ok && (R3f > 0.0f);
+            // err <= tol as |e_R| <= 3 tol |R3| and |e_Rdot| <= 3 tol max(|Rdot3|, v_floor):
+            // the FP64 estimate against thresholds formed in FP32 (a relative rounding of
+            // 6e-8 on tol, no FP64 product); the growth factor takes err from the FP32
+            // images of the same quantities
+            accept = ok && le(aeR, f2d_fin(__fmul_rn(K.tol3f, aRf))) &&
+                     le(aeV, f2d_fin(__fmul_rn(K.tol3f, aVf)));
+            errf = fmaxf(__fmul_rn(d2f(aeR), rcp32(__fmul_rn(3.0f, aRf))),
+                         __fmul_rn(d2f(aeV), rcp32(__fmul_rn(3.0f, aVf))));
             full64 = false;
         }
         ++n;
-        const float fac = growth_factor(K, d2f(err), ok);
-        if (ok && le(err, K.tol)) {
+        const float fac = growth_factor(K, errf, ok);
+        // the next proposal, kept in FP32 between calls anyway: an exact FP32 product
+        const double hn = f2d_fin(__fmul_rn(htf, fac));
+        if (accept) {
             if (full64) {
                 xi64 = nR - bc.R0;
                 V = nV;
@@ -505,13 +516,13 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             }
             if (last) {
                 const bool clipped = !le(h, rem);
-                h = (clipped && fac >= 1.0f) ? h : ht * f2d_fin(fac);
+                h = (clipped && fac >= 1.0f) ? h : hn;
                 break;
             }
             rem -= ht;
-            h = ht * f2d_fin(fac);
+            h = hn;
         } else {
-            h = ht * f2d_fin(fac);
+            h = hn;
         }
     }
     R = bc.R0 + xi64;

@@ -45,9 +45,8 @@ struct StepConst {
     int32_t gas_mode;
     int32_t max_attempts;
     int32_t n_fixed;      // > 0: fixed mode with n_fixed sub-steps
-    double rho, inv_rho, c, inv_c, mu, sigma, gamma, pv, p0;
+    double rho, inv_rho, c, inv_c, pv, p0;
     double three_gamma;   // 3 gamma
-    double four_mu;       // 4 mu
     double two_sigma;     // 2 sigma
     double ic_rho;        // (1/c)/rho
     double fmu_ic_rho;    // 4 mu (1/c)/rho
@@ -57,7 +56,6 @@ struct StepConst {
     double m05_inv_c;     // -0.5 / c
     double tol;
     double tol3;          // 3 tol (Trial carries three times the embedded difference)
-    double cbrt_tol;      // tol^(1/3)
     double v_floor;
     double v_collapse;    // mixed: |Rdot| above this takes the FP64 path (c/20)
     double r_collapse;    // mixed: R/R0 below this takes the FP64 path (0.2)
@@ -84,6 +82,7 @@ struct StepConst {
     float inv_rhof, inv_cf, four_muf, two_sigmaf, three_gammaf, ic_rhof, fmu_ic_rhof, v_floorf;
     float cbrt_tolf, v_collapsef, r_collapsef, cf;
     float tg_ic_rhof;     // 3 gamma (1/c)/rho
+    float tol3f;          // 3 tol
     BinConst bins[PAB_MAX_BINS];
 };
 
