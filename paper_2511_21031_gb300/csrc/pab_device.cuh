@@ -261,9 +261,11 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
 // FP64, at two FP64 additions where the direct FP64 form takes three.  For
 // finite |k| < 2^100 (the parts then stay inside f2d_fin's range); a trial's
 // increments are many orders below that, and a non-finite one fails the trial.
-__device__ __forceinline__ double embedded_diff(float k1, float k2, float k3)
+// d, the FP32 difference fl(2 k3 - fl(k1 + k2)), is returned too: it differs
+// from the exact difference only by the two rounding errors.
+__device__ __forceinline__ double embedded_diff(float k1, float k2, float k3, float &d)
 {
-    float s, es, d, ed;
+    float s, es, ed;
     two_sum(k1, k2, s, es);
     two_sum(__fmul_rn(2.0f, k3), -s, d, ed);
     return f2d_fin(d) + (f2d_fin(ed) - f2d_fin(es));
@@ -312,8 +314,9 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
     Trial t;
     t.R = R + f2d_fin(in.d3R);
     t.V = V + f2d_fin(in.d3V);
-    t.eR = embedded_diff(in.k1R, in.k2R, in.k3R);
-    t.eV = embedded_diff(in.k1V, in.k2V, in.k3V);
+    float dR, dV;
+    t.eR = embedded_diff(in.k1R, in.k2R, in.k3R, dR);
+    t.eV = embedded_diff(in.k1V, in.k2V, in.k3V, dV);
     t.ok = in.ok && gt0(t.R) && finite64(t.V);
     return t;
 }
@@ -480,8 +483,9 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const Incr32 in = incr32(K, bc, A, xi, v, htf);
             d3R = in.d3R;
             d3V = in.d3V;
-            const double aeR = abs_nn(embedded_diff(in.k1R, in.k2R, in.k3R));
-            const double aeV = abs_nn(embedded_diff(in.k1V, in.k2V, in.k3V));
+            float dR, dV;
+            const double aeR = abs_nn(embedded_diff(in.k1R, in.k2R, in.k3R, dR));
+            const double aeV = abs_nn(embedded_diff(in.k1V, in.k2V, in.k3V, dV));
             const float R3f = __fadd_rn(bc.R0f, __fadd_rn(xi, d3R));
             const float aRf = fabsf(R3f);
             const float aVf = fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf);
@@ -489,11 +493,12 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             // err <= tol as |e_R| <= 3 tol |R3| and |e_Rdot| <= 3 tol max(|Rdot3|, v_floor):
             // the FP64 estimate against thresholds formed in FP32 (a relative rounding of
             // 6e-8 on tol, no FP64 product); the growth factor takes err from the FP32
-            // images of the same quantities
+            // differences d (they differ from the estimate only where it is tiny, and the
+            // factor is 5 there either way) and the FP32 images of R3, Rdot3
             accept = ok && le(aeR, f2d_fin(__fmul_rn(K.tol3f, aRf))) &&
                      le(aeV, f2d_fin(__fmul_rn(K.tol3f, aVf)));
-            errf = fmaxf(__fmul_rn(d2f(aeR), rcp32(__fmul_rn(3.0f, aRf))),
-                         __fmul_rn(d2f(aeV), rcp32(__fmul_rn(3.0f, aVf))));
+            errf = fmaxf(__fmul_rn(fabsf(dR), rcp32(__fmul_rn(3.0f, aRf))),
+                         __fmul_rn(fabsf(dV), rcp32(__fmul_rn(3.0f, aVf))));
             full64 = false;
         }
         ++n;
@@ -610,8 +615,9 @@ __device__ __forceinline__ double quad_terms_mixed(const StepConst &K, const Bin
     const float u = xi * bc.invR0f;
     const float Rf = bc.R0f + xi, Vf = d2f(V);
     const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-    const float dev = bc.dpeqf + pgdev + div32(K.two_sigmaf * u - K.four_muf * Vf, Rf);
-    const float wr2f = d2f(wr2), wr3f = d2f(wr3);
+    const float iRf = rcp32(Rf);
+    const float dev = bc.dpeqf + pgdev + (K.two_sigmaf * u - K.four_muf * Vf) * iRf;
+    const float wr3f = d2f(wr3), wr2f = wr3f * iRf;  // w R^2 = w R^3 / R
     tf[0] = wr2f * Vf;
     tf[1] = wr3f * dev;
     tf[2] = wr3f * Vf * Vf;

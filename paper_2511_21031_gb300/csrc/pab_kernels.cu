@@ -57,11 +57,11 @@ __device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinCo
     const float Rf = bc.R0f + xi;
     const float u = xi * bc.invR0f;
     const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-    const float dev = pgdev + div32(K.two_sigmaf * u - K.four_muf * v, Rf);
-    const double wr2 = bc.w * R * R;
-    const double wr3 = wr2 * R;
-    const float wr2f = d2f(wr2);
+    const float iRf = rcp32(Rf);
+    const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * v) * iRf;
+    const double wr3 = bc.w * R * R * R;
     const float wr3f = d2f(wr3);
+    const float wr2f = wr3f * iRf;  // w R^2 = w R^3 / R
     acc.add_m3(wr3);
     acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
     acc.m2vf = fmaf(wr2f, v, acc.m2vf);

@@ -90,7 +90,8 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
         if (isfinite(k1) && isfinite(k2) && isfinite(k3) && fabsf(k1) < 0x1p100f &&
             fabsf(k2) < 0x1p100f && fabsf(k3) < 0x1p100f) {  // the helper's domain
             const double ref = 2.0 * (double)k3 - ((double)k1 + (double)k2);
-            const double got = pab::embedded_diff(k1, k2, k3);
+            float d32;
+            const double got = pab::embedded_diff(k1, k2, k3, d32);
             const double tol = 4.0 * DBL_EPSILON * (fabs(2.0 * (double)k3) + fabs((double)k1) +
                                                     fabs((double)k2));
             bad |= (!(fabs(got - ref) <= tol)) << 7;
