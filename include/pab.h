@@ -55,7 +55,11 @@ typedef enum {
     PAB_ESTATE = 6         /* call not valid in the handle's state */
 } pab_status;
 
-/* precision */
+/* precision: PAB_FP64 computes every step in FP64.  PAB_MIXED evaluates the
+ * Keller-Miksis right-hand sides in FP32, written in deviations from
+ * equilibrium, and keeps in FP64 the state, the embedded error estimate and the
+ * accept decision, the time bookkeeping and a compensated alpha sum; bins near
+ * collapse (R < 0.2 R0 or |Rdot| > c/20) take whole FP64 trials. */
 enum { PAB_FP64 = 0, PAB_MIXED = 1 };
 /* stepper */
 enum { PAB_ADAPTIVE = 0, PAB_FIXED = 1 };
@@ -181,7 +185,9 @@ pab_status pab_status_flags(pab_t *h, uint32_t *flags, int64_t *n_flagged, int64
                             int64_t *n_fp64, void *stream);
 
 /* Checkpoint / resume: copy the state out of / into the handle (device
- * buffers [Nb][C]; h_dev may be NULL to leave h untouched on set). */
+ * buffers [Nb][C]; h_dev may be NULL to leave h untouched on set).  A carried
+ * h that is not a number in (0, dt] (NaN, zero, negative, infinite or above
+ * the call's dt) makes the next call start that bin's step at dt. */
 pab_status pab_get_state(pab_t *h, double *R_dev, double *Rdot_dev, float *h_dev, void *stream);
 pab_status pab_set_state(pab_t *h, const double *R_dev, const double *Rdot_dev, const float *h_dev,
                          void *stream);
