@@ -71,7 +71,7 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
  *                 6 (float)x (bit patterns, with subnormal float results
  *                 flushed to a signed zero; NaN for NaN), 7 the embedded
  *                 difference 2 k3 - (k1 + k2) of k1 = f, k2 = (float)x,
- *                 k3 = (float)y against FP64 within 4 ulp of its terms
+ *                 k3 = (float)y against FP64 within 2^-46 of its terms
  *                 (where |k1|, |k2|, |k3| < 2^100),
  *                 8 2|x| and 2s (s the subnormal or zero with the bits of |x|
  *                 shifted right by 12) against the FP64 additions, 9 the

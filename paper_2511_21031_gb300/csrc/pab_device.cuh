@@ -255,20 +255,20 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
 
 // The embedded difference 2 k3 - (k1 + k2) of FP32 increments, from exact
 // parts: k1 + k2 = s + e_s and 2 k3 - s = d + e_d by FP32 TwoSum (2 k3 is
-// exact), so the difference is d + (e_d - e_s) exactly.  The three parts are
-// combined in FP64 (e_d - e_s is exact there whenever their exponents differ
-// by less than 29), so the result is the exact difference rounded once to
-// FP64, at two FP64 additions where the direct FP64 form takes three.  For
-// finite |k| < 2^100 (the parts then stay inside f2d_fin's range); a trial's
-// increments are many orders below that, and a non-finite one fails the trial.
-// d, the FP32 difference fl(2 k3 - fl(k1 + k2)), is returned too: it differs
-// from the exact difference only by the two rounding errors.
+// exact), so the difference is d + (e_d - e_s) exactly.  The two rounding
+// errors are combined in FP32 (e_d - e_s rounded once, an error of at most
+// 2^-48 (|d| + |s|)) and added to d in FP64: the difference to within 2^-47 of
+// the increments at one FP64 addition, where promoting the k's and subtracting
+// in FP64 takes three (and keeps a relative error of 2^-53 of the increments).
+// For finite |k| < 2^100 (the parts then stay inside f2d_fin's range); a
+// trial's increments are many orders below that, and a non-finite one fails
+// the trial.
 __device__ __forceinline__ double embedded_diff(float k1, float k2, float k3, float &d)
 {
     float s, es, ed;
     two_sum(k1, k2, s, es);
     two_sum(__fmul_rn(2.0f, k3), -s, d, ed);
-    return f2d_fin(d) + (f2d_fin(ed) - f2d_fin(es));
+    return f2d_fin(d) + f2d_fin(__fsub_rn(ed, es));
 }
 
 // The three FP32 right-hand sides of one trial, on increments from the state

@@ -84,16 +84,18 @@ __global__ void bits_check_kernel(long long n, const float *f, const double *x, 
         } else {
             bad |= (!isnan(pab::d2f(xi))) << 6;
         }
-        // the embedded difference against the same quantity in FP64 (two
-        // roundings there, about one in the library)
+        // the embedded difference against the same quantity in FP64: within
+        // 2^-46 of the terms (the library combines the two FP32 rounding errors
+        // in FP32, an error of at most 2^-47 of them; the FP64 reference rounds
+        // twice)
         const float k1 = f[i], k2 = __double2float_rn(xi), k3 = __double2float_rn(yi);
         if (isfinite(k1) && isfinite(k2) && isfinite(k3) && fabsf(k1) < 0x1p100f &&
             fabsf(k2) < 0x1p100f && fabsf(k3) < 0x1p100f) {  // the helper's domain
             const double ref = 2.0 * (double)k3 - ((double)k1 + (double)k2);
             float d32;
             const double got = pab::embedded_diff(k1, k2, k3, d32);
-            const double tol = 4.0 * DBL_EPSILON * (fabs(2.0 * (double)k3) + fabs((double)k1) +
-                                                    fabs((double)k2));
+            const double tol = 0x1p-46 * (fabs(2.0 * (double)k3) + fabs((double)k1) +
+                                           fabs((double)k2));
             bad |= (!(fabs(got - ref) <= tol)) << 7;
         }
         // the short float -> double on its domain (finite, |f| < 2^104)
