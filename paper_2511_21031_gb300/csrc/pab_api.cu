@@ -200,12 +200,13 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->cf = (float)c->c;
     K->tr_Rg = c->R_g;
     K->tr_Rv = c->R_v;
-    K->tr_Tw = c->T_w;
-    K->tr_RvTw = c->R_v * c->T_w;
+    K->tr_RvTw_4pi = c->R_v * c->T_w / (4.0 * M_PI);
     K->tr_rho_vw = c->gas_mode == PAB_GAS_TRANSFER ? c->pv / (c->R_v * c->T_w) : 0.0;
     K->tr_inv_RgTw = c->gas_mode == PAB_GAS_TRANSFER ? 1.0 / (c->R_g * c->T_w) : 0.0;
-    K->tr_kT = (c->gamma - 1.0) / c->gamma * c->k_bw * c->beta_T;
-    K->tr_Dc = c->D_vg * c->beta_c;
+    const double kT = (c->gamma - 1.0) / c->gamma * c->k_bw * c->beta_T;
+    K->tr_kT_43pi = 4.0 / 3.0 * M_PI * kT;
+    K->tr_kT_Tw = kT * c->T_w;
+    K->tr_Dc_4pi = 4.0 * M_PI * c->D_vg * c->beta_c;
     double m3 = 0.0;
     for (int i = 0; i < c->n_bins; ++i) {
         pab::BinConst &b = K->bins[i];

@@ -62,12 +62,12 @@ struct StepConst {
     double nb_default;    // n_b when the caller passes no n_b field
     // contents with heat and mass transfer (gas_mode PAB_GAS_TRANSFER)
     double tr_Rg, tr_Rv;  // gas constants of the gas and of the vapour
-    double tr_Tw;         // wall temperature
-    double tr_RvTw;       // R_v T_w
+    double tr_RvTw_4pi;   // R_v T_w / (4 pi)
     double tr_rho_vw;     // pv / (R_v T_w): vapour density at the wall
     double tr_inv_RgTw;   // 1 / (R_g T_w)
-    double tr_kT;         // (gamma - 1)/gamma k_bw beta_T
-    double tr_Dc;         // D beta_c
+    double tr_kT_43pi;    // (4 pi/3) (gamma - 1)/gamma k_bw beta_T
+    double tr_kT_Tw;      // (gamma - 1)/gamma k_bw beta_T T_w
+    double tr_Dc_4pi;     // 4 pi D beta_c
     // (1 + d)^(-3 gamma) = sum_k gas_c[k] d^k for |d| <= gas_dmax (truncation below half an ulp)
     double gas_c[kGasTerms];
     double gas_dmax;

@@ -41,20 +41,20 @@ __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc
 // share one reciprocal: X = D beta_c rho_bw (rho_vw D2 - m_v R_g rho_bw) / (D2 rho_gw).
 // The heat term (gamma - 1)/gamma k_bw beta_T (T_w - T_mean)/R shares the factor 1/R:
 //   dp_b/dt = 3 gamma/R ((R_v T_w X + kT (T_w - T_mean))/R - Rdot p_b),
-//   dm_v/dt = 4 pi R^2 mdot = 4 pi R X.
+//   dm_v/dt = 4 pi R^2 mdot = 4 pi R X,
+// with the constants folded in: X4 = 4 pi X, and kT T_mean = (4 pi/3) kT p_b R^3/(m_v R_v + m_g R_g).
 __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, const State4 &s,
                                                double iR, double &dpb, double &dmv)
 {
-    const double Vb = (4.0 / 3.0 * kPi) * s.R * s.R * s.R;
-    const double T_mean = s.pb * Vb * rcp64(fma(s.mv, K.tr_Rv, mRg));
+    const double T3 = s.pb * s.R * s.R * s.R * rcp64(fma(s.mv, K.tr_Rv, mRg));  // T_mean 3/(4 pi)
     const double mvRg = s.mv * K.tr_Rg;
     const double D2 = mvRg + mRg;                          // (m_v + m_g) R_g
     const double rho_gw = (s.pb - K.pv) * K.tr_inv_RgTw;   // gas density at the wall
     const double rho_bw = K.tr_rho_vw + rho_gw;
-    const double X = K.tr_Dc * rho_bw * fma(K.tr_rho_vw, D2, -mvRg * rho_bw) * rcp64(D2 * rho_gw);
-    const double q = fma(K.tr_RvTw, X, K.tr_kT * (K.tr_Tw - T_mean));
+    const double X4 = K.tr_Dc_4pi * rho_bw * fma(K.tr_rho_vw, D2, -mvRg * rho_bw) * rcp64(D2 * rho_gw);
+    const double q = fma(K.tr_RvTw_4pi, X4, fma(-K.tr_kT_43pi, T3, K.tr_kT_Tw));
     dpb = K.three_gamma * iR * fma(q, iR, -s.V * s.pb);
-    dmv = (4.0 * kPi) * s.R * X;
+    dmv = s.R * X4;
 }
 
 // Keller-Miksis, Eq. (keller_miksis), with the state p_b, regrouped as in
