@@ -249,6 +249,7 @@ struct pab_el_s {
     float *h = nullptr;
     pab::Counters *counters = nullptr;
     pab::Counters *counters_host = nullptr;
+    double *gas_tab = nullptr;  // gas-term nodes (K.gas_tab points here), shared by every bubble
     char err[512] = {0};
 };
 
@@ -387,6 +388,23 @@ pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const doub
         if (err == cudaSuccess)
             err = cudaMemsetAsync(e->h, 0, (size_t)N * sizeof(float), s);
     }
+    // the gas-term node table of the polytropic gas (a function of R/R0 alone, so one
+    // table serves every bubble)
+    std::vector<double> tab;
+    if (err == cudaSuccess && c.gas_mode == PAB_GAS_POLYTROPIC) {
+        int J = 0;
+        double il2q = 0.0;
+        pab::gas_table(3.0 * c.gamma, e->K.gas_dmax_tab, &tab, &J, &il2q);
+        err = cudaMallocAsync((void **)&e->gas_tab, tab.size() * sizeof(double), s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(e->gas_tab, tab.data(), tab.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess) {
+            e->K.gas_tab = e->gas_tab;
+            e->K.gas_J = J;
+            e->K.gas_inv_log2q = (float)il2q;
+        }
+    }
     if (err == cudaSuccess)
         err = cudaStreamSynchronize(s);  // the host tables above go out of scope
     if (err != cudaSuccess) {
@@ -405,7 +423,7 @@ void pab_el_destroy(pab_el_t *e)
     if (!e)
         return;
     cudaStream_t s = e->create_stream;
-    void *bufs[] = {e->pos, e->cell, e->bub, e->R, e->V, e->h, e->counters};
+    void *bufs[] = {e->pos, e->cell, e->bub, e->R, e->V, e->h, e->counters, e->gas_tab};
     for (void *b : bufs)
         if (b)
             cudaFreeAsync(b, s);
