@@ -355,6 +355,14 @@ struct pab_batch_s {
     std::vector<long long> offset;          // arena offset of each slot
     std::vector<long long> size;            // bin-states of each slot
     std::map<long long, long long> free_ranges;  // offset -> length
+    // gas-term node tables shared by the slots of one 3 gamma (keyed by its bit
+    // pattern), kept until the batch is destroyed
+    struct GasTab {
+        double *dev;
+        int J;
+        double inv_log2q;
+    };
+    std::map<unsigned long long, GasTab> gas_tabs;
     long long used = 0;
     size_t smem_bytes = 0;
     int block_warps = 8;
@@ -599,6 +607,8 @@ void pab_batch_destroy(pab_batch_t *b)
     for (void *p : dev)
         if (p)
             cudaFreeAsync(p, s);
+    for (auto &kv : b->gas_tabs)
+        cudaFreeAsync(kv.second.dev, s);
     cudaStreamSynchronize(s);
     void *host[] = {b->K_host, b->desc_host, b->cnt_host};
     for (void *p : host)
@@ -641,6 +651,29 @@ pab_status pab_batch_admit(pab_batch_t *b, const pab_config *cfg, void *stream, 
     cudaError_t e = cudaStreamSynchronize(s);  // no step in flight reads the slot tables
     pab::StepConst &K = b->K_host[s_idx];
     pab::make_const(cfg, R0, w, &K);
+    std::vector<double> tab;  // host values of a new gas table, alive until the sync below
+    if (e == cudaSuccess && cfg->gas_mode == PAB_GAS_POLYTROPIC) {
+        const double a = 3.0 * cfg->gamma;
+        unsigned long long key;
+        std::memcpy(&key, &a, sizeof(key));
+        auto it = b->gas_tabs.find(key);
+        if (it == b->gas_tabs.end()) {
+            pab_batch_s::GasTab t{nullptr, 0, 0.0};
+            pab::gas_table(a, K.gas_dmax_tab, &tab, &t.J, &t.inv_log2q);
+            e = cudaMallocAsync((void **)&t.dev, tab.size() * sizeof(double), s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t.dev, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                it = b->gas_tabs.emplace(key, t).first;
+            else if (t.dev)
+                cudaFreeAsync(t.dev, s);
+        }
+        if (e == cudaSuccess) {
+            K.gas_tab = it->second.dev;
+            K.gas_J = it->second.J;
+            K.gas_inv_log2q = (float)it->second.inv_log2q;
+        }
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->K_dev + s_idx, &K, sizeof(pab::StepConst), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
