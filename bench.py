@@ -55,10 +55,39 @@ FP64_FLOPS_PER_BINSTEP = 26.1
 # on the 64^3 x 31 grid, 285.6 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 35.1
 FP64_PIPE_ACTIVE_NCU = 0.910
+# The mixed step kernel on the same 64^3 x 31 launch (ncu --set full): DRAM bytes
+# per bin-step and the utilisations that bound it (issue slots first).
+MIXED_DRAM_BYTES_PER_BINSTEP = 35.3
+MIXED_ISSUE_ACTIVE_NCU = 0.784
+MIXED_FP64_PIPE_ACTIVE_NCU = 0.699
+MIXED_FMA_PIPE_ACTIVE_NCU = 0.366
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of this machine's GPUs, else the fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (no measured peak available)"
 
 
 def _dist():
     return pdist.env_rank()
+
+
+def _mixed_roofline(bin_steps_per_s):
+    """The mixed kernel against its ceilings: HBM traffic at this rate against the measured
+    copy bandwidth (live), and the issue and pipe utilisations of its ncu capture."""
+    peak, src = _hbm_peak()
+    gbs = MIXED_DRAM_BYTES_PER_BINSTEP * bin_steps_per_s / 1e9
+    return {"bound": "issue", "achieved_hbm_gbs": gbs, "hbm_peak_gbs": peak, "hbm_frac": gbs / peak,
+            "hbm_peak_source": src, "issue_active_ncu": MIXED_ISSUE_ACTIVE_NCU,
+            "fp64_pipe_active_ncu": MIXED_FP64_PIPE_ACTIVE_NCU,
+            "fma_pipe_active_ncu": MIXED_FMA_PIPE_ACTIVE_NCU,
+            "counters": "profiles/step_kernel_mixed_grid64.md"}
 
 
 def make_workload(name, rank, edge=0):
@@ -586,6 +615,7 @@ def run_ours(args):
                 "fp64_trial_fraction": r["status"]["n_fp64"] / max(1, r["status"]["n_attempts"]),
                 "speedup_vs_fp64_grid128": (vbs / (r["ms_total"] * 1e-3)) / value,
                 "error_vs_fp64_oracle": _mixed_error_sample(vwl, min(total, 40)),
+                "roofline": _mixed_roofline(vbs / (r["ms_total"] * 1e-3)),
             })
             vs.close()
             del vps
