@@ -61,6 +61,11 @@ MIXED_DRAM_BYTES_PER_BINSTEP = 35.3
 MIXED_ISSUE_ACTIVE_NCU = 0.784
 MIXED_FP64_PIPE_ACTIVE_NCU = 0.699
 MIXED_FMA_PIPE_ACTIVE_NCU = 0.366
+# The batch kernel on 16 instances (ncu --set full): DRAM bytes per bin-state and utilisations.
+BATCH_DRAM_BYTES_PER_BINSTEP = 42.5
+BATCH_ISSUE_ACTIVE_NCU = 0.781
+BATCH_FP64_PIPE_ACTIVE_NCU = 0.583
+BATCH_FMA_PIPE_ACTIVE_NCU = 0.376
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -78,16 +83,22 @@ def _dist():
     return pdist.env_rank()
 
 
-def _mixed_roofline(bin_steps_per_s):
-    """The mixed kernel against its ceilings: HBM traffic at this rate against the measured
+def _mixed_roofline(bin_steps_per_s, batched=False):
+    """A mixed kernel against its ceilings: HBM traffic at this rate against the measured
     copy bandwidth (live), and the issue and pipe utilisations of its ncu capture."""
     peak, src = _hbm_peak()
-    gbs = MIXED_DRAM_BYTES_PER_BINSTEP * bin_steps_per_s / 1e9
+    if batched:
+        per, iss, f64, fma, prof = (BATCH_DRAM_BYTES_PER_BINSTEP, BATCH_ISSUE_ACTIVE_NCU,
+                                    BATCH_FP64_PIPE_ACTIVE_NCU, BATCH_FMA_PIPE_ACTIVE_NCU,
+                                    "profiles/batch_kernel_mixed_16inst.md")
+    else:
+        per, iss, f64, fma, prof = (MIXED_DRAM_BYTES_PER_BINSTEP, MIXED_ISSUE_ACTIVE_NCU,
+                                    MIXED_FP64_PIPE_ACTIVE_NCU, MIXED_FMA_PIPE_ACTIVE_NCU,
+                                    "profiles/step_kernel_mixed_grid64.md")
+    gbs = per * bin_steps_per_s / 1e9
     return {"bound": "issue", "achieved_hbm_gbs": gbs, "hbm_peak_gbs": peak, "hbm_frac": gbs / peak,
-            "hbm_peak_source": src, "issue_active_ncu": MIXED_ISSUE_ACTIVE_NCU,
-            "fp64_pipe_active_ncu": MIXED_FP64_PIPE_ACTIVE_NCU,
-            "fma_pipe_active_ncu": MIXED_FMA_PIPE_ACTIVE_NCU,
-            "counters": "profiles/step_kernel_mixed_grid64.md"}
+            "hbm_peak_source": src, "issue_active_ncu": iss, "fp64_pipe_active_ncu": f64,
+            "fma_pipe_active_ncu": fma, "counters": prof}
 
 
 def make_workload(name, rank, edge=0):
@@ -627,6 +638,7 @@ def run_ours(args):
     if args.variants and args.batched and ws == 1:
         bv = _bench_batched(args, stream, dev, n_instances=args.batch_instances)
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
+        bv["roofline"] = _mixed_roofline(bv["value"], batched=True)
         variants.append(bv)
 
     if args.variants and args.el and ws == 1:
