@@ -55,12 +55,12 @@ FP64_FLOPS_PER_BINSTEP = 26.1
 # on the 64^3 x 31 grid, 285.6 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 35.1
 FP64_PIPE_ACTIVE_NCU = 0.910
-# The mixed step kernel on the same 64^3 x 31 launch (ncu --set full): DRAM bytes
-# per bin-step and the utilisations that bound it (issue slots first).
-MIXED_DRAM_BYTES_PER_BINSTEP = 35.3
-MIXED_ISSUE_ACTIVE_NCU = 0.784
-MIXED_FP64_PIPE_ACTIVE_NCU = 0.699
-MIXED_FMA_PIPE_ACTIVE_NCU = 0.366
+# The mixed step kernel on a timed 128^3 x 31 launch (ncu --set full, one-warp CTAs):
+# DRAM bytes per bin-step and the utilisations that bound it (issue slots first).
+MIXED_DRAM_BYTES_PER_BINSTEP = 41.7
+MIXED_ISSUE_ACTIVE_NCU = 0.828
+MIXED_FP64_PIPE_ACTIVE_NCU = 0.710
+MIXED_FMA_PIPE_ACTIVE_NCU = 0.390
 # The batch kernel on 16 instances (ncu --set full): DRAM bytes per bin-state and utilisations.
 BATCH_DRAM_BYTES_PER_BINSTEP = 42.5
 BATCH_ISSUE_ACTIVE_NCU = 0.781

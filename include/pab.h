@@ -102,7 +102,8 @@ typedef struct {
     double alpha0;          /* default n_b = alpha0 / (4/3 pi sum_i w_i R0_i^3) */
     double Rdot0_ref;       /* initial Rdot_i = Rdot0_ref * R0_i / R0ref (0: rest) */
     int32_t record_attempts;/* non-zero: keep per-bin trial counts of the last call */
-    int32_t block_warps;    /* warps per CTA, 1..16 (0: default 4); cells per CTA is 32 */
+    int32_t block_warps;    /* warps per CTA, 1..16 (0: the default, 4 in PAB_FP64 and
+                               1 in PAB_MIXED); cells per CTA is 32 */
     /* Contents with heat and mass transfer (gas_mode PAB_GAS_TRANSFER; FP64 only;
      * pab_transfer.h): gas constants of the gas and of the vapour, wall (liquid)
      * temperature, thermal conductivity of the contents, vapour-gas diffusion
@@ -214,7 +215,7 @@ pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
  *
  * There is no handle: the caller passes the configuration and owns the whole
  * state.  cfg is validated exactly as in pab_create (record_attempts and
- * block_warps = 0 are ignored; 4 warps per CTA then).  The bin table is the one
+ * block_warps = 0 are ignored; the default warps per CTA then).  The bin table is the one
  * pab_create builds from cfg (R0_i = R0ref exp(-K s + i 2 K s/(Nb-1)) for Nb > 1).
  * R_dev, Rdot_dev: FP64 [Nb][C] state, advanced in place (device).
  * h_dev: FP32 [Nb][C] carried sub-step, in place (device; 0 before the first

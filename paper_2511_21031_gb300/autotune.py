@@ -18,7 +18,7 @@ import time
 import numpy as np
 
 BATCH_CANDIDATES = tuple((w, c, g) for w in (4, 8, 16) for c in (1, 2, 4, 8) for g in (1, 2))
-SOLVER_CANDIDATES = (2, 4, 8, 16)
+SOLVER_CANDIDATES = (1, 2, 4, 8, 16)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 

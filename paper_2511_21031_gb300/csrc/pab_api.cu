@@ -393,7 +393,7 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
     h->cfg.R0_host = nullptr;
     h->cfg.w_host = nullptr;
     h->create_stream = (cudaStream_t)stream;
-    h->block_warps = cfg->block_warps > 0 ? cfg->block_warps : pab::kDefaultWarps;
+    h->block_warps = cfg->block_warps > 0 ? cfg->block_warps : pab::default_warps(cfg->precision);
     build_const(cfg, R0, w, &h->K);
     cudaError_t e = cudaGetDevice(&h->device);
     const size_t n = n_state(h);
@@ -829,7 +829,8 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
     a.out = moments_dev;
     a.counters = scratch;
     if (e == cudaSuccess)
-        e = pab::launch_step(K, cfg->precision, a, cfg->block_warps > 0 ? cfg->block_warps : pab::kDefaultWarps, s);
+        e = pab::launch_step(K, cfg->precision, a,
+                             cfg->block_warps > 0 ? cfg->block_warps : pab::default_warps(cfg->precision), s);
     if (e == cudaSuccess && status_dev)
         e = cudaMemcpyAsync(status_dev, scratch, sizeof(pab::Counters), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {

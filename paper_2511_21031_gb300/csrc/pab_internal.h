@@ -28,10 +28,14 @@ struct BinConst {
     float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
 };
 
-// Warps per CTA of the step kernels when the configuration leaves it open:
-// measured on the 128^3 x 31 lines, 4 and 8 tie in FP64 and 4 is 16 % faster in
-// mixed precision (a tile's warps wait less for each other at the reduction).
+// Warps per CTA of the step kernels when the configuration leaves it open,
+// measured on the 128^3 x 31 lines: in FP64 1, 2, 4 and 8 warps lie within 1 %
+// (4 is kept); in mixed precision one warp per CTA is 5 % faster than 2 or 4
+// (25.6e9 against 24.4e9 and 24.5e9 bin-steps/s): the warp sums its tile's bins
+// itself, without the cross-warp reduction and its barrier.
 constexpr int kDefaultWarps = 4;
+constexpr int kDefaultWarpsMixed = 1;
+inline int default_warps(int precision) { return precision == PAB_MIXED ? kDefaultWarpsMixed : kDefaultWarps; }
 
 constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
 constexpr int kGasTabTerms = 4;   // degree 3 around the nodes of a gas table
