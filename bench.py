@@ -94,7 +94,7 @@ def _mixed_roofline(bin_steps_per_s, batched=False):
     else:
         per, iss, f64, fma, prof = (MIXED_DRAM_BYTES_PER_BINSTEP, MIXED_ISSUE_ACTIVE_NCU,
                                     MIXED_FP64_PIPE_ACTIVE_NCU, MIXED_FMA_PIPE_ACTIVE_NCU,
-                                    "profiles/step_kernel_mixed_grid64.md")
+                                    "profiles/step_kernel_mixed.md")
     gbs = per * bin_steps_per_s / 1e9
     return {"bound": "issue", "achieved_hbm_gbs": gbs, "hbm_peak_gbs": peak, "hbm_frac": gbs / peak,
             "hbm_peak_source": src, "issue_active_ncu": iss, "fp64_pipe_active_ncu": f64,
