@@ -49,7 +49,7 @@ typedef struct {
     int32_t precision;        /* PAB_FP64 or PAB_MIXED, for every slot */
     int64_t capacity_bins;    /* arena size in bin-states; 0: 80 % of free device memory / 20 B */
     int32_t block_warps;      /* warps per CTA (0: 8) */
-    int32_t ctas_per_sm;      /* persistent CTAs per SM (0: as many as fit, at most 4) */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM, 0..32 (0: as many as fit, at most 4) */
     int32_t bins_per_grab;    /* bins a warp takes per shared-memory grab (0: 1) */
     int32_t max_bins;         /* largest Nb any slot will use (0: PAB_MAX_BINS); sizes shared memory */
 } pab_batch_config;
@@ -101,7 +101,9 @@ pab_status pab_batch_usage(const pab_batch_t *b, int32_t *active_slots, int64_t 
                            int64_t *capacity_bins);
 
 /* Launch shape used by later steps (the autotuner's knobs); invalidates the
- * captured graph.  block_warps 1..16, ctas_per_sm 1..8, bins_per_grab 1..8. */
+ * captured graph.  block_warps 1..16, ctas_per_sm 1..32, bins_per_grab 1..8; a CTA of
+ * one warp sums its tile's moment terms itself (no shared per-bin terms, so more
+ * CTAs fit on an SM), with the same results as the wider shapes. */
 pab_status pab_batch_set_launch(pab_batch_t *b, int32_t block_warps, int32_t ctas_per_sm,
                                 int32_t bins_per_grab);
 

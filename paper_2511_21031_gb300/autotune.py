@@ -17,7 +17,8 @@ import time
 
 import numpy as np
 
-BATCH_CANDIDATES = tuple((w, c, g) for w in (4, 8, 16) for c in (1, 2, 4, 8) for g in (1, 2))
+BATCH_CANDIDATES = tuple((w, c, g) for w in (4, 8, 16) for c in (1, 2, 4, 8) for g in (1, 2)) + \
+    tuple((1, c, 1) for c in (8, 16, 24, 32))  # one-warp CTAs sum their own terms
 SOLVER_CANDIDATES = (1, 2, 4, 8, 16)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 

@@ -140,7 +140,97 @@ __global__ void __launch_bounds__(kOrderThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent batch kernel.
+// Pieces of the persistent batch kernel.
+// ---------------------------------------------------------------------------
+// Advance bin b of cell c over the slot's flow step, store the state and count.
+template <bool MIXED>
+__device__ __forceinline__ void advance_one(const StepConst &K, const BinConst &bc, const SlotDesc &d,
+                                            int b, long long c, double p_inf, bool p_ok, double &R,
+                                            double &V, GasBase &g, uint32_t &fl_or, uint32_t &n_flag,
+                                            uint32_t &n_att, uint32_t &n64)
+{
+    const size_t k = (size_t)b * (size_t)d.C + (size_t)c;
+    R = d.R[k];
+    V = d.V[k];
+    float hc = d.h[k];
+    int na = 0, nd = 0;
+    g.reset();
+    const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
+    d.R[k] = R;  // unchanged when the input was not finite
+    d.V[k] = V;
+    d.h[k] = hc;
+    fl_or |= fl;
+    n_flag += (fl != 0);
+    n_att += na;
+    n64 += nd;
+}
+
+// Running quadrature sums of one cell, in bin order: w R^3 (compensated in
+// MIXED), and the other three terms (FP32 sums in MIXED, FP64 otherwise).
+struct TermSums {
+    double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
+    float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
+};
+template <bool MIXED>
+__device__ __forceinline__ void add_terms(TermSums &S, double x, const float *tf, const double *td)
+{
+    if (MIXED) {
+        neumaier_add(S.m3, S.m3c, x);
+        S.m2vf = __fadd_rn(S.m2vf, tf[0]);
+        S.m3pf = __fadd_rn(S.m3pf, tf[1]);
+        S.m3v2f = __fadd_rn(S.m3v2f, tf[2]);
+    } else {
+        S.m3 = __dadd_rn(S.m3, x);
+        S.m2v = __dadd_rn(S.m2v, td[0]);
+        S.m3p = __dadd_rn(S.m3p, td[1]);
+        S.m3v2 = __dadd_rn(S.m3v2, td[2]);
+    }
+}
+
+// The 7 moments of cell c from its sums.
+template <bool MIXED>
+__device__ __forceinline__ void write_moments(const StepConst &K, const SlotDesc &d, long long c,
+                                              const TermSums &S)
+{
+    double m3 = S.m3, m2v = S.m2v, m3p = S.m3p, m3v2 = S.m3v2;
+    if (MIXED) {
+        m3 += S.m3c;
+        m2v = f2d(S.m2vf);
+        m3p = fma(K.p0, m3, f2d(S.m3pf));  // p0 sum w R^3 + sum w R^3 (p_bw - p0)
+        m3v2 = f2d(S.m3v2f);
+    }
+    const double nb = d.nb ? d.nb[c] : K.nb_default;
+    const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
+    const double inv_m3 = 1.0 / m3;
+    const long long C = d.C;
+    d.out[0 * C + c] = nb;
+    d.out[1 * C + c] = alpha;
+    d.out[2 * C + c] = m3;
+    d.out[3 * C + c] = m2v;
+    d.out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
+    d.out[5 * C + c] = (MIXED ? m3p : K.rho * m3p) * inv_m3;  // FP64 terms are over rho
+    d.out[6 * C + c] = m3v2 * inv_m3;
+}
+
+// One tile's status counts into the slot's counters.
+__device__ __forceinline__ void flush_slot(SlotCounters *sc, uint32_t f, unsigned long long a,
+                                           unsigned long long t, unsigned long long e)
+{
+    if (f)
+        atomicOr(&sc->flags_or, f);
+    if (a)
+        atomicAdd(&sc->n_flagged, a);
+    if (t) {
+        atomicAdd(&sc->n_attempts, t);
+        atomicAdd(&sc->step_attempts, t);
+    }
+    if (e)
+        atomicAdd(&sc->n_fp64, e);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernel.  A CTA of one warp sums its tile's terms itself and
+// needs only the slot's constants in shared memory; wider CTAs stage the terms.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
 // At most 80 registers: the per-bin terms in shared memory (about 37 KB per CTA
@@ -207,6 +297,40 @@ __global__ void __maxnreg__(80)
         const double p_inf = valid ? d.p_inf[c] : K.p0;
         const bool p_ok = finite64(p_inf);
         uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
+        TermSums S;
+
+        if (nw == 1) {
+            // one warp: the tile's bins in order, each bin's terms summed as they come,
+            // in the order and with the arithmetic of the staged sum below (the same
+            // results for every launch shape), without shared terms or barriers
+            for (int b = 0; b < d.B && valid; ++b) {
+                const BinConst &bc = K.bins[b];
+                double R, V;
+                GasBase g;
+                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, fl_or, n_flag, n_att, n64);
+                if (d.out) {
+                    if (MIXED) {
+                        float tf[3];
+                        const double x = quad_terms_mixed(K, bc, R, V, tf);
+                        add_terms<MIXED>(S, x, tf, nullptr);
+                    } else {
+                        double t[4];
+                        quad_terms64(K, bc, R, V, t, g);
+                        add_terms<MIXED>(S, t[0], nullptr, t + 1);
+                    }
+                }
+            }
+            fl_or = __reduce_or_sync(0xffffffffu, fl_or);
+            n_flag = __reduce_add_sync(0xffffffffu, n_flag);
+            n_att = __reduce_add_sync(0xffffffffu, n_att);
+            n64 = __reduce_add_sync(0xffffffffu, n64);
+            if (d.out && valid)
+                write_moments<MIXED>(K, d, c, S);
+            if (lane == 0)
+                flush_slot(cnt + slot, fl_or, n_flag, n_att, n64);
+            __syncwarp();
+            continue;
+        }
 
         for (;;) {
             int b0 = 0;
@@ -220,21 +344,9 @@ __global__ void __maxnreg__(80)
                 if (!valid)
                     continue;
                 const BinConst &bc = K.bins[b];
-                const size_t k = (size_t)b * (size_t)d.C + (size_t)c;
-                double R = d.R[k];
-                double V = d.V[k];
-                float hc = d.h[k];
-                int na = 0, nd = 0;
+                double R, V;
                 GasBase g;
-                g.reset();
-                const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
-                d.R[k] = R;  // unchanged when the input was not finite
-                d.V[k] = V;
-                d.h[k] = hc;
-                fl_or |= fl;
-                n_flag += (fl != 0);
-                n_att += na;
-                n64 += nd;
+                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, fl_or, n_flag, n_att, n64);
                 if (d.out) {
                     if (MIXED) {
                         float tf[3];
@@ -263,39 +375,21 @@ __global__ void __maxnreg__(80)
         }
         __syncthreads();
         if (warp == 0 && d.out && valid) {
-            double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
-            float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
             for (int b = 0; b < d.B; ++b) {
                 const double x = terms[(size_t)b * kTile + lane];
                 if (MIXED) {
-                    neumaier_add(m3, m3c, x);
-                    m2vf += terms_f[((size_t)0 * max_bins + b) * kTile + lane];
-                    m3pf += terms_f[((size_t)1 * max_bins + b) * kTile + lane];
-                    m3v2f += terms_f[((size_t)2 * max_bins + b) * kTile + lane];
+                    const float tf[3] = {terms_f[((size_t)0 * max_bins + b) * kTile + lane],
+                                         terms_f[((size_t)1 * max_bins + b) * kTile + lane],
+                                         terms_f[((size_t)2 * max_bins + b) * kTile + lane]};
+                    add_terms<MIXED>(S, x, tf, nullptr);
                 } else {
-                    m3 += x;
-                    m2v += terms_d[((size_t)0 * max_bins + b) * kTile + lane];
-                    m3p += terms_d[((size_t)1 * max_bins + b) * kTile + lane];
-                    m3v2 += terms_d[((size_t)2 * max_bins + b) * kTile + lane];
+                    const double td[3] = {terms_d[((size_t)0 * max_bins + b) * kTile + lane],
+                                          terms_d[((size_t)1 * max_bins + b) * kTile + lane],
+                                          terms_d[((size_t)2 * max_bins + b) * kTile + lane]};
+                    add_terms<MIXED>(S, x, nullptr, td);
                 }
             }
-            m3 += m3c;
-            if (MIXED) {
-                m2v = f2d(m2vf);
-                m3p = fma(K.p0, m3, f2d(m3pf));  // p0 sum w R^3 + sum w R^3 (p_bw - p0)
-                m3v2 = f2d(m3v2f);
-            }
-            const double nb = d.nb ? d.nb[c] : K.nb_default;
-            const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
-            const double inv_m3 = 1.0 / m3;
-            const long long C = d.C;
-            d.out[0 * C + c] = nb;
-            d.out[1 * C + c] = alpha;
-            d.out[2 * C + c] = m3;
-            d.out[3 * C + c] = m2v;
-            d.out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
-            d.out[5 * C + c] = (MIXED ? m3p : K.rho * m3p) * inv_m3;  // FP64 terms are over rho
-            d.out[6 * C + c] = m3v2 * inv_m3;
+            write_moments<MIXED>(K, d, c, S);
         }
         if (threadIdx.x == 0) {
             uint32_t f = 0;
@@ -306,17 +400,7 @@ __global__ void __maxnreg__(80)
                 t += s_cnt[2][w];
                 e += s_cnt[3][w];
             }
-            SlotCounters *sc = cnt + slot;
-            if (f)
-                atomicOr(&sc->flags_or, f);
-            if (a)
-                atomicAdd(&sc->n_flagged, a);
-            if (t) {
-                atomicAdd(&sc->n_attempts, t);
-                atomicAdd(&sc->step_attempts, t);
-            }
-            if (e)
-                atomicAdd(&sc->n_fp64, e);
+            flush_slot(cnt + slot, f, a, t, e);
         }
         __syncthreads();
     }
@@ -439,6 +523,13 @@ void arena_give(pab_batch_t *b, long long off, long long n)
     b->used -= n;
 }
 
+// Dynamic shared memory of a launch: the slot's constants, and for CTAs of more
+// than one warp the per-bin terms of a tile too.
+size_t launch_smem(const pab_batch_t *b)
+{
+    return b->block_warps == 1 ? pab::const_bytes() : b->smem_bytes;
+}
+
 int resident_ctas(const pab_batch_t *b)
 {
     int per_sm = 0;
@@ -446,10 +537,10 @@ int resident_ctas(const pab_batch_t *b)
     cudaError_t e;
     if (b->cfg.precision == PAB_MIXED)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pab::batch_kernel<true>, threads,
-                                                          b->smem_bytes);
+                                                          launch_smem(b));
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pab::batch_kernel<false>, threads,
-                                                          b->smem_bytes);
+                                                          launch_smem(b));
     if (e != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int want = b->ctas_per_sm > 0 ? b->ctas_per_sm : 4;
@@ -471,10 +562,10 @@ cudaError_t enqueue_step(pab_batch_t *b, cudaStream_t s, int grid)
     const int threads = b->block_warps * 32;
     const int maxb = b->cfg.max_bins;
     if (b->cfg.precision == PAB_MIXED)
-        pab::batch_kernel<true><<<grid, threads, b->smem_bytes, s>>>(
+        pab::batch_kernel<true><<<grid, threads, launch_smem(b), s>>>(
             b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
     else
-        pab::batch_kernel<false><<<grid, threads, b->smem_bytes, s>>>(
+        pab::batch_kernel<false><<<grid, threads, launch_smem(b), s>>>(
             b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
     return cudaGetLastError();
 }
@@ -511,7 +602,7 @@ pab_status pab_batch_create(const pab_batch_config *cfg, void *stream, pab_batch
     *out = nullptr;
     if (!cfg || cfg->max_slots < 1 || cfg->max_slots > pab::kMaxSlots ||
         (cfg->precision != PAB_FP64 && cfg->precision != PAB_MIXED) || cfg->capacity_bins < 0 ||
-        cfg->block_warps < 0 || cfg->block_warps > 16 || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8 ||
+        cfg->block_warps < 0 || cfg->block_warps > 16 || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
         cfg->bins_per_grab < 0 || cfg->bins_per_grab > 8 || cfg->max_bins < 0 ||
         cfg->max_bins > PAB_MAX_BINS) {
         fprintf(stderr, "pab_batch_create: invalid batch configuration\n");
@@ -872,7 +963,7 @@ pab_status pab_batch_set_launch(pab_batch_t *b, int32_t block_warps, int32_t cta
 {
     if (!b)
         return PAB_EINVAL;
-    if (block_warps < 1 || block_warps > 16 || ctas_per_sm < 1 || ctas_per_sm > 8 ||
+    if (block_warps < 1 || block_warps > 16 || ctas_per_sm < 1 || ctas_per_sm > 32 ||
         bins_per_grab < 1 || bins_per_grab > 8)
         return bfail(b, PAB_EINVAL, "pab_batch_set_launch: out of range");
     b->block_warps = block_warps;

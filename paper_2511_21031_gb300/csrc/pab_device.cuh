@@ -591,36 +591,39 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 }
 
 // Quadrature terms of one bin at (R, Rdot), FP64: w R^3, w R^2 Rdot,
-// w R^3 p_bw / rho (= w R^3 p_b/rho - w R^2 s/rho), w R^3 Rdot^2.
+// w R^3 p_bw / rho (= w R^3 p_b/rho - w R^2 s/rho), w R^3 Rdot^2.  Every product
+// is rounded explicitly, so a sum of the terms comes out the same whether the
+// caller stores them first or adds them as they come.
 __device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
                                              double t[4], GasBase &g)
 {
-    const double wr2 = bc.w * R * R;
-    const double wr3 = wr2 * R;
+    const double wr2 = __dmul_rn(__dmul_rn(bc.w, R), R);
+    const double wr3 = __dmul_rn(wr2, R);
     t[0] = wr3;
-    t[1] = wr2 * V;
-    t[2] = fma(wr3, bubble_pressure_rho64(K, bc, R, g), -wr2 * fma(K.fmu_rho, V, K.tsig_rho));
-    t[3] = wr3 * V * V;
+    t[1] = __dmul_rn(wr2, V);
+    t[2] = fma(wr3, bubble_pressure_rho64(K, bc, R, g), -__dmul_rn(wr2, fma(K.fmu_rho, V, K.tsig_rho)));
+    t[3] = __dmul_rn(__dmul_rn(wr3, V), V);
 }
 
 // The same terms in mixed precision: w R^3 in FP64 (for the compensated alpha
 // sum), and in FP32 w R^2 Rdot, w R^3 (p_bw - p0) (the wall pressure in
-// deviation form; p0 sum w R^3 is added once per cell) and w R^3 Rdot^2.
+// deviation form; p0 sum w R^3 is added once per cell) and w R^3 Rdot^2, with
+// explicit roundings as above.
 __device__ __forceinline__ double quad_terms_mixed(const StepConst &K, const BinConst &bc, double R,
                                                    double V, float tf[3])
 {
-    const double wr2 = bc.w * R * R;
-    const double wr3 = wr2 * R;
+    const double wr3 = __dmul_rn(__dmul_rn(__dmul_rn(bc.w, R), R), R);
     const float xi = d2f(R - bc.R0);
-    const float u = xi * bc.invR0f;
-    const float Rf = bc.R0f + xi, Vf = d2f(V);
+    const float u = __fmul_rn(xi, bc.invR0f);
+    const float Rf = __fadd_rn(bc.R0f, xi), Vf = d2f(V);
     const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
     const float iRf = rcp32(Rf);
-    const float dev = bc.dpeqf + pgdev + (K.two_sigmaf * u - K.four_muf * Vf) * iRf;
-    const float wr3f = d2f(wr3), wr2f = wr3f * iRf;  // w R^2 = w R^3 / R
-    tf[0] = wr2f * Vf;
-    tf[1] = wr3f * dev;
-    tf[2] = wr3f * Vf * Vf;
+    const float st = __fmaf_rn(K.two_sigmaf, u, __fmul_rn(-K.four_muf, Vf));  // 2 sigma u - 4 mu Rdot
+    const float dev = __fadd_rn(__fadd_rn(bc.dpeqf, pgdev), __fmul_rn(st, iRf));
+    const float wr3f = d2f(wr3), wr2f = __fmul_rn(wr3f, iRf);  // w R^2 = w R^3 / R
+    tf[0] = __fmul_rn(wr2f, Vf);
+    tf[1] = __fmul_rn(wr3f, dev);
+    tf[2] = __fmul_rn(__fmul_rn(wr3f, Vf), Vf);
     return wr3;
 }
 

@@ -97,7 +97,7 @@ def test_batch_fp64_matches_oracle():
             assert e <= 1e-6, (k, e)
 
 
-@pytest.mark.parametrize("launch", [(4, 1, 1), (16, 2, 2), (8, 4, 1)])
+@pytest.mark.parametrize("launch", [(4, 1, 1), (16, 2, 2), (8, 4, 1), (1, 16, 1)])
 def test_graph_replay_and_launch_shape_do_not_change_results(launch):
     insts = _instances(n=5, seed=23)
     a = _run_batch(insts, 12, "mixed")
