@@ -91,7 +91,7 @@ def test_invalid_batch_configs_are_refused_without_device_work():
     from paper_2511_21031_gb300 import batch
     lib = batch.load()
     for bad in (dict(max_slots=0), dict(max_slots=5000), dict(precision=3), dict(block_warps=17),
-                dict(ctas_per_sm=9), dict(bins_per_grab=9), dict(max_bins=64), dict(capacity_bins=-1)):
+                dict(ctas_per_sm=33), dict(bins_per_grab=9), dict(max_bins=64), dict(capacity_bins=-1)):
         c = batch.pab_batch_config_default(**bad)
         out = ctypes.c_void_p()
         assert lib.pab_batch_create(ctypes.byref(c), None, ctypes.byref(out)) == pab.PAB_EINVAL
