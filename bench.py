@@ -61,11 +61,12 @@ MIXED_DRAM_BYTES_PER_BINSTEP = 41.7
 MIXED_ISSUE_ACTIVE_NCU = 0.828
 MIXED_FP64_PIPE_ACTIVE_NCU = 0.710
 MIXED_FMA_PIPE_ACTIVE_NCU = 0.390
-# The batch kernel on 16 instances (ncu --set full): DRAM bytes per bin-state and utilisations.
-BATCH_DRAM_BYTES_PER_BINSTEP = 42.5
-BATCH_ISSUE_ACTIVE_NCU = 0.781
-BATCH_FP64_PIPE_ACTIVE_NCU = 0.583
-BATCH_FMA_PIPE_ACTIVE_NCU = 0.376
+# The batch kernel on 16 instances (ncu --set full, one-warp CTAs): DRAM bytes per
+# bin-state and utilisations.
+BATCH_DRAM_BYTES_PER_BINSTEP = 42.8
+BATCH_ISSUE_ACTIVE_NCU = 0.839
+BATCH_FP64_PIPE_ACTIVE_NCU = 0.646
+BATCH_FMA_PIPE_ACTIVE_NCU = 0.421
 HBM_FALLBACK_GBS = 6800.0
 
 
