@@ -233,10 +233,12 @@ __device__ __forceinline__ void flush_slot(SlotCounters *sc, uint32_t f, unsigne
 // needs only the slot's constants in shared memory; wider CTAs stage the terms.
 // ---------------------------------------------------------------------------
 template <bool MIXED>
-// At most 80 registers: the per-bin terms in shared memory (about 37 KB per CTA
-// at Nb = 51) leave room for 6 CTAs of 4 warps per SM, which 80 registers still
-// fit; the unbounded build takes 118 (4 CTAs), 64 would spill.
-__global__ void __maxnreg__(80)
+// At most 72 registers.  One-warp CTAs (the autotuner's choice) are bounded by
+// registers alone: 28 fit on an SM at 72, 24 at 80, 32 at 64 with spills
+// (batched line 15.8e9 against 15.5e9 and 15.5e9 bin-steps/s).  Wider CTAs stage
+// the per-bin terms in shared memory (about 37 KB per CTA at Nb = 51), which
+// leaves room for 6 CTAs of 4 warps per SM at either count.
+__global__ void __maxnreg__(72)
     batch_kernel(const SlotDesc *__restrict__ slots, const int *__restrict__ order,
                  const long long *__restrict__ start, Queue *q, SlotCounters *cnt,
                  int bins_per_grab, int max_bins)
