@@ -73,6 +73,10 @@ enum { PAB_GAS_POLYTROPIC = 0, PAB_GAS_EMPTY = 1, PAB_GAS_TRANSFER = 2 };
 #define PAB_FLAG_NONPOS 8u       /* R <= 0 after the step */
 
 #define PAB_MAX_BINS 63
+/* Largest cell count any entry point accepts (3.4e10 cells, far beyond what HBM holds at
+ * any Nb): every size, index and grid product of a handle stays inside 64-bit and
+ * launch limits. */
+#define PAB_MAX_CELLS (1LL << 35)
 
 /*
  * Configuration of one handle.  pab_config_default fills water (Sec. 5):
@@ -81,7 +85,7 @@ enum { PAB_GAS_POLYTROPIC = 0, PAB_GAS_EMPTY = 1, PAB_GAS_TRANSFER = 2 };
  * v_floor 1e-3 sqrt(p0/rho), max_attempts 100000; alpha0 4e-5; equilibrium start.
  */
 typedef struct {
-    int64_t n_cells;        /* C >= 1 */
+    int64_t n_cells;        /* C: 1..PAB_MAX_CELLS */
     int32_t n_bins;         /* Nb: 1, or odd 3..PAB_MAX_BINS (Simpson needs odd Nb) */
     int32_t gas_mode;       /* PAB_GAS_POLYTROPIC: p_b = pv + p_g0 (R0/R)^(3 gamma),
                                p_g0 = p0 + 2 sigma/R0 - pv; PAB_GAS_EMPTY: p_b = pv;
@@ -228,7 +232,8 @@ pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
  * PAB_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
  * until the process exits.  The block does not grow with the problem, so the
  * only sizes refused (PAB_EINVAL, nothing launched) are those the kernel
- * cannot take: n_bins outside 1..PAB_MAX_BINS (odd), n_cells < 1.  The call
+ * cannot take: n_bins outside 1..PAB_MAX_BINS (odd), n_cells outside
+ * 1..PAB_MAX_CELLS.  The call
  * clears the block, launches the step kernel and copies the block out; it
  * calls no cudaMalloc, cudaFree or allocating library routine.  Every call
  * shares the block, so calls that overlap on the GPU (other streams, other

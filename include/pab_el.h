@@ -36,7 +36,8 @@ typedef struct pab_el_s pab_el_t;
  * gas_mode, tol, v_floor, max_attempts; the bin and cell fields are ignored;
  * adaptive FP64 stepping).  pos_host: [3][N] positions (x row, y row, z row);
  * R0_host: [N] equilibrium radii; the bubbles start at rest at R = R0.
- * Errors: PAB_EINVAL (N < 0, non-positive sizes or radii, non-finite positions),
+ * Errors: PAB_EINVAL (N < 0 or above PAB_MAX_CELLS, non-positive sizes or radii,
+ * nx * ny * nz above PAB_MAX_CELLS, non-finite positions),
  * PAB_ENOMEM, PAB_ECUDA.
  */
 pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const double *pos_host,

@@ -105,8 +105,8 @@ pab_status validate(const pab_config *c, char *msg, size_t n)
         snprintf(msg, n, __VA_ARGS__);  \
         return PAB_EINVAL;              \
     } while (0)
-    if (c->n_cells < 1)
-        BAD("n_cells must be >= 1 (got %lld)", (long long)c->n_cells);
+    if (c->n_cells < 1 || c->n_cells > PAB_MAX_CELLS)
+        BAD("n_cells must be 1..%lld (got %lld)", (long long)PAB_MAX_CELLS, (long long)c->n_cells);
     if (c->n_bins < 1 || c->n_bins > PAB_MAX_BINS || (c->n_bins > 1 && c->n_bins % 2 == 0))
         BAD("n_bins must be 1 or odd in 3..%d (got %d)", PAB_MAX_BINS, c->n_bins);
     if (!finite_pos(c->rho) || !(c->c > 0.0) || !(c->mu >= 0.0) || !(c->sigma >= 0.0) ||

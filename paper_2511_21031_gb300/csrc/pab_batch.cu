@@ -604,6 +604,7 @@ pab_status pab_batch_create(const pab_batch_config *cfg, void *stream, pab_batch
     *out = nullptr;
     if (!cfg || cfg->max_slots < 1 || cfg->max_slots > pab::kMaxSlots ||
         (cfg->precision != PAB_FP64 && cfg->precision != PAB_MIXED) || cfg->capacity_bins < 0 ||
+        cfg->capacity_bins > PAB_MAX_CELLS * PAB_MAX_BINS ||
         cfg->block_warps < 0 || cfg->block_warps > 16 || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 ||
         cfg->bins_per_grab < 0 || cfg->bins_per_grab > 8 || cfg->max_bins < 0 ||
         cfg->max_bins > PAB_MAX_BINS) {

@@ -303,6 +303,7 @@ pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const doub
         return PAB_EINVAL;
     *out = nullptr;
     if (!liquid || n_bubbles < 0 || nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !std::isfinite(dx) ||
+        (double)nx * (double)ny * (double)nz > (double)PAB_MAX_CELLS ||
         (n_bubbles > 0 && (!pos_host || !R0_host))) {
         fprintf(stderr, "pab_el_create: invalid arguments\n");
         return PAB_EINVAL;
@@ -336,11 +337,12 @@ pab_status pab_el_create(const pab_config *liquid, int64_t n_bubbles, const doub
             return PAB_EINVAL;
         }
         bub[(size_t)n] = pab::make_bin(&c, r0, 1.0);
-        const long long i = (long long)std::floor(x / dx), j = (long long)std::floor(y / dx),
-                        k = (long long)std::floor(z / dx);
-        cell[(size_t)n] = (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz)
-                              ? (k * ny + j) * nx + i
-                              : -1;
+        // range-checked in FP64 before the conversion, so a bubble far outside the grid
+        // (or at an infinite x / dx) never meets an out-of-range integer conversion
+        const double fi = std::floor(x / dx), fj = std::floor(y / dx), fk = std::floor(z / dx);
+        const bool in = fi >= 0.0 && fi < (double)nx && fj >= 0.0 && fj < (double)ny && fk >= 0.0 &&
+                        fk < (double)nz;
+        cell[(size_t)n] = in ? ((long long)fk * ny + (long long)fj) * nx + (long long)fi : -1;
     }
     pab_el_t *e = new (std::nothrow) pab_el_t();
     if (!e)

@@ -20,6 +20,7 @@ PAB_ADAPTIVE, PAB_FIXED = 0, 1
 PAB_GAS_POLYTROPIC, PAB_GAS_EMPTY, PAB_GAS_TRANSFER = 0, 1, 2
 FLAG_STEP_LIMIT, FLAG_NONFINITE, FLAG_SUPERSONIC, FLAG_NONPOS = 1, 2, 4, 8
 MAX_BINS = 63
+MAX_CELLS = 1 << 35
 N_MOMENTS = 7
 MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3Rdot2_over_R3")
 

@@ -91,7 +91,8 @@ def test_invalid_batch_configs_are_refused_without_device_work():
     from paper_2511_21031_gb300 import batch
     lib = batch.load()
     for bad in (dict(max_slots=0), dict(max_slots=5000), dict(precision=3), dict(block_warps=17),
-                dict(ctas_per_sm=33), dict(bins_per_grab=9), dict(max_bins=64), dict(capacity_bins=-1)):
+                dict(ctas_per_sm=33), dict(bins_per_grab=9), dict(max_bins=64), dict(capacity_bins=-1),
+                dict(capacity_bins=pab.MAX_CELLS * pab.MAX_BINS + 1)):
         c = batch.pab_batch_config_default(**bad)
         out = ctypes.c_void_p()
         assert lib.pab_batch_create(ctypes.byref(c), None, ctypes.byref(out)) == pab.PAB_EINVAL
@@ -110,11 +111,32 @@ def test_config_defaults_are_water_and_paper_tolerance():
 @pytest.mark.parametrize("bad", [dict(n_bins=20), dict(n_bins=2), dict(n_bins=65), dict(n_cells=0),
                                  dict(rho=-1.0), dict(tol=0.0), dict(stepper=1, n_fixed_sub=0),
                                  dict(precision=7), dict(gas_mode=3), dict(max_attempts=0),
-                                 dict(n_bins=21, s_lognormal=0.0), dict(block_warps=17)])
+                                 dict(n_bins=21, s_lognormal=0.0), dict(block_warps=17),
+                                 dict(n_cells=pab.MAX_CELLS + 1), dict(n_cells=-(1 << 62))])
 def test_invalid_configs_are_refused_without_device_work(bad):
     cfg = pab.pab_config_default(**{"n_cells": 8, **bad})
     out = ctypes.c_void_p()
     st = pab.load().pab_create(ctypes.byref(cfg), None, ctypes.byref(out))
+    assert st == pab.PAB_EINVAL
+    assert out.value is None
+
+
+@pytest.mark.parametrize("n,nx,ny,nz,dx", [(-1, 4, 4, 4, 1e-3), (1, 0, 4, 4, 1e-3), (1, 4, 4, 4, 0.0),
+                                          (1, 4, 4, 4, float("inf")),
+                                          (1, 1 << 12, 1 << 12, (1 << 11) + 1, 1e-3),
+                                          (pab.MAX_CELLS + 1, 4, 4, 4, 1e-3)])
+def test_invalid_el_populations_are_refused_without_device_work(n, nx, ny, nz, dx):
+    """Sizes the EL grid and its cell indices cannot hold (nx ny nz or N above the cell cap)
+    are refused like the others, before any device call and before any position is read."""
+    from paper_2511_21031_gb300 import el
+    lib = el.load()
+    cfg = pab.pab_config_default()
+    out = ctypes.c_void_p()
+    pos = (ctypes.c_double * 3)(1e-4, 1e-4, 1e-4)
+    R0 = (ctypes.c_double * 1)(1e-5)
+    st = lib.pab_el_create(ctypes.byref(cfg), n, ctypes.addressof(pos) if n >= 1 else None,
+                           ctypes.addressof(R0) if n >= 1 else None, nx, ny, nz, dx, None,
+                           ctypes.byref(out))
     assert st == pab.PAB_EINVAL
     assert out.value is None
 
