@@ -170,6 +170,7 @@ pab_status pab_bubble_step_host(pab_t *h, const double *p_inf_host, const double
  * finished.  A call's host buffers must stay valid and unchanged, and its
  * moments_host is not ready, until pab_host_wait returns (or until the second
  * call after it has returned).  Pinned host memory is required for overlap.
+ * On an error return nothing of the failed call is still in flight.
  * Errors: as pab_bubble_step_host.
  */
 pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_host, const double *nb_host,

@@ -926,6 +926,12 @@ extern "C" pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_h
         e = cudaMalloc((void **)&h->pipe_out[k], 7 * C * sizeof(double));
     if (e != cudaSuccess)
         return cuda_fail(h, e, "pab_bubble_step_host_async setup");
+    // after a failure past this point nothing of this call may still touch the caller's
+    // buffers: wait for whatever of it the copy streams already hold
+    auto drain = [h]() {
+        cudaStreamSynchronize(h->pipe_in);
+        cudaStreamSynchronize(h->pipe_outs);
+    };
     e = cudaMemcpyAsync(h->pipe_p[k], p_inf_host, C * sizeof(double), cudaMemcpyHostToDevice, h->pipe_in);
     if (e == cudaSuccess && nb_host)
         e = cudaMemcpyAsync(h->pipe_nb[k], nb_host, C * sizeof(double), cudaMemcpyHostToDevice, h->pipe_in);
@@ -933,12 +939,16 @@ extern "C" pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_h
         e = cudaEventRecord(h->ev_in[k], h->pipe_in);
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(s, h->ev_in[k], 0);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess) {
+        drain();
         return cuda_fail(h, e, "pab_bubble_step_host_async H2D");
+    }
     pab_status st = pab_bubble_step(h, h->pipe_p[k], nb_host ? h->pipe_nb[k] : nullptr, dt,
                                     moments_host ? h->pipe_out[k] : nullptr, stream);
-    if (st != PAB_OK)
+    if (st != PAB_OK) {
+        drain();
         return st;
+    }
     e = cudaEventRecord(h->ev_step[k], s);
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(h->pipe_outs, h->ev_step[k], 0);
@@ -947,8 +957,10 @@ extern "C" pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_h
                             h->pipe_outs);
     if (e == cudaSuccess)
         e = cudaEventRecord(h->ev_out[k], h->pipe_outs);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess) {
+        drain();
         return cuda_fail(h, e, "pab_bubble_step_host_async D2H");
+    }
     h->pipe_busy[k] = true;
     h->pipe_next = 1 - k;
     return PAB_OK;

@@ -8,6 +8,7 @@ the library's kernels; if the library is missing this module raises.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
 from typing import Optional
@@ -312,6 +313,7 @@ class Solver:
                 self._keep.append(arr)
                 kw[key] = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
         self.cfg = pab_config_default(**kw)
+        self._in_flight = collections.deque(maxlen=2)  # host tensors of pipelined calls
         self.n_cells = int(n_cells)
         self.n_bins = int(n_bins)
         self.precision = precision
@@ -366,21 +368,29 @@ class Solver:
 
     def step_host_async(self, p_inf_host, dt: float, moments_host=None, nb_host=None, stream=None):
         """Pipelined end-to-end form: returns at once; moments_host is ready (and the host
-        tensors free) after host_wait() or after the second call after this one."""
+        tensors free) after host_wait() or after the second call after this one.  The solver
+        holds the host tensors of the calls that may still be in flight, so temporaries passed
+        here stay alive until their copies have run."""
         import torch
+        if p_inf_host is None:
+            raise ValueError("p_inf_host is required")
         for t, shape, name in ((p_inf_host, (self.n_cells,), "p_inf_host"), (nb_host, (self.n_cells,), "nb_host"),
                                (moments_host, (N_MOMENTS, self.n_cells), "moments_host")):
             if t is not None and (t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous()
                                   or tuple(t.shape) != shape):
                 raise ValueError(f"{name} must be a contiguous float64 CPU tensor of shape {shape}")
-        _check(self.handle, load().pab_bubble_step_host_async(
+        st = load().pab_bubble_step_host_async(
             self.handle, p_inf_host.data_ptr(), nb_host.data_ptr() if nb_host is not None else None, float(dt),
-            moments_host.data_ptr() if moments_host is not None else None, _stream_handle(stream) or None),
-            "pab_bubble_step_host_async")
+            moments_host.data_ptr() if moments_host is not None else None, _stream_handle(stream) or None)
+        _check(self.handle, st, "pab_bubble_step_host_async")
+        # a call returns only once the call two before it has finished, so the last two
+        # calls' tensors are all that can still be in flight
+        self._in_flight.append((p_inf_host, nb_host, moments_host))
         return moments_host
 
     def host_wait(self):
         _check(self.handle, load().pab_host_wait(self.handle), "pab_host_wait")
+        self._in_flight.clear()
 
     def status(self, stream=None, raise_on_error=False):
         return pab_status_flags(self.handle, _stream_handle(stream), raise_on_error)
@@ -471,8 +481,10 @@ class Solver:
 
     def close(self):
         if getattr(self, "handle", None):
-            pab_destroy(self.handle)
+            pab_destroy(self.handle)  # waits for the pipelined calls' copies
             self.handle = None
+        if hasattr(self, "_in_flight"):
+            self._in_flight.clear()
 
     def __del__(self):
         try:

@@ -152,3 +152,56 @@ def test_null_handle_calls_return_einval():
     lib.pab_destroy(None)
     assert lib.pab_last_error(None) == b"NULL handle"
     assert pab.status_string(pab.PAB_ESTEP_LIMIT) == "PAB_ESTEP_LIMIT"
+
+
+def test_pipelined_host_calls_keep_their_host_tensors_alive(monkeypatch):
+    """Solver.step_host_async returns before its copies run: the tensors of the last two calls
+    (the ones the library may still be copying) stay referenced until host_wait, those of older
+    calls are dropped, and a refused call holds nothing."""
+    import collections
+    import gc
+    import types
+    import weakref
+
+    import torch
+    status = {"rc": pab.PAB_OK}
+
+    class FakeLib:
+        def pab_bubble_step_host_async(self, h, p, nb, dt, m, s):
+            return status["rc"]
+
+        def pab_host_wait(self, h):
+            return pab.PAB_OK
+
+        def pab_last_error(self, h):
+            return b"fake"
+
+        def pab_status_string(self, s):
+            return b"PAB_ECUDA"
+
+    monkeypatch.setattr(pab, "load", lambda *a, **k: FakeLib())
+    sol = object.__new__(pab.Solver)
+    sol.handle, sol.n_cells, sol.n_bins = 1, 4, 1
+    sol._in_flight = collections.deque(maxlen=2)
+    stream = types.SimpleNamespace(cuda_stream=0)
+    refs = []
+    for k in range(3):
+        p = torch.full((4,), float(k), dtype=torch.float64)
+        m = torch.empty((7, 4), dtype=torch.float64)
+        refs.append((weakref.ref(p), weakref.ref(m)))
+        sol.step_host_async(p, 1e-8, moments_host=m, stream=stream)
+        del p, m
+    gc.collect()
+    assert refs[0][0]() is None and refs[0][1]() is None
+    assert all(r() is not None for pair in refs[1:] for r in pair)
+    sol.host_wait()
+    gc.collect()
+    assert all(r() is None for pair in refs for r in pair)
+    status["rc"] = pab.PAB_ECUDA
+    p = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(pab.PabError):
+        sol.step_host_async(p, 1e-8, stream=stream)
+    assert len(sol._in_flight) == 0
+    with pytest.raises(ValueError):
+        sol.step_host_async(None, 1e-8, stream=stream)
+    sol.handle = None
