@@ -72,7 +72,13 @@ pab_status pab_batch_admit(pab_batch_t *b, const pab_config *cfg, void *stream, 
 /* Attach the slot's per-step inputs and outputs: p_inf_dev [C] (required),
  * nb_dev [C] or NULL (default n_b), moments_dev [7][C] or NULL, and dt > 0.
  * The pointers are read by every later step until re-bound, so the caller
- * refreshes the pressure in place between steps. */
+ * refreshes the pressure in place between steps.  A step reads the slot table
+ * when it runs, so bind (like admit and release) first waits, on the host,
+ * until the batch's last enqueued step has finished: binding between steps is
+ * safe on any stream, and costs that wait.  Steps enqueued into the caller's
+ * own stream capture are not waited for.
+ * Errors: PAB_EINVAL (slot not admitted, NULL p_inf_dev, dt <= 0 or non-finite),
+ * PAB_ECUDA. */
 pab_status pab_batch_bind(pab_batch_t *b, int32_t slot, const double *p_inf_dev, const double *nb_dev,
                           double *moments_dev, double dt);
 

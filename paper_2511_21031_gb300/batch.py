@@ -95,6 +95,7 @@ class Batch:
             raise PabError(st, "pab_batch_create (details on stderr)")
         self.handle = out.value
         self.slots = {}  # slot -> (n_cells, n_bins)
+        self._bound = {}  # slot -> the tensors whose pointers the library holds for its steps
 
     def _check(self, st, what):
         if st != pab.PAB_OK:
@@ -117,25 +118,30 @@ class Batch:
                 return None
             raise
 
+    def _ptr(self, t, shape, dtype, name):
+        if t is None:
+            return None
+        if t.device != self.device or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != shape:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor {shape} on {self.device}")
+        return t.data_ptr()
+
     def bind(self, slot: int, p_inf, dt: float, moments=None, nb=None):
+        """Bind the slot's inputs and outputs for the following steps.  The library keeps the
+        pointers, so the batch holds the tensors until the slot is bound again or released."""
         import torch
         C, _ = self.slots[slot]
-
-        def ptr(t, shape, name):
-            if t is None:
-                return None
-            if t.device != self.device or t.dtype != torch.float64 or not t.is_contiguous() \
-                    or tuple(t.shape) != shape:
-                raise ValueError(f"{name} must be a contiguous float64 tensor {shape} on {self.device}")
-            return t.data_ptr()
-        self._check(load().pab_batch_bind(self.handle, int(slot), ptr(p_inf, (C,), "p_inf"),
-                                          ptr(nb, (C,), "nb"), ptr(moments, (pab.N_MOMENTS, C), "moments"),
+        f64 = torch.float64
+        self._check(load().pab_batch_bind(self.handle, int(slot), self._ptr(p_inf, (C,), f64, "p_inf"),
+                                          self._ptr(nb, (C,), f64, "nb"),
+                                          self._ptr(moments, (pab.N_MOMENTS, C), f64, "moments"),
                                           float(dt)), "pab_batch_bind")
+        self._bound[slot] = (p_inf, nb, moments)
 
     def release(self, slot: int, stream=None):
         self._check(load().pab_batch_release(self.handle, int(slot), _stream(stream) or None),
                     "pab_batch_release")
         self.slots.pop(slot, None)
+        self._bound.pop(slot, None)
 
     def step(self, graph: bool = False, stream=None):
         fn = load().pab_batch_step_graph if graph else load().pab_batch_step
@@ -161,8 +167,13 @@ class Batch:
         return R, V, h
 
     def set_state(self, slot: int, R, V, h=None, stream=None):
-        self._check(load().pab_batch_set_state(self.handle, int(slot), R.data_ptr(), V.data_ptr(),
-                                               h.data_ptr() if h is not None else None,
+        import torch
+        C, B = self.slots[slot]
+        if R is None or V is None:
+            raise ValueError("R and Rdot are required")
+        self._check(load().pab_batch_set_state(self.handle, int(slot), self._ptr(R, (B, C), torch.float64, "R"),
+                                               self._ptr(V, (B, C), torch.float64, "Rdot"),
+                                               self._ptr(h, (B, C), torch.float32, "h"),
                                                _stream(stream) or None), "pab_batch_set_state")
 
     def usage(self):
@@ -181,6 +192,8 @@ class Batch:
         if getattr(self, "handle", None):
             load().pab_batch_destroy(self.handle)
             self.handle = None
+        if hasattr(self, "_bound"):
+            self._bound.clear()
 
     def __del__(self):
         try:

@@ -458,6 +458,11 @@ struct pab_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t capture_stream = nullptr;  // the legacy default stream cannot be captured
+    // A step copies the slot table from desc_host when it runs, not when it is enqueued, so
+    // the table may be rewritten only after the last enqueued step has finished: each step
+    // records ev_step, and whatever rewrites the table waits for it first.
+    cudaEvent_t ev_step = nullptr;
+    bool step_pending = false;
     char err[512] = {0};
 };
 
@@ -577,6 +582,31 @@ bool valid_slot(const pab_batch_t *b, int slot)
     return slot >= 0 && slot < b->cfg.max_slots && b->admitted[slot];
 }
 
+// Wait until the last enqueued step has finished (it reads the slot tables when it runs).
+cudaError_t wait_last_step(pab_batch_t *b)
+{
+    if (!b->step_pending)
+        return cudaSuccess;
+    const cudaError_t e = cudaEventSynchronize(b->ev_step);
+    if (e == cudaSuccess)
+        b->step_pending = false;
+    return e;
+}
+
+// Mark a step enqueued on s.  A step enqueued into the caller's own stream capture is not
+// marked: it runs when the caller launches that graph, which the caller orders.
+cudaError_t mark_step(pab_batch_t *b, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return e;
+    e = cudaEventRecord(b->ev_step, s);
+    if (e == cudaSuccess)
+        b->step_pending = true;
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -659,6 +689,8 @@ pab_status pab_batch_create(const pab_batch_config *cfg, void *stream, pab_batch
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&b->ev_step, cudaEventDisableTiming);
+    if (e == cudaSuccess)
         e = cudaMallocHost((void **)&b->K_host, sizeof(pab::StepConst) * ms);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&b->desc_host, sizeof(pab::SlotDesc) * ms);
@@ -710,6 +742,8 @@ void pab_batch_destroy(pab_batch_t *b)
             cudaFreeHost(p);
     if (b->capture_stream)
         cudaStreamDestroy(b->capture_stream);
+    if (b->ev_step)
+        cudaEventDestroy(b->ev_step);
     delete b;
 }
 
@@ -742,7 +776,9 @@ pab_status pab_batch_admit(pab_batch_t *b, const pab_config *cfg, void *stream, 
         return bfail(b, PAB_ENOMEM, "pab_batch_admit: %lld bin-states do not fit (%lld of %lld in use)",
                      n, b->used, (long long)b->cfg.capacity_bins);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaStreamSynchronize(s);  // no step in flight reads the slot tables
+    cudaError_t e = wait_last_step(b);  // no step in flight reads the slot tables
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
     pab::StepConst &K = b->K_host[s_idx];
     pab::make_const(cfg, R0, w, &K);
     std::vector<double> tab;  // host values of a new gas table, alive until the sync below
@@ -808,6 +844,9 @@ pab_status pab_batch_bind(pab_batch_t *b, int32_t slot, const double *p_inf_dev,
         return bfail(b, PAB_EINVAL, "pab_batch_bind: p_inf_dev is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt))
         return bfail(b, PAB_EINVAL, "pab_batch_bind: dt must be positive and finite");
+    const cudaError_t e = wait_last_step(b);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "pab_batch_bind");
     pab::SlotDesc &d = b->desc_host[slot];
     d.p_inf = p_inf_dev;
     d.nb = nb_dev;
@@ -824,7 +863,9 @@ pab_status pab_batch_release(pab_batch_t *b, int32_t slot, void *stream)
         return PAB_EINVAL;
     if (!valid_slot(b, slot))
         return bfail(b, PAB_EINVAL, "pab_batch_release: slot %d is not admitted", slot);
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaError_t e = wait_last_step(b);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess)
         return bcuda(b, e, "pab_batch_release");
     std::memset(&b->desc_host[slot], 0, sizeof(pab::SlotDesc));
@@ -839,6 +880,8 @@ pab_status pab_batch_step(pab_batch_t *b, void *stream)
     if (!b)
         return PAB_EINVAL;
     cudaError_t e = enqueue_step(b, (cudaStream_t)stream, resident_ctas(b));
+    if (e == cudaSuccess)
+        e = mark_step(b, (cudaStream_t)stream);
     return e == cudaSuccess ? PAB_OK : bcuda(b, e, "pab_batch_step");
 }
 
@@ -868,6 +911,8 @@ pab_status pab_batch_step_graph(pab_batch_t *b, void *stream)
         }
     }
     e = cudaGraphLaunch(b->graph_exec, s);
+    if (e == cudaSuccess)
+        e = mark_step(b, s);
     return e == cudaSuccess ? PAB_OK : bcuda(b, e, "pab_batch_step_graph launch");
 }
 

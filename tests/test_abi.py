@@ -205,3 +205,59 @@ def test_pipelined_host_calls_keep_their_host_tensors_alive(monkeypatch):
     with pytest.raises(ValueError):
         sol.step_host_async(None, 1e-8, stream=stream)
     sol.handle = None
+
+
+def test_batch_binding_holds_bound_tensors_and_checks_state_shapes(monkeypatch):
+    """The library keeps a bound slot's pointers for every later step, so the Batch holds the
+    tensors until the slot is re-bound or released; set_state refuses tensors of the wrong
+    shape or type before the library sees them."""
+    import gc
+    import types
+    import weakref
+
+    import torch
+    from paper_2511_21031_gb300 import batch
+
+    class FakeLib:
+        def pab_batch_bind(self, h, slot, p, nb, m, dt):
+            return pab.PAB_OK
+
+        def pab_batch_release(self, h, slot, s):
+            return pab.PAB_OK
+
+        def pab_batch_set_state(self, h, slot, R, V, hh, s):
+            return pab.PAB_OK
+
+    monkeypatch.setattr(batch, "load", lambda *a, **k: FakeLib())
+    b = object.__new__(batch.Batch)
+    b.handle, b.device = 1, torch.device("cpu")
+    b.slots, b._bound = {0: (4, 3)}, {}
+    stream = types.SimpleNamespace(cuda_stream=0)
+    p = torch.zeros(4, dtype=torch.float64)
+    m = torch.empty((7, 4), dtype=torch.float64)
+    rp, rm = weakref.ref(p), weakref.ref(m)
+    b.bind(0, p, 1e-8, moments=m)
+    del p, m
+    gc.collect()
+    assert rp() is not None and rm() is not None
+    b.bind(0, torch.ones(4, dtype=torch.float64), 1e-8)
+    gc.collect()
+    assert rp() is None and rm() is None
+    q = b._bound[0][0]
+    rq = weakref.ref(q)
+    del q
+    b.release(0, stream=stream)
+    gc.collect()
+    assert rq() is None and 0 not in b.slots
+    b.slots[1] = (4, 3)
+    R = torch.zeros((3, 4), dtype=torch.float64)
+    b.set_state(1, R, R.clone(), torch.zeros((3, 4), dtype=torch.float32), stream=stream)
+    for bad in (dict(R=torch.zeros((4, 3), dtype=torch.float64)), dict(R=torch.zeros((3, 4), dtype=torch.float32)),
+                dict(h=torch.zeros((3, 4), dtype=torch.float64)), dict(R=None)):
+        kw = dict(R=R, V=R.clone(), h=None)
+        kw.update(bad)
+        with pytest.raises(ValueError):
+            b.set_state(1, kw["R"], kw["V"], kw["h"], stream=stream)
+    with pytest.raises(ValueError):
+        b.bind(1, torch.zeros(5, dtype=torch.float64), 1e-8)
+    b.handle = None

@@ -109,6 +109,39 @@ def test_graph_replay_and_launch_shape_do_not_change_results(launch):
         np.testing.assert_array_equal(x["moments"], y["moments"])
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_rebinding_between_queued_steps_uses_each_steps_own_inputs(graph):
+    """A step reads the slot table when it runs, not when it is enqueued: binding fresh
+    pressure tensors before each step while the earlier steps are still queued (behind a busy
+    GPU) gives the same bits as refreshing one bound tensor in place."""
+    import torch
+    insts = _instances(n=4, seed=24)
+    n_steps = 8
+    ref = _run_batch(insts, n_steps, "mixed", graph=graph)
+    b = Batch(max_slots=len(insts) + 2, precision="mixed",
+              capacity_bins=sum(w.n_cells * w.n_bins for w in insts) + 1000, max_bins=51)
+    slots = [b.admit(w.n_cells, w.n_bins, **_cfg(w)) for w in insts]
+    moms = [torch.empty((7, w.n_cells), dtype=torch.float64, device="cuda") for w in insts]
+    ps = [[torch.as_tensor(w.pressure_step(n), device="cuda") for w in insts] for n in range(n_steps)]
+    torch.cuda.synchronize()
+    sleep = getattr(torch.cuda, "_sleep", None)
+    if sleep is not None:
+        sleep(50_000_000)  # a bounded spin of about 25 ms, so that the steps below queue up
+    for n in range(n_steps):
+        for s, w, p, m in zip(slots, insts, ps[n], moms):
+            b.bind(s, p, w.dt, moments=m)
+        b.step(graph=graph)
+    torch.cuda.synchronize()
+    for s, m, r in zip(slots, moms, ref):
+        R, V, h = b.get_state(s)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(R.cpu().numpy(), r["R"])
+        np.testing.assert_array_equal(V.cpu().numpy(), r["V"])
+        np.testing.assert_array_equal(h.cpu().numpy(), r["h"])
+        np.testing.assert_array_equal(m.cpu().numpy(), r["moments"])
+    b.close()
+
+
 def test_admission_by_arena_memory_release_and_reuse():
     import torch
     b = Batch(max_slots=3, precision="mixed", capacity_bins=10 * 21 + 5 * 11, max_bins=21)
