@@ -1,6 +1,7 @@
 """Batched persistent kernel: every slot advances exactly as the single-instance
-step advances it alone, graph replay equals plain launches, admission by
-arena memory, release and reuse, and parity with the FP64 oracle."""
+step advances it alone, graph replay equals plain launches, rebinding between
+queued steps reaches only the later steps, admission by arena memory, release
+and reuse, and parity with the FP64 oracle."""
 import numpy as np
 import pytest
 
