@@ -1,0 +1,52 @@
+"""Host logic of the launch-shape autotuner on the CPU: the cache key names the GPU, the
+precision, the Nb mix and the size class of the work; the cache file is replaced atomically
+and survives a damaged file; a cached choice is returned without timing anything."""
+import json
+
+from paper_2511_21031_gb300 import autotune, workloads
+
+
+def _insts():
+    return workloads.batched_instances(n=5, seed=3, edge_lo=5, edge_hi=12, n_steps=4)
+
+
+def test_cache_key_names_gpu_precision_nb_mix_and_size_class(monkeypatch):
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "GPU-X")
+    insts = _insts()
+    k = autotune.batch_key(insts, "mixed")
+    nbs = sorted({w.n_bins for w in insts})
+    cells = sum(w.n_cells for w in insts)
+    assert k == f"GPU-X|batch|mixed|nb{nbs}|cells~1e{len(str(cells)) - 1}"
+    assert autotune.batch_key(insts, "fp64") != k
+    assert autotune.batch_key(insts[:1], "mixed") != k or len(nbs) == 1
+
+
+def test_cache_round_trip_and_damaged_file(tmp_path):
+    path = str(tmp_path / "cache.json")
+    assert autotune._load(path) == {}
+    autotune._save(path, {"a": {"block_warps": 1}})
+    assert autotune._load(path) == {"a": {"block_warps": 1}}
+    assert [p.name for p in tmp_path.iterdir()] == ["cache.json"]   # no temporary left behind
+    open(path, "w").write("{not json")
+    assert autotune._load(path) == {}
+
+
+def test_cached_choice_is_returned_without_timing(monkeypatch, tmp_path):
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "GPU-X")
+    insts = _insts()
+    path = str(tmp_path / "cache.json")
+    choice = dict(block_warps=1, ctas_per_sm=32, bins_per_grab=1, ms=1.0)
+    json.dump({autotune.batch_key(insts, "mixed"): choice}, open(path, "w"))
+
+    def no_timing(*a, **k):
+        raise AssertionError("a cached choice must not be re-timed")
+    monkeypatch.setattr(autotune, "_time_events", no_timing)
+    got = autotune.tune_batch(insts, precision="mixed", cache_path=path)
+    assert got == dict(choice, cached=True)
+
+
+def test_candidate_sets_are_within_the_library_ranges():
+    for w, c, g in autotune.BATCH_CANDIDATES:
+        assert 1 <= w <= 16 and 1 <= c <= 32 and 1 <= g <= 8
+    assert len(set(autotune.BATCH_CANDIDATES)) == len(autotune.BATCH_CANDIDATES) == 28
+    assert all(1 <= w <= 16 for w in autotune.SOLVER_CANDIDATES)
