@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the ensemble-averaged bubble-dynamics source update.
 
-TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package; the product path
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()``, and the
+CPU-baseline leg and the ``--impl reference`` arm of ``bench.py`` may import this package; the product path
 (``paper_2511_21031_gb300``) never does, and this package never imports it.
 
 This module only marshals numpy arrays into the plain C oracle

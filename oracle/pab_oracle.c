@@ -3,8 +3,8 @@
  * source update of "Hardware-Accelerated Phase-Averaging for Cavitating Bubbly
  * Flows" (arXiv 2511.21031).
  *
- * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
- * leg of the benchmark may load this library.  The product path (the CUDA
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check, and the CPU-baseline
+ * leg and the reference arm of the benchmark may load this library.  The product path (the CUDA
  * library) shares no code, header, table or helper with it.
  *
  * Every function follows the paper's statement of the method in the paper's
