@@ -205,7 +205,18 @@ pab_status pab_get_attempts(pab_t *h, int32_t *attempts_dev, void *stream);
 /* Copy the bin table (host arrays of n_bins) and the default n_b. */
 pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double *nb_default);
 
-/* Launch shape: warps per CTA (1..32; each warp covers 32 cells and strides
+/*
+ * The bin table and default n_b that pab_create builds for cfg (Sec. 2.2:
+ * lognormal R0 in Nb bins with Simpson weights, or the explicit table; n_b =
+ * alpha0 / (4/3 pi sum_i w_i R0_i^3), Eq. e:ndf at equilibrium), computed on
+ * the host with no handle and no device.  R0_host and w_host receive n_bins
+ * values each; nb_default may be NULL.  The values are those pab_get_bins
+ * returns for a handle of the same cfg.
+ * Errors: PAB_EINVAL (NULL cfg or outputs, cfg refused as pab_create refuses it).
+ */
+pab_status pab_bin_table(const pab_config *cfg, double *R0_host, double *w_host, double *nb_default);
+
+/* Launch shape: warps per CTA (1..16; each warp covers 32 cells and strides
  * over the bins).  Used by the autotuner. */
 pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
 

@@ -651,6 +651,32 @@ pab_status pab_get_attempts(pab_t *h, int32_t *attempts_dev, void *stream)
     return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_get_attempts");
 }
 
+pab_status pab_bin_table(const pab_config *cfg, double *R0_host, double *w_host, double *nb_default)
+{
+    if (!cfg || !R0_host || !w_host)
+        return PAB_EINVAL;
+    char msg[256];
+    if (validate(cfg, msg, sizeof(msg)) != PAB_OK) {
+        fprintf(stderr, "pab_bin_table: %s\n", msg);
+        return PAB_EINVAL;
+    }
+    double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
+    if (!pab::bin_table(cfg, R0, w)) {
+        fprintf(stderr, "pab_bin_table: invalid bin table request\n");
+        return PAB_EINVAL;
+    }
+    // the constants a handle of this cfg would hold, so the values are the handle's own
+    pab::StepConst K;
+    build_const(cfg, R0, w, &K);
+    for (int i = 0; i < K.B; ++i) {
+        R0_host[i] = K.bins[i].R0;
+        w_host[i] = K.bins[i].w;
+    }
+    if (nb_default)
+        *nb_default = K.nb_default;
+    return PAB_OK;
+}
+
 pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double *nb_default)
 {
     if (!h)

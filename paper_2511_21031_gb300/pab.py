@@ -27,7 +27,7 @@ MOMENT_NAMES = ("n_b", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3R
 
 EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_bubble_step_host", "pab_bubble_step_host_async", "pab_host_wait", "pab_status_flags", "pab_get_state", "pab_set_state",
-           "pab_get_attempts", "pab_get_bins", "pab_set_block_warps", "pab_destroy",
+           "pab_get_attempts", "pab_get_bins", "pab_bin_table", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
            "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check",
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_set_state": (i32, [vp, vp, vp, vp, vp]),
         "pab_get_attempts": (i32, [vp, vp, vp]),
         "pab_get_bins": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pab_bin_table": (i32, [ctypes.POINTER(pab_config), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                ctypes.POINTER(dbl)]),
         "pab_set_block_warps": (i32, [vp, i32]),
         "pab_destroy": (None, [vp]),
         "pab_last_error": (ctypes.c_char_p, [vp]),
@@ -188,6 +190,18 @@ def pab_set_state(h, R_ptr, Rdot_ptr, h_ptr, stream=0):
 
 def pab_get_attempts(h, att_ptr, stream=0):
     _check(h, load().pab_get_attempts(h, att_ptr or None, stream or None), "pab_get_attempts")
+
+
+def pab_bin_table(**cfg):
+    """(R0, w, n_b default) that pab_create builds for the config (host only, no device)."""
+    c = pab_config_default(**cfg)
+    R0 = (ctypes.c_double * c.n_bins)()
+    w = (ctypes.c_double * c.n_bins)()
+    nb = ctypes.c_double()
+    st = load().pab_bin_table(ctypes.byref(c), R0, w, ctypes.byref(nb))
+    if st != PAB_OK:
+        raise PabError(st, "pab_bin_table rejected the configuration (details on stderr)")
+    return list(R0), list(w), nb.value
 
 
 def pab_get_bins(h, n_bins: int):
