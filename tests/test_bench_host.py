@@ -54,6 +54,7 @@ def test_mixed_roofline_object(batched):
     assert d["hbm_frac"] == pytest.approx(d["achieved_hbm_gbs"] / d["hbm_peak_gbs"])
     assert 0.0 < d["issue_active_ncu"] <= 1.0 and 0.0 < d["fp64_pipe_active_ncu"] <= 1.0
     assert os.path.exists(os.path.join(ROOT, d["counters"]))
+    assert isinstance(d["counters_build"], str) and d["counters_build"]
 
 
 def test_hbm_peak_falls_back_when_no_measurement_is_there(monkeypatch):
