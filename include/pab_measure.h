@@ -1,9 +1,10 @@
 /*
  * pab_measure.h - measurement aid shipped with libpab.
  *
- * The paper has no counterpart of this entry point: it only serves the
- * roofline of the bubble kernels by measuring how fast this GPU retires
- * fused multiply-adds in FP64 and in FP32.
+ * The paper has no counterpart of these entry points: they serve the
+ * roofline of the bubble kernels (how fast this GPU retires fused
+ * multiply-adds in FP64 and in FP32) and the tests of the kernels' helper
+ * arithmetic and of the host-built gas-term table.
  */
 #ifndef PAB_MEASURE_H
 #define PAB_MEASURE_H
@@ -87,6 +88,23 @@ pab_status pab_math_check(int64_t n, const double *R_dev, const double *Rb_dev, 
 pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, const double *y_dev,
                           double *f2d_dev, double *f2d_hw, double *rcp_dev, double *div_dev,
                           double *seed_dev, uint16_t *cmp_dev, void *stream);
+
+/*
+ * The gas-term node table a handle builds for the polytropic exponent gamma,
+ * on the host (no handle, no device).  The gas factor (R0/R)^(3 gamma) is
+ * x^(-3 gamma) with x = R/R0; the table holds nodes x_j = q^j, j = -J..J
+ * (covering 1/25..25), each as *stride doubles {x_j, c_0, .., c_d, 0 ..}
+ * with c_k the coefficients of the binomial series of (x_j + delta)^(-3 gamma)
+ * in delta, so that x^(-3 gamma) = sum_k c_k (x - x_j)^k for x near x_j.
+ * *dmax receives the bound on |x/x_j - 1| within which the first omitted term
+ * stays below half an ulp; the nodes are spaced so that the nearest one (in
+ * log x) is always within it.  *n_nodes = 2 J + 1.  When tab_host is not NULL
+ * it receives the table if capacity (doubles) holds it.
+ * Errors: PAB_EINVAL (gamma not positive and finite, NULL counts, capacity
+ * too small).
+ */
+pab_status pab_gas_table(double gamma, double *tab_host, int64_t capacity, int32_t *n_nodes,
+                         int32_t *stride, double *dmax);
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,7 @@
 #include "pab.h"
 #include "pab_transfer.h"
 #include "pab_closure.h"
+#include "pab_measure.h"
 #include "pab_internal.h"
 
 struct pab_s {
@@ -674,6 +675,35 @@ pab_status pab_bin_table(const pab_config *cfg, double *R0_host, double *w_host,
     }
     if (nb_default)
         *nb_default = K.nb_default;
+    return PAB_OK;
+}
+
+pab_status pab_gas_table(double gamma, double *tab_host, int64_t capacity, int32_t *n_nodes,
+                         int32_t *stride, double *dmax)
+{
+    if (!finite_pos(gamma) || !n_nodes || !stride || !dmax || capacity < 0)
+        return PAB_EINVAL;
+    // the bound a handle of this gamma derives, from the same constants builder
+    pab_config cfg;
+    pab_config_default(&cfg);
+    cfg.gamma = gamma;
+    double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
+    if (!pab::bin_table(&cfg, R0, w))
+        return PAB_EINVAL;
+    pab::StepConst K;
+    build_const(&cfg, R0, w, &K);
+    std::vector<double> tab;
+    int J = 0;
+    double il2q = 0.0;
+    pab::gas_table(3.0 * gamma, K.gas_dmax_tab, &tab, &J, &il2q);
+    *n_nodes = 2 * J + 1;
+    *stride = pab::kGasTabStride;
+    *dmax = K.gas_dmax_tab;
+    if (tab_host) {
+        if ((size_t)capacity < tab.size())
+            return PAB_EINVAL;
+        std::memcpy(tab_host, tab.data(), tab.size() * sizeof(double));
+    }
     return PAB_OK;
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_get_attempts", "pab_get_bins", "pab_bin_table", "pab_set_block_warps", "pab_destroy",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
-           "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check",
+           "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check", "pab_gas_table",
            "pab_get_contents", "pab_set_contents")
 NOALLOC_SCRATCH_BYTES = 256
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_get_attempts": (i32, [vp, vp, vp]),
         "pab_get_bins": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "pab_bin_table": (i32, [ctypes.POINTER(pab_config), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                ctypes.POINTER(dbl)]),
+        "pab_gas_table": (i32, [dbl, vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(dbl)]),
         "pab_set_block_warps": (i32, [vp, i32]),
         "pab_destroy": (None, [vp]),
@@ -202,6 +204,22 @@ def pab_bin_table(**cfg):
     if st != PAB_OK:
         raise PabError(st, "pab_bin_table rejected the configuration (details on stderr)")
     return list(R0), list(w), nb.value
+
+
+def pab_gas_table(gamma: float):
+    """(nodes [2J+1][stride] float64 array, dmax) of the host-built gas-term table (no device)."""
+    import numpy as np
+    lib = load()
+    n, stride, dmax = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    st = lib.pab_gas_table(float(gamma), None, 0, ctypes.byref(n), ctypes.byref(stride), ctypes.byref(dmax))
+    if st != PAB_OK:
+        raise PabError(st, "pab_gas_table")
+    tab = np.empty((n.value, stride.value), dtype=np.float64)
+    st = lib.pab_gas_table(float(gamma), tab.ctypes.data, tab.size, ctypes.byref(n), ctypes.byref(stride),
+                           ctypes.byref(dmax))
+    if st != PAB_OK:
+        raise PabError(st, "pab_gas_table")
+    return tab, dmax.value
 
 
 def pab_get_bins(h, n_bins: int):
