@@ -261,3 +261,23 @@ def test_batch_binding_holds_bound_tensors_and_checks_state_shapes(monkeypatch):
     with pytest.raises(ValueError):
         b.bind(1, torch.zeros(5, dtype=torch.float64), 1e-8)
     b.handle = None
+
+
+def test_product_path_fails_loudly_without_its_library_or_a_device(monkeypatch, tmp_path):
+    """No CPU fallback: a missing library is an error, not a silent substitute, and the solver,
+    batch and bubble-cloud classes refuse to run without a CUDA device."""
+    import torch
+    from paper_2511_21031_gb300 import _build, batch, el
+    monkeypatch.setattr(pab, "_LIB", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libpab.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        pab.load(build_if_missing=False)
+    monkeypatch.undo()
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pab.Solver(8)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        batch.Batch(max_slots=2, capacity_bins=100)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        el.BubbleCloud([[0.0], [0.0], [0.0]], [1e-5], 4, 4, 4, 1e-4)
