@@ -116,21 +116,37 @@ def make_workload(name, rank, edge=0):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    nvidia-smi numbers the GPUs in its own (PCI) order and ignores CUDA_VISIBLE_DEVICES, so a
+    torch device index may name another GPU there: every GPU is sampled with its index and
+    UUID, and the samples of the one whose UUID is the torch device's are kept (those with the
+    torch index when the UUID is not known)."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None):
         self.index = index
+        self.uuid = uuid
         self.proc = None
         self.lines = []
+
+    @staticmethod
+    def device_uuid(index):
+        """The torch device's UUID, or None where this torch does not report it."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(index).uuid).strip()
+            return u or None
+        except Exception:
+            return None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -151,24 +167,39 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
+        return self.summarise(self.lines, self.index, self.uuid)
+
+    @staticmethod
+    def summarise(lines, index, uuid=None):
+        """Median SM clock, maximum clock and the throttle reasons seen active in the samples
+        of the GPU with this UUID (else this nvidia-smi index)."""
+        def norm(u):
+            u = u.strip().lower()
+            return u[4:] if u.startswith("gpu-") else u
+        rows = [[p.strip() for p in ln.split(",")] for ln in lines]
+        rows = [r for r in rows if len(r) >= 10]
+        mine = [r for r in rows if uuid and norm(r[1]) == norm(uuid)]
+        matched = "uuid"
+        if not mine:
+            mine = [r for r in rows if r[0] == str(index)]
+            matched = "index"
         sm, mx, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
+        for r in mine:
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                clk, top = float(r[2]), float(r[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[4:8]):
+            sm.append(clk)
+            mx = top
+            for n, v in zip(names, r[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu": mine[0][1] if matched == "uuid" else f"index {index}",
+                "matched_by": matched}
 
 
 def cpu_baseline(wl, seconds=12.0, sample_cells=16384):
@@ -526,7 +557,9 @@ def run_ours(args):
         ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(total)]
         solver.moments()  # one reduce-only launch (profiled for its per-bin cost)
     torch.cuda.synchronize()
-    res = _time_steps(solver, wl, ps, args, stream, clocks=ClockSampler(torch.cuda.current_device()),
+    dev_index = torch.cuda.current_device()
+    res = _time_steps(solver, wl, ps, args, stream,
+                      clocks=ClockSampler(dev_index, ClockSampler.device_uuid(dev_index)),
                       keep_start=True)
     if "trace" in res:
         if rank == 0:

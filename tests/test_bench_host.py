@@ -69,3 +69,32 @@ def test_hbm_peak_falls_back_when_no_measurement_is_there(monkeypatch):
     monkeypatch.setattr(builtins, "open", no_peaks)
     peak, src = bench._hbm_peak()
     assert peak == bench.HBM_FALLBACK_GBS and "fallback" in src
+
+
+def test_clock_summary_of_nvidia_smi_samples():
+    """The samples of the bench's own GPU (by UUID, else by index) give the median SM clock, the
+    maximum and every throttle reason seen active ("Not Active" is not); other GPUs' samples and
+    malformed lines are ignored, and no samples give None."""
+    bench = _bench()
+    na, a = "Not Active", "Active"
+    U0, U3 = "GPU-aaaa0000-0000-0000-0000-000000000000", "GPU-bbbb3333-3333-3333-3333-333333333333"
+    lines = [
+        f"0, {U0}, 2070, 2070, 900.1, 0x0000000000000000, {na}, {na}, {na}, {na}",
+        f"3, {U3}, 1500, 2070, 1390.5, 0x0000000000000008, {a}, {na}, {na}, {na}",
+        f"0, {U0}, 1980, 2070, 1390.5, 0x0000000000000004, {na}, {na}, {na}, {a}",
+        "garbage",
+        f"0, {U0}, [N/A], 2070, 1000.0, 0x0, {na}, {na}, {na}, {na}",
+        f"3, {U3}, 1400, 2070, 1390.5, 0x0000000000000008, {a}, {na}, {na}, {na}",
+        f"0, {U0}, 2040, 2070, 1200.0, 0x0000000000000000, {na}, {na}, {na}, {na}",
+    ]
+    # torch's device 0 is nvidia-smi's GPU 3 (UUID without the GPU- prefix, as torch prints it)
+    d = bench.ClockSampler.summarise(lines, 0, U3[4:])
+    assert d["matched_by"] == "uuid" and d["gpu"] == U3 and d["samples"] == 2
+    assert d["sm_mhz"] == 1450.0 and d["reasons"] == ["hw_slowdown"]
+    # UUID unknown or not listed: the index decides, as nvidia-smi numbers them
+    for u in (None, "GPU-ffff"):
+        d = bench.ClockSampler.summarise(lines, 0, u)
+        assert d == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
+                     "gpu": "index 0", "matched_by": "index"}
+    assert bench.ClockSampler.summarise(lines, 5, None) is None
+    assert bench.ClockSampler.summarise([], 0) is None and bench.ClockSampler.summarise(["x"], 0) is None
