@@ -221,7 +221,7 @@ def cpu_baseline(wl, seconds=12.0, sample_cells=16384):
         if time.perf_counter() - t0 >= seconds or steps >= wl.n_steps:
             break
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.max_threads()
     return {"value": sub.n_cells * sub.n_bins * steps / el, "unit": "bin-steps/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {steps} flow steps of {wl.name}"}
@@ -247,7 +247,7 @@ def run_reference(args):
         oracle.step(P, R0, sub.pressure_step(n), sub.dt, R, V, h)
     el = time.perf_counter() - t0
     value = sub.n_cells * sub.n_bins * args.steps / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.max_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bin-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",

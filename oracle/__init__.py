@@ -117,6 +117,8 @@ def _lib():
             alt = os.environ.get("PAB_ORACLE_LIB")
             lib = ctypes.CDLL(alt if alt else build())
             P = ctypes.POINTER(_Params)
+            lib.orc_max_threads.argtypes = []
+            lib.orc_max_threads.restype = ctypes.c_int
             lib.orc_bins.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, _dp, _dp]
             lib.orc_bins.restype = ctypes.c_int
@@ -180,6 +182,11 @@ def _ptr(a, typ):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def max_threads() -> int:
+    """Threads the oracle's OpenMP loops run with."""
+    return int(_lib().orc_max_threads())
 
 
 def bins(n_bins: int, R0ref: float = 10e-6, s: float = 0.3, K: float = 5.0):

@@ -30,6 +30,20 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the OpenMP regions below run with (1 without OpenMP): the core count reported
+ * beside the oracle's timings.  A query only; no arithmetic of the method. */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Parameters of the liquid, the gas and the stepper.                        */
