@@ -49,9 +49,9 @@ typedef struct {
     int32_t precision;        /* PAB_FP64 or PAB_MIXED, for every slot */
     int64_t capacity_bins;    /* arena size in bin-states, at most PAB_MAX_CELLS x PAB_MAX_BINS;
                                  0: 80 % of free device memory / 20 B */
-    int32_t block_warps;      /* warps per CTA (0: 8) */
+    int32_t block_warps;      /* warps per CTA, 0..16 (0: 8) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM, 0..32 (0: as many as fit, at most 4) */
-    int32_t bins_per_grab;    /* bins a warp takes per shared-memory grab (0: 1) */
+    int32_t bins_per_grab;    /* bins a warp takes per shared-memory grab, 0..8 (0: 1) */
     int32_t max_bins;         /* largest Nb any slot will use (0: PAB_MAX_BINS); sizes shared memory */
 } pab_batch_config;
 
