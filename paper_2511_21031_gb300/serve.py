@@ -21,6 +21,13 @@ next iteration boundary and share the following launches with them.  Each
 request's arithmetic is independent of the others (the kernel owns every
 (cell, bin) of a slot alone), so its result is the same alone and in the mix.
 Latency is completion time minus arrival time on the engine's clock.
+
+Cancellation and timeouts are host-side and act at iteration boundaries, when
+no launch is in flight: a cancelled request (cancel(rid)) or one still
+unfinished `timeout` seconds after its arrival leaves the queue, or, if
+active, is released with the work done so far; it completes with status
+"cancelled" or "timeout" and no result, and its slot and arena space go to
+the queue.
 """
 from __future__ import annotations
 
@@ -50,12 +57,13 @@ class _Active:
 class Completion:
     rid: int
     arrival: float
-    admitted: float
+    admitted: float          # NaN for a request that never left the queue
     done: float
-    bin_steps: int
+    bin_steps: int           # work done (all of it for status "done")
     flags: int
     attempts: int
     moments: Optional[np.ndarray] = None
+    status: str = "done"     # "done", "cancelled" or "timeout"
 
     @property
     def latency(self):
@@ -76,6 +84,12 @@ class ServingEngine:
         self.keep_moments = keep_moments
         self.stream = stream or torch.cuda.Stream()
         self.dev = torch.device("cuda", torch.cuda.current_device())
+        self._cancelled = set()
+
+    def cancel(self, rid: int):
+        """Cancel request rid: it leaves the queue, or its slot is released, at the next
+        iteration boundary (safe to call from another thread while run() serves)."""
+        self.__dict__.setdefault("_cancelled", set()).add(rid)
 
     def _admit(self, req, now):
         w = req.work
@@ -90,11 +104,13 @@ class ServingEngine:
         self.batch.bind(slot, p, w.dt, moments=m)
         return _Active(req, slot, 0, theta, p, m, now)
 
-    def run(self, requests: List, clock: str = "wall", max_iterations: int = 10 ** 9) -> Dict:
+    def run(self, requests: List, clock: str = "wall", max_iterations: int = 10 ** 9,
+            timeout: Optional[float] = None) -> Dict:
         """Serve the requests (sorted by arrival).  clock="wall": arrivals are
         released by wall time since start; clock="virtual": time advances by the
         GPU time of each iteration only (arrivals are released at iteration
-        boundaries in virtual time)."""
+        boundaries in virtual time).  timeout: seconds after its arrival within
+        which a request must finish, else it is dropped (status "timeout")."""
         t = self.torch
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
@@ -110,6 +126,15 @@ class ServingEngine:
         def now():
             return time.perf_counter() - t0 if clock == "wall" else vnow
 
+        cancelled = self.__dict__.setdefault("_cancelled", set())
+
+        def dropped(req, tn):
+            if req.rid in cancelled:
+                return "cancelled"
+            if timeout is not None and tn - req.arrival > timeout:
+                return "timeout"
+            return None
+
         while (pending or waiting or active) and iters < max_iterations:
             tn = now()
             if not active and not waiting and pending and pending[0].arrival > tn:
@@ -121,6 +146,25 @@ class ServingEngine:
                 tn = now()
             while pending and pending[0].arrival <= tn:
                 waiting.append(pending.popleft())
+            # cancellations and timeouts, at the boundary (no launch in flight)
+            if cancelled or timeout is not None:
+                for r in [r for r in waiting if dropped(r, tn)]:
+                    waiting.remove(r)
+                    done.append(Completion(r.rid, r.arrival, float("nan"), tn, 0, 0, 0,
+                                           status=dropped(r, tn)))
+                keep = []
+                for a in active:
+                    why = dropped(a.req, tn)
+                    if why is None:
+                        keep.append(a)
+                        continue
+                    w = a.req.work
+                    st = self.batch.status(a.slot, stream=self.stream)
+                    self.batch.release(a.slot, stream=self.stream)
+                    done.append(Completion(a.req.rid, a.req.arrival, a.admitted_at, tn,
+                                           w.n_cells * w.n_bins * a.step, st["flags"], st["n_attempts"],
+                                           status=why))
+                active = keep
             while waiting:
                 a = self._admit(waiting[0], tn)
                 if a is None:
@@ -169,9 +213,13 @@ class ServingEngine:
                     still.append(a)
             active = still
         elapsed = now()
-        lat = np.array([c.latency for c in done]) if done else np.array([float("nan")])
+        cancelled.clear()  # a cancellation applies to the run it was made for
+        ok = [c for c in done if c.status == "done"]
+        lat = np.array([c.latency for c in ok]) if ok else np.array([float("nan")])
         return {
-            "completed": len(done), "iterations": iters, "elapsed_s": elapsed, "gpu_busy_s": busy_s,
+            "completed": len(ok), "cancelled": sum(c.status == "cancelled" for c in done),
+            "timed_out": sum(c.status == "timeout" for c in done),
+            "iterations": iters, "elapsed_s": elapsed, "gpu_busy_s": busy_s,
             "bin_steps": total_bin_steps,
             "throughput_bin_steps_per_s": total_bin_steps / elapsed if elapsed > 0 else float("nan"),
             "gpu_throughput_bin_steps_per_s": total_bin_steps / busy_s if busy_s > 0 else float("nan"),
@@ -202,12 +250,14 @@ def main(argv=None):
     ap.add_argument("--capacity-bins", type=int, default=2_000_000_000)
     ap.add_argument("--clock", default="wall", choices=("wall", "virtual"))
     ap.add_argument("--launch", type=int, nargs=3, default=None)
+    ap.add_argument("--timeout", type=float, default=None,
+                    help="seconds after arrival within which a request must finish")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     for rate in args.rates:
         reqs = workloads.request_stream(n=args.requests, rate=rate, n_steps=args.steps)
         eng = ServingEngine(capacity_bins=args.capacity_bins, launch=args.launch)
-        rep = eng.run(reqs, clock=args.clock)
+        rep = eng.run(reqs, clock=args.clock, timeout=args.timeout)
         eng.close()
         rep.pop("completions")
         print(json.dumps(dict(rate=rate, requests=args.requests, **rep)), flush=True)

@@ -1,6 +1,7 @@
 """Continuous batching: requests admitted by device memory as slots free up,
-their steps sharing launches with the requests already running, and every
-result identical alone and in the mix."""
+their steps sharing launches with the requests already running, every result
+identical alone and in the mix, and a request cancelled while running released
+without disturbing the others."""
 import numpy as np
 import pytest
 
@@ -56,3 +57,36 @@ def test_request_larger_than_the_arena_is_reported():
     with pytest.raises(RuntimeError):
         eng.run(reqs, clock="virtual")
     eng.close()
+
+
+def test_request_cancelled_while_running_leaves_the_others_untouched():
+    """A request cancelled after five launches is released at the next iteration boundary with
+    the work done so far; every other request's result is still the one it gets alone."""
+    reqs = _requests(n=6, seed=34)
+    cap = sum(r.work.bins_total for r in reqs)
+    eng = ServingEngine(capacity_bins=cap, max_slots=len(reqs), keep_moments=True)
+    victim = reqs[0].rid
+    launches = [0]
+    step = eng.batch.step
+
+    def step_then_cancel(*a, **k):
+        step(*a, **k)
+        launches[0] += 1
+        if launches[0] == 5:
+            eng.cancel(victim)
+    eng.batch.step = step_then_cancel
+    mix = eng.run(reqs, clock="virtual")
+    eng.close()
+    assert (mix["completed"], mix["cancelled"]) == (len(reqs) - 1, 1)
+    by_id = {c.rid: c for c in mix["completions"]}
+    v = by_id[victim]
+    assert v.status == "cancelled" and v.moments is None
+    assert 0 < v.bin_steps < reqs[0].work.bins_total * reqs[0].work.n_steps
+    for r in reqs[1:]:
+        e = ServingEngine(capacity_bins=r.work.bins_total, max_slots=1, keep_moments=True)
+        alone = e.run([r], clock="virtual")
+        e.close()
+        a = alone["completions"][0]
+        assert by_id[r.rid].status == "done"
+        np.testing.assert_array_equal(a.moments, by_id[r.rid].moments)
+        assert a.attempts == by_id[r.rid].attempts

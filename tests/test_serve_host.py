@@ -5,10 +5,12 @@ bin-states, admission while the bins fit) and a fake CUDA clock (every batched
 step costs STEP_S seconds), on the engine's virtual clock, so the schedule is
 exact and can be checked by hand: FIFO admission in arrival order, a head of
 queue that waits for memory without being overtaken, arrivals joining at the
-next iteration boundary, idle gaps, latency and bin-step accounting, and the
-per-step carrier pressure bound to each slot.  The device side of the same loop
+next iteration boundary, idle gaps, latency and bin-step accounting, the
+per-step carrier pressure bound to each slot, and cancellation and timeouts
+of queued and active requests.  The device side of the same loop
 is covered by tests/test_gpu_serve.py."""
 import contextlib
+import math
 
 import numpy as np
 import pytest
@@ -30,6 +32,7 @@ class FakeBatch:
         self.admitted = []      # slots in admission order
         self.steps = []         # active slots at each batched step
         self.pressures = {}     # slot -> [p of each step]
+        self.on_step = None     # called with the number of steps taken so far
 
     def try_admit(self, n_cells, n_bins, stream=None, **cfg):
         need = n_cells * n_bins
@@ -53,6 +56,8 @@ class FakeBatch:
             s["steps"] += 1
         self.steps.append(sorted(self.slots))
         self.clock += STEP_S
+        if self.on_step:
+            self.on_step(len(self.steps))
 
     def status(self, slot, stream=None):
         return {"flags": 0, "n_attempts": self.slots[slot]["steps"]}
@@ -109,6 +114,7 @@ def engine(capacity):
     eng.keep_moments = False
     eng.stream = None
     eng.dev = torch.device("cpu")
+    eng._cancelled = set()
     return eng, fb
 
 
@@ -194,3 +200,55 @@ def test_each_step_binds_the_workloads_own_carrier_pressure():
         assert len(ps) == r.work.n_steps
         for n, p in enumerate(ps):
             np.testing.assert_allclose(p, r.work.pressure_step(n), rtol=1e-15, atol=0.0)
+
+
+def test_no_cancellation_or_timeout_by_default():
+    eng, _ = engine(capacity=1000)
+    rep = eng.run([req(0, 0.0, cells=4, steps=3)], clock="virtual")
+    assert (rep["completed"], rep["cancelled"], rep["timed_out"]) == (1, 0, 0)
+    assert rep["completions"][0].status == "done"
+
+
+def test_cancelled_queued_request_never_takes_a_slot():
+    eng, fb = engine(capacity=100)
+    reqs = [req(0, 0.0, cells=20, steps=3), req(1, 0.0, cells=20, steps=2), req(2, 0.0, cells=5, steps=2)]
+    eng.cancel(1)                                   # r1 would wait for r0's memory
+    rep = eng.run(reqs, clock="virtual")
+    c = by_rid(rep)
+    assert c[1].status == "cancelled" and math.isnan(c[1].admitted) and c[1].bin_steps == 0
+    assert fb.admitted == [0, 1]                    # slots of r0 and r2; r1 never admitted
+    assert fb.steps[0] == [0, 1]                    # r2 no longer waits behind r1
+    assert c[2].latency == pytest.approx(2 * STEP_S)
+    assert (rep["completed"], rep["cancelled"]) == (2, 1)
+    assert not eng._cancelled                       # cleared for the next run
+
+
+def test_cancelled_active_request_is_released_at_the_next_boundary():
+    eng, fb = engine(capacity=100)
+    reqs = [req(0, 0.0, cells=20, steps=10), req(1, 0.0, cells=20, steps=2)]   # r1 waits for r0
+    fb.on_step = lambda n: eng.cancel(0) if n == 4 else None
+    rep = eng.run(reqs, clock="virtual")
+    c = by_rid(rep)
+    assert c[0].status == "cancelled" and c[0].done == pytest.approx(4 * STEP_S)
+    assert c[0].bin_steps == 60 * 4 and c[0].attempts == 4
+    assert c[1].admitted == pytest.approx(4 * STEP_S) and c[1].status == "done"
+    assert fb.steps == [[0]] * 4 + [[1]] * 2 and fb.used == 0
+    assert rep["bin_steps"] == 60 * 4 + 60 * 2
+    assert rep["latency_s"]["p50"] == pytest.approx(c[1].latency)   # over finished requests only
+
+
+def test_timeout_drops_queued_and_active_requests():
+    eng, fb = engine(capacity=100)
+    reqs = [req(0, 0.0, cells=20, steps=10), req(1, 0.0, cells=20, steps=2),
+            req(2, 4.0 * STEP_S, cells=5, steps=2)]
+    rep = eng.run(reqs, clock="virtual", timeout=4.5 * STEP_S)
+    c = by_rid(rep)
+    # r0 runs 5 steps and is over its time at the boundary at 5 ms; r1 waited for memory all
+    # that time and times out in the queue; r2, queued behind r1 since 4 ms, is admitted at
+    # that boundary and finishes
+    assert c[0].status == "timeout" and c[0].bin_steps == 60 * 5 and c[0].done == pytest.approx(5 * STEP_S)
+    assert c[1].status == "timeout" and math.isnan(c[1].admitted)
+    assert c[2].status == "done" and c[2].admitted == pytest.approx(5 * STEP_S)
+    assert c[2].latency == pytest.approx(3 * STEP_S)
+    assert (rep["completed"], rep["timed_out"], rep["cancelled"]) == (1, 2, 0)
+    assert fb.used == 0 and not fb.slots
