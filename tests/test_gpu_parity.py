@@ -293,3 +293,36 @@ def test_invalid_carried_step_size_falls_back_to_dt():
         m.close()
     for x, y in zip(*outs):
         assert torch.equal(x, y)
+
+
+def test_calls_on_other_streams_give_the_create_streams_bits():
+    """Every call is ordered on the stream it is given, not on the one the handle was created
+    on: steps issued on a side stream and then on the legacy default stream (the caller ordering
+    the two) give the bits of the same steps on the create stream."""
+    import torch
+    wl = workloads.config_small()
+    ps = [torch.as_tensor(wl.pressure_step(k), device="cuda") for k in range(30)]
+    s_create, s_side = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    a = pab.Solver(wl.n_cells, wl.n_bins, s_lognormal=wl.s, stream=s_create)
+    b = pab.Solver(wl.n_cells, wl.n_bins, s_lognormal=wl.s, stream=s_create)
+    ma = torch.empty((7, wl.n_cells), dtype=torch.float64, device="cuda")
+    mb = torch.empty_like(ma)
+    torch.cuda.synchronize()
+    for k in range(30):
+        a.step(ps[k], wl.dt, moments=ma, stream=s_create)
+    for k in range(15):
+        b.step(ps[k], wl.dt, moments=mb, stream=s_side)
+    legacy = torch.cuda.default_stream()
+    legacy.wait_stream(s_side)
+    for k in range(15, 30):
+        b.step(ps[k], wl.dt, moments=mb, stream=legacy)
+    ra = a.get_state(stream=s_create)
+    rb = b.get_state(stream=legacy)
+    torch.cuda.synchronize()
+    for x, y in zip(ra, rb):
+        assert torch.equal(x, y)
+    assert torch.equal(ma, mb)
+    assert a.status(stream=s_create)["n_attempts"] == b.status(stream=legacy)["n_attempts"]
+    a.close()
+    b.close()
