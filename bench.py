@@ -331,19 +331,35 @@ def _mixed_error_sample(wl, n_steps, n_cells=256):
         p = torch.as_tensor(sub.pressure_step(n), device="cuda")
         sm.step(p, sub.dt, moments=mm)
         sd.step(p, sub.dt, moments=md)
-    Rm, _, _ = sm.get_state()
+    Rm, Vm, _ = sm.get_state()
     Rd, Vd, _ = sd.get_state()
     w = np.array(sd.w)
     g, o = mm.cpu().numpy(), md.cpu().numpy()
-    Rm, Rd, Vd = Rm.cpu().numpy(), Rd.cpu().numpy(), Vd.cpu().numpy()
-    scale = np.sum(w[:, None] * Rd * Rd * (np.abs(Vd) + 1e-2), axis=0)
-    out = {"R": float(np.max(np.abs(Rm - Rd) / Rd)),
-           "alpha": float(np.max(np.abs(g[1] - o[1]) / o[1])),
-           "R2Rdot": float(np.max(np.abs(g[3] - o[3]) / scale)),
-           "sample": f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {n_steps} steps"}
+    Rm, Vm, Rd, Vd = Rm.cpu().numpy(), Vm.cpu().numpy(), Rd.cpu().numpy(), Vd.cpu().numpy()
+    v_floor = 1e-3 * math.sqrt(sub.fluid["p0"] / sub.fluid["rho"])
+    out = _mixed_errors(g, o, Rm, Vm, Rd, Vd, w, v_floor)
+    out["sample"] = f"{sub.n_cells} seeded cells x {sub.n_bins} bins x {n_steps} steps"
     sm.close()
     sd.close()
     return out
+
+
+def _mixed_errors(g, o, Rm, Vm, Rd, Vd, w, v_floor):
+    """Error of every mixed output against the FP64 one: R and the positive moments relative,
+    Rdot against max(|Rdot|, v_floor), the signed sums (<R^2 Rdot>, S_alpha) against the sum of
+    their absolute terms plus the floor, and <R^3 Rdot^2>/<R^3> against max(|value|, v_floor^2)."""
+    w = np.asarray(w)[:, None]
+    scale = np.sum(w * Rd * Rd * (np.abs(Vd) + v_floor), axis=0)
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+    return {"R": rel(Rm, Rd),
+            "Rdot": float(np.max(np.abs(Vm - Vd) / np.maximum(np.abs(Vd), v_floor))),
+            "alpha": rel(g[1], o[1]), "R3": rel(g[2], o[2]),
+            "R2Rdot": float(np.max(np.abs(g[3] - o[3]) / scale)),
+            "S_alpha": float(np.max(np.abs(g[4] - o[4]) / (3.0 * o[1] * scale / o[2]))),
+            "R3pbw_over_R3": rel(g[5], o[5]),
+            "R3Rdot2_over_R3": float(np.max(np.abs(g[6] - o[6]) / np.maximum(np.abs(o[6]), v_floor ** 2)))}
 
 
 TRANSFER_PV = 2338.0  # saturated vapour pressure of water at 20 C

@@ -98,3 +98,28 @@ def test_clock_summary_of_nvidia_smi_samples():
                      "gpu": "index 0", "matched_by": "index"}
     assert bench.ClockSampler.summarise(lines, 5, None) is None
     assert bench.ClockSampler.summarise([], 0) is None and bench.ClockSampler.summarise(["x"], 0) is None
+
+
+def test_mixed_error_report_covers_every_output():
+    """The bench's mixed-against-FP64 error: zero for equal outputs, the planted relative error
+    for each output, and the floors where a value passes through zero."""
+    import numpy as np
+    bench = _bench()
+    g = np.random.Generator(np.random.PCG64(5))
+    B, C, vf = 5, 7, 1e-2
+    w = g.uniform(0.1, 1.0, B)
+    w /= w.sum()
+    Rd = g.uniform(5e-6, 2e-5, (B, C))
+    Vd = g.normal(0.0, 1.0, (B, C))
+    o = np.abs(g.normal(1.0, 0.1, (7, C)))
+    o[3] = g.normal(0.0, 1e-10, C)           # signed sums
+    o[4] = g.normal(0.0, 1e3, C)
+    e0 = bench._mixed_errors(o.copy(), o, Rd.copy(), Vd.copy(), Rd, Vd, w, vf)
+    keys = {"R", "Rdot", "alpha", "R3", "R2Rdot", "S_alpha", "R3pbw_over_R3", "R3Rdot2_over_R3"}
+    assert set(e0) == keys and all(v == 0.0 for v in e0.values())
+    eps = 1e-7
+    e = bench._mixed_errors(o * (1 + eps), o, Rd * (1 + eps), Vd * (1 + eps), Rd, Vd, w, vf)
+    for k in ("R", "alpha", "R3", "R3pbw_over_R3"):
+        assert e[k] == pytest.approx(eps, rel=1e-6), k
+    assert 0.0 < e["Rdot"] <= eps * (1 + 1e-6)
+    assert 0.0 < e["R2Rdot"] < eps and 0.0 < e["S_alpha"] and e["R3Rdot2_over_R3"] <= eps * (1 + 1e-6)
