@@ -281,3 +281,20 @@ def test_product_path_fails_loudly_without_its_library_or_a_device(monkeypatch, 
         batch.Batch(max_slots=2, capacity_bins=100)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         el.BubbleCloud([[0.0], [0.0], [0.0]], [1e-5], 4, 4, 4, 1e-4)
+
+
+@pytest.mark.parametrize("header", [os.path.basename(h) for h in HEADERS])
+def test_header_compiles_standalone_as_c_and_cpp(header):
+    """Each public header is a C ABI: it compiles on its own as C99, C11 and C++17 with all
+    warnings as errors, and pulls in nothing but the standard integer types and pab.h."""
+    with tempfile.TemporaryDirectory() as d:
+        for std, ext, cc in (("c99", "c", "gcc"), ("c11", "c", "gcc"), ("c++17", "cpp", "g++")):
+            src = os.path.join(d, "t." + ext)
+            open(src, "w").write(f'#include "{header}"\nint main(void) {{ return 0; }}\n')
+            r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                                "-I", os.path.join(ROOT, "include"), "-c", src, "-o", os.path.join(d, "t.o")],
+                               capture_output=True, text=True)
+            assert r.returncode == 0, (header, std, r.stderr[-800:])
+    text = open(os.path.join(ROOT, "include", header)).read()
+    includes = set(re.findall(r'#include\s+[<"]([^>"]+)[>"]', text))
+    assert includes <= {"stdint.h", "stddef.h", "pab.h"}, includes
