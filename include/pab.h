@@ -145,8 +145,9 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out);
 pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_dev,
                            double dt, double *moments_dev, void *stream);
 
-/* Reduce the current state into moments_dev [7][C] (same rows as above)
- * without advancing it.  nb_dev as in pab_bubble_step. */
+/* Reduce the current state into moments_dev [7][C] (same rows as above:
+ * Eqs. e:ndf, e:alpha and e:pressure of Sec. 2.2) without advancing it.
+ * nb_dev as in pab_bubble_step.  Errors: PAB_EINVAL (NULL moments_dev), PAB_ECUDA. */
 pab_status pab_moments(pab_t *h, const double *nb_dev, double *moments_dev, void *stream);
 
 /*
@@ -154,7 +155,8 @@ pab_status pab_moments(pab_t *h, const double *nb_dev, double *moments_dev, void
  * when not NULL) to the device, runs pab_bubble_step, copies the moments to
  * moments_host [7][C] (when not NULL) and synchronises `stream`.  Pinned host
  * memory makes the copies asynchronous DMA.  Staging buffers are allocated on
- * first use and owned by the handle.
+ * first use and owned by the handle.  The step is the one of pab_bubble_step;
+ * the host buffering has no counterpart in the paper.
  */
 pab_status pab_bubble_step_host(pab_t *h, const double *p_inf_host, const double *nb_host,
                                 double dt, double *moments_host, void *stream);
@@ -181,8 +183,9 @@ pab_status pab_bubble_step_host_async(pab_t *h, const double *p_inf_host, const 
 pab_status pab_host_wait(pab_t *h);
 
 /*
- * Synchronise `stream`, return the status accumulated since the last call
- * and reset it: *flags = OR of per-bin PAB_FLAG_* bits, *n_flagged = number
+ * Status of the bounded stepper (no counterpart in the paper, which describes
+ * no failure handling).  Synchronise `stream`, return the status accumulated
+ * since the last call and reset it: *flags = OR of per-bin PAB_FLAG_* bits, *n_flagged = number
  * of bin-steps that set any bit, *n_attempts = total trials, *n_fp64 = trials
  * taken on the FP64 path in PAB_MIXED mode.  Any output pointer may be NULL.
  * Returns PAB_ENONFINITE or PAB_ESTEP_LIMIT when those bits are set, else PAB_OK.
@@ -190,10 +193,13 @@ pab_status pab_host_wait(pab_t *h);
 pab_status pab_status_flags(pab_t *h, uint32_t *flags, int64_t *n_flagged, int64_t *n_attempts,
                             int64_t *n_fp64, void *stream);
 
-/* Checkpoint / resume: copy the state out of / into the handle (device
- * buffers [Nb][C]; h_dev may be NULL to leave h untouched on set).  A carried
+/* Checkpoint / resume (no counterpart in the paper): copy the state out of /
+ * into the handle (device buffers [Nb][C]; h_dev may be NULL to leave h
+ * untouched on set).  A carried
  * h that is not a number in (0, dt] (NaN, zero, negative, infinite or above
- * the call's dt) makes the next call start that bin's step at dt. */
+ * the call's dt) makes the next call start that bin's step at dt.  On get any
+ * destination may be NULL to skip it.  Errors: PAB_EINVAL (NULL handle; on set,
+ * NULL R_dev or Rdot_dev), PAB_ECUDA. */
 pab_status pab_get_state(pab_t *h, double *R_dev, double *Rdot_dev, float *h_dev, void *stream);
 pab_status pab_set_state(pab_t *h, const double *R_dev, const double *Rdot_dev, const float *h_dev,
                          void *stream);
@@ -263,7 +269,8 @@ pab_status pab_bubble_step_noalloc(const pab_config *cfg, const double *p_inf_de
                                    double *Rdot_dev, float *h_dev, double *moments_dev,
                                    int64_t *status_dev, void *stream);
 
-/* Release the state on the creation stream.  NULL-safe. */
+/* Release the state on the creation stream (waiting for pipelined host
+ * calls first).  NULL-safe. */
 void pab_destroy(pab_t *h);
 
 /* Description of the last failure on this handle ("" if none). */
