@@ -34,7 +34,8 @@ pab_status pab_strang_half(pab_t *h, const double *p_inf_dev, const double *nb_d
                            double *moments_dev, void *stream);
 
 /*
- * Conservative bubble variables of the current state: qR_dev[i][c] = n_b[c] R,
+ * Conservative bubble variables of the current state (the transported n_b R_i and
+ * n_b Rdot_i of Sec. 2.2 and Listing 2): qR_dev[i][c] = n_b[c] R,
  * qV_dev[i][c] = n_b[c] Rdot ([Nb][C], device).  nb_dev [C] or NULL for the
  * handle's default n_b.  Errors: PAB_EINVAL (NULL outputs), PAB_ECUDA.
  */
