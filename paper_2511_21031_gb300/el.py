@@ -115,9 +115,20 @@ class BubbleCloud:
                                             _stream(stream) or None), "pab_el_get_state")
         return R, V, h
 
+    def _bubbles(self, t, dtype, name):
+        if t is None:
+            return None
+        if t.device != self.device or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != (self.N,):
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of {self.N} bubbles on {self.device}")
+        return t.data_ptr()
+
     def set_state(self, R, V, h=None, stream=None):
-        self._check(load().pab_el_set_state(self.handle, R.data_ptr(), V.data_ptr(),
-                                            h.data_ptr() if h is not None else None,
+        import torch
+        if R is None or V is None:
+            raise ValueError("R and Rdot are required")
+        self._check(load().pab_el_set_state(self.handle, self._bubbles(R, torch.float64, "R"),
+                                            self._bubbles(V, torch.float64, "Rdot"),
+                                            self._bubbles(h, torch.float32, "h"),
                                             _stream(stream) or None), "pab_el_set_state")
 
     def close(self):

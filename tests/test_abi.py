@@ -298,3 +298,35 @@ def test_header_compiles_standalone_as_c_and_cpp(header):
     text = open(os.path.join(ROOT, "include", header)).read()
     includes = set(re.findall(r'#include\s+[<"]([^>"]+)[>"]', text))
     assert includes <= {"stdint.h", "stddef.h", "pab.h"}, includes
+
+
+def test_bubble_cloud_set_state_checks_shapes(monkeypatch):
+    """The volume-averaged binding refuses state tensors of the wrong length, type or device
+    before the library sees them."""
+    import torch
+    from paper_2511_21031_gb300 import el
+    calls = []
+
+    class FakeLib:
+        def pab_el_set_state(self, h, R, V, hh, s):
+            calls.append((R, V, hh))
+            return pab.PAB_OK
+
+    monkeypatch.setattr(el, "load", lambda *a, **k: FakeLib())
+    cl = object.__new__(el.BubbleCloud)
+    cl.handle, cl.device, cl.N = 1, torch.device("cpu"), 3
+    import types
+    s = types.SimpleNamespace(cuda_stream=0)
+    R = torch.ones(3, dtype=torch.float64)
+    cl.set_state(R, R.clone(), torch.ones(3, dtype=torch.float32), stream=s)
+    cl.set_state(R, R.clone(), stream=s)
+    assert len(calls) == 2 and calls[1][2] is None
+    for bad in (dict(R=torch.ones(4, dtype=torch.float64)), dict(R=torch.ones(3, dtype=torch.float32)),
+                dict(h=torch.ones(3, dtype=torch.float64)), dict(V=None),
+                dict(R=torch.ones((3, 1), dtype=torch.float64))):
+        kw = dict(R=R, V=R.clone(), h=None)
+        kw.update(bad)
+        with pytest.raises(ValueError):
+            cl.set_state(kw["R"], kw["V"], kw["h"], stream=s)
+    assert len(calls) == 2
+    cl.handle = None
