@@ -45,6 +45,19 @@ MUTATIONS = [
      "p[c] = (1.0 - alpha) * p_l[c] + alpha * (moments[5 * C + c] + rho * moments[6 * C + c]);"),
     ("stiffened gas without gamma on pi_inf", "p_l[i] = (gamma_l - 1.0) * rho_l[i] * e_l[i] - gamma_l * pi_inf;",
      "p_l[i] = (gamma_l - 1.0) * rho_l[i] * e_l[i] - pi_inf;"),
+    ("alpha with 4 pi for 4/3 pi", "double alpha = 4.0 / 3.0 * M_PI * n_b[c] * M3;",
+     "double alpha = 4.0 * M_PI * n_b[c] * M3;"),
+    ("bin spacing over B instead of B - 1", "double dphi = 2.0 * K * s / (double)(B - 1);",
+     "double dphi = 2.0 * K * s / (double)B;"),
+    ("bin weights not normalised", "w[i] = w[i] / total;", "w[i] = w[i];"),
+    ("polytropic exponent gamma for 3 gamma", "double p_gas = p_g0 * pow(R0 / R, 3.0 * P->gamma);",
+     "double p_gas = p_g0 * pow(R0 / R, P->gamma);"),
+    ("p_g0 without surface tension", "double p_g0 = P->p0 + 2.0 * P->sigma / R0 - P->pv;",
+     "double p_g0 = P->p0 - P->pv;"),
+    ("embedded member taken as the Euler stage", "z[k] = 0.5 * y[k] + 0.5 * (y1[k] + h * f[k]);",
+     "z[k] = y1[k];"),
+    ("error norm without the Rdot floor", "if (vscale < v_floor)", "if (0)"),
+    ("<R^3 p_bw> with R^2", "M3P += w[b] * r3 * p_bw;", "M3P += w[b] * r * r * p_bw;"),
 ]
 
 # Mistakes in the non-polytropic contents, caught by tests/test_oracle_transfer.py.
