@@ -347,15 +347,15 @@ __device__ __forceinline__ float growth_factor(const StepConst &K, float errf, b
 // (two FP64 products and integer compares on the threefold differences the
 // trial carries, against 3 tol; when ok holds R3 is positive and finite).  The
 // factor takes err from the FP32 images of the same quantities.
-struct Verdict {
+struct Decision {
     bool accept;
     float fac;
 };
-__device__ __forceinline__ Verdict judge64(const StepConst &K, const Trial &t)
+__device__ __forceinline__ Decision decide64(const StepConst &K, const Trial &t)
 {
     const double aR = abs_nn(t.R);
     const double vs = max_nn(abs_nn(t.V), K.v_floor);
-    Verdict v;
+    Decision v;
     v.accept = t.ok && le(abs_nn(t.eR), K.tol3 * aR) && le(abs_nn(t.eV), K.tol3 * vs);
     const float errf = (1.0f / 3.0f) * fmaxf(__fdividef(d2f(abs_nn(t.eR)), d2f(aR)),
                                              __fdividef(d2f(abs_nn(t.eV)), d2f(vs)));
@@ -392,7 +392,7 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
         const double ht = last ? rem : h;
         const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g);
         ++n;
-        const Verdict vd = judge64(K, tr);
+        const Decision vd = decide64(K, tr);
         const double fac = f2d_fin(vd.fac);
         if (vd.accept) {
             R = tr.R;

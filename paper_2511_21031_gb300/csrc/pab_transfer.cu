@@ -130,7 +130,7 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
         const double ht = last ? rem : h;
         const Trial4 tr = trial4(K, mRg, pinf_rho, y, ht);
         ++n;
-        const Verdict vd = judge64(K, Trial{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok});
+        const Decision vd = decide64(K, Trial{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok});
         const double fac = f2d_fin(vd.fac);
         if (vd.accept) {
             y = tr.y;
