@@ -499,6 +499,85 @@ def _bench_serving(args, n_requests=16, rate=200.0):
                        "bins_per_grab": tune["bins_per_grab"], "autotuned": True}}
 
 
+# Algorithmic HBM bytes of the carrier-coupling kernels (FP64): per cell and per (bin, cell).
+CLOSURE_BYTES = {
+    # alpha, <R^3 p_bw>/<R^3>, <R^3 Rdot^2>/<R^3> and p_l in, p out
+    "mixture_pressure": (40.0, 0.0),
+    # R and Rdot in, n_b R and n_b Rdot out (default n_b)
+    "get_conservative": (0.0, 32.0),
+    # alpha in and n_b out per cell; n_b R and n_b Rdot in, R and Rdot out per bin-cell
+    "set_conservative": (16.0, 32.0),
+}
+
+
+def _bench_closure(args, stream, dev):
+    """One Strang-split flow step of the carrier coupling (pab_closure.h) on the 128^3 x 31 FP64
+    workload: the bubble half step at the flow step's start pressure, the mixture pressure from its
+    moments (the carrier pressure standing in for the liquid pressure), the conservative variables
+    out and back (the carrier transports n_b R_i and n_b Rdot_i, n_b recovered from alpha), and the
+    second half step at the end pressure.  Each kernel group is timed with CUDA events."""
+    import torch
+
+    from paper_2511_21031_gb300 import pab
+    wl = make_workload("grid128", 0, args.edge)
+    C, B = wl.n_cells, wl.n_bins
+    total = args.warmup + args.steps
+    sol = pab.Solver(C, B, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K, alpha0=wl.alpha0)
+    with torch.cuda.stream(stream):
+        ps = [wl.pressure_at(n * wl.dt, xp=torch, device=dev) for n in range(total + 1)]
+        mom = torch.empty((pab.N_MOMENTS, C), dtype=torch.float64, device=dev)
+        pmix = torch.empty(C, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    names = ("half_1", "mixture_pressure", "get_conservative", "set_conservative", "half_2")
+
+    def flow_step(n):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            sol.strang_half(ps[n], wl.dt, moments=mom, stream=stream)
+            evs[1].record(stream)
+            sol.mixture_pressure(mom, ps[n], out=pmix, stream=stream)
+            evs[2].record(stream)
+            qR, qV = sol.get_conservative(stream=stream)
+            evs[3].record(stream)
+            sol.set_conservative(mom[1], qR, qV, stream=stream)
+            evs[4].record(stream)
+            sol.strang_half(ps[n + 1], wl.dt, moments=mom, stream=stream)
+            evs[5].record(stream)
+        # qR and qV were allocated on `stream`: the caching allocator reuses their blocks only
+        # for later work on that stream, ordered after this step
+        return evs
+
+    for n in range(args.warmup):
+        flow_step(n)
+    sol.status(stream=stream)
+    torch.cuda.synchronize()
+    timed = [flow_step(args.warmup + k) for k in range(args.steps)]
+    torch.cuda.synchronize()
+    ms = {k: 0.0 for k in names}
+    for evs in timed:
+        for i, k in enumerate(names):
+            ms[k] += evs[i].elapsed_time(evs[i + 1])
+    st = sol.status(stream=stream)
+    sol.close()
+    del ps, timed
+    peak, src = _hbm_peak()
+    kernels = {}
+    for k, (per_cell, per_bin_cell) in CLOSURE_BYTES.items():
+        per_step_ms = ms[k] / args.steps
+        gbs = (per_cell * C + per_bin_cell * C * B) / (per_step_ms * 1e-3) / 1e9
+        kernels[k] = {"ms_per_step": per_step_ms, "algorithmic_gbs": gbs, "hbm_frac": gbs / peak}
+    total_ms = sum(ms.values())
+    bs = C * B * args.steps
+    return {"workload": wl.name.replace("fp64", "strang"), "label": "Strang-split flow step with the closure (FP64)",
+            "precision": "fp64", "value": bs / (total_ms * 1e-3), "unit": "bin-steps/s",
+            "ms_per_step": total_ms / args.steps,
+            "half_steps_ms_per_step": (ms["half_1"] + ms["half_2"]) / args.steps,
+            "closure_kernels": kernels, "hbm_peak_gbs": peak, "hbm_peak_source": src,
+            "trials_per_bin_step": st["n_attempts"] / bs, "status_flags": st["flags"],
+            "parity": "tests/test_gpu_closure.py (against the oracle)"}
+
+
 def _bench_el(args, stream, dev):
     """Volume-averaged (EL) model: fixed bubbles (R0 = 10 um, alpha0 = 1e-3) in a
     128^3 grid of 75 um cells, each advanced under its cell's pressure (0.5 p0 at
@@ -674,6 +753,13 @@ def run_ours(args):
     if args.variants and args.el and ws == 1:
         variants.append(_bench_el(args, stream, dev))
 
+    if args.variants and args.closure and ws == 1:
+        try:
+            variants.append(_bench_closure(args, stream, dev))
+        except Exception as e:  # a failed extra line must not cost the bench its result
+            variants.append({"workload": "strang closure", "error": repr(e)[:300]})
+            torch.cuda.synchronize()
+
     if args.variants and args.serving and ws == 1:
         variants.append(_bench_serving(args))
 
@@ -741,6 +827,8 @@ def main():
                     help="skip the continuous-batching serving line")
     ap.add_argument("--no-transfer", dest="transfer", action="store_false",
                     help="skip the heat-and-mass-transfer contents line")
+    ap.add_argument("--no-closure", dest="closure", action="store_false",
+                    help="skip the Strang-split flow step with the carrier-coupling kernels")
     ap.add_argument("--no-el", dest="el", action="store_false",
                     help="skip the volume-averaged (EL) line")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",

@@ -123,3 +123,69 @@ def test_mixed_error_report_covers_every_output():
         assert e[k] == pytest.approx(eps, rel=1e-6), k
     assert 0.0 < e["Rdot"] <= eps * (1 + 1e-6)
     assert 0.0 < e["R2Rdot"] < eps and 0.0 < e["S_alpha"] and e["R3Rdot2_over_R3"] <= eps * (1 + 1e-6)
+
+
+def test_closure_line_times_each_kernel_group(monkeypatch):
+    """The Strang-split closure line on the CPU with a fake solver whose calls advance a fake
+    event clock by known amounts: per-group times, the flow-step rate and each closure kernel's
+    algorithmic bandwidth come out of that clock, and set_conservative gets alpha from row 1."""
+    import contextlib
+    import types
+
+    import torch
+    from paper_2511_21031_gb300 import pab
+    bench = _bench()
+    clock = [0.0]
+    cost = {"strang_half": 4.0, "mixture_pressure": 1.0, "get_conservative": 2.0, "set_conservative": 3.0}
+
+    class FakeSolver:
+        def __init__(self, C, B, **kw):
+            self.C, self.B = C, B
+
+        def strang_half(self, p, dt, moments=None, stream=None):
+            assert p.shape == (self.C,) and moments.shape == (pab.N_MOMENTS, self.C)
+            clock[0] += cost["strang_half"]
+
+        def mixture_pressure(self, m, p_l, out=None, stream=None):
+            clock[0] += cost["mixture_pressure"]
+
+        def get_conservative(self, stream=None):
+            clock[0] += cost["get_conservative"]
+            return torch.zeros((self.B, self.C)), torch.zeros((self.B, self.C))
+
+        def set_conservative(self, alpha, qR, qV, stream=None):
+            assert alpha.shape == (self.C,) and qR.shape == (self.B, self.C)
+            clock[0] += cost["set_conservative"]
+
+        def status(self, stream=None):
+            return {"n_attempts": 7, "flags": 0}
+
+        def close(self):
+            pass
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = clock[0]
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(pab, "Solver", FakeSolver)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    args = types.SimpleNamespace(edge=8, warmup=3, steps=2)
+    d = bench._bench_closure(args, None, torch.device("cpu"))
+    C, B = 8 ** 3, 31
+    assert d["ms_per_step"] == pytest.approx(14.0) and d["half_steps_ms_per_step"] == pytest.approx(8.0)
+    assert d["value"] == pytest.approx(C * B / 14e-3)
+    k = d["closure_kernels"]
+    assert k["mixture_pressure"]["ms_per_step"] == pytest.approx(1.0)
+    assert k["mixture_pressure"]["algorithmic_gbs"] == pytest.approx(40.0 * C / 1e-3 / 1e9)
+    assert k["get_conservative"]["algorithmic_gbs"] == pytest.approx(32.0 * C * B / 2e-3 / 1e9)
+    assert k["set_conservative"]["algorithmic_gbs"] == pytest.approx((16.0 * C + 32.0 * C * B) / 3e-3 / 1e9)
+    assert k["set_conservative"]["hbm_frac"] == pytest.approx(k["set_conservative"]["algorithmic_gbs"] / d["hbm_peak_gbs"])
+    assert d["status_flags"] == 0 and d["workload"].endswith("strang")
