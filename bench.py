@@ -741,27 +741,30 @@ def run_ours(args):
             del vps
             torch.cuda.synchronize()
 
-    if args.variants and args.transfer and ws == 1:
-        variants.append(_bench_transfer(args, stream, dev, value))
+    def extra(name, fn):
+        # a failed extra line must not cost the bench its result: it is recorded instead
+        try:
+            variants.append(fn())
+        except Exception as e:
+            variants.append({"workload": name, "error": repr(e)[:300]})
+            torch.cuda.synchronize()
 
-    if args.variants and args.batched and ws == 1:
+    def batched():
         bv = _bench_batched(args, stream, dev, n_instances=args.batch_instances)
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
         bv["roofline"] = _mixed_roofline(bv["value"], batched=True)
-        variants.append(bv)
+        return bv
 
+    if args.variants and args.transfer and ws == 1:
+        extra("transfer", lambda: _bench_transfer(args, stream, dev, value))
+    if args.variants and args.batched and ws == 1:
+        extra("batched", batched)
     if args.variants and args.el and ws == 1:
-        variants.append(_bench_el(args, stream, dev))
-
+        extra("el", lambda: _bench_el(args, stream, dev))
     if args.variants and args.closure and ws == 1:
-        try:
-            variants.append(_bench_closure(args, stream, dev))
-        except Exception as e:  # a failed extra line must not cost the bench its result
-            variants.append({"workload": "strang closure", "error": repr(e)[:300]})
-            torch.cuda.synchronize()
-
+        extra("strang closure", lambda: _bench_closure(args, stream, dev))
     if args.variants and args.serving and ws == 1:
-        variants.append(_bench_serving(args))
+        extra("serving", lambda: _bench_serving(args))
 
     fma = None
     if args.peak_probe:
