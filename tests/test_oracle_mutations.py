@@ -58,6 +58,11 @@ MUTATIONS = [
      "z[k] = y1[k];"),
     ("error norm without the Rdot floor", "if (vscale < v_floor)", "if (0)"),
     ("<R^3 p_bw> with R^2", "M3P += w[b] * r3 * p_bw;", "M3P += w[b] * r * r * p_bw;"),
+    ("carried proposal always h_try * fac", "h = (clipped && fac >= 1.0) ? h : h_try * fac;",
+     "h = h_try * fac;"),
+    ("unclipped proposal kept whatever fac", "h = (clipped && fac >= 1.0) ? h : h_try * fac;",
+     "h = clipped ? h : h_try * fac;"),
+    ("no forced 0.2 after a non-positive stage", "if (!positive && fac > 0.2)", "if (0)"),
 ]
 
 # Mistakes in the non-polytropic contents, caught by tests/test_oracle_transfer.py.

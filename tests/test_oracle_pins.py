@@ -205,6 +205,56 @@ def test_adaptive_driver_step_limit_flag_keeps_last_accepted_state():
     assert np.all(np.isfinite(y))
 
 
+def _taylor3(x):
+    return 1.0 + x + x * x / 2.0 + x ** 3 / 6.0
+
+
+def test_controller_carries_unclipped_proposal_when_last_trial_was_clipped():
+    """Sec. 3 leaves the controller open; the reading keeps the unclipped proposal when the
+    last trial was shortened to land on dt and the error would let the step grow (fac >= 1),
+    and otherwise carries h_try * fac.  On y' = 0 the error is exactly zero, so fac = 5."""
+    zero = np.zeros((2, 2))
+    # One trial of exactly dt: not clipped, so the carried proposal is dt * 5.
+    y = np.array([1.0, 0.0])
+    h = np.zeros(1, dtype=np.float32)
+    assert oracle.linear_advance(zero, y, h, 1.0, 1e-4, 1e-3) == (0, 1)
+    assert h[0] == 5.0
+    # Carried 3/8: the first trial grows the proposal to 15/8; the second is clipped to the
+    # 5/8 left and fac = 5 >= 1, so 15/8 is carried (h_try * fac would give 25/8).
+    y = np.array([1.0, 0.0])
+    h = np.array([0.375], dtype=np.float32)
+    assert oracle.linear_advance(zero, y, h, 1.0, 1e-4, 1e-3) == (0, 2)
+    assert h[0] == 1.875
+    # y' = -y from a carried 1/4 at tol 0.18: trial 1 (x = -1/4) grows h to 1/4 * fac1 > 3/4,
+    # so trial 2 is clipped to 3/4; its error lies between 0.729 tol and tol, so it is
+    # accepted with fac < 1 and the carried proposal is 3/4 * fac2, not the unclipped h.
+    A = np.array([[-1.0, 0.0], [0.0, 0.0]])
+    tol = 0.18
+    err = [abs(x ** 3 / 6.0) / abs(_taylor3(x)) for x in (-0.25, -0.75)]
+    fac = [0.9 * (tol / e) ** (1.0 / 3.0) for e in err]
+    assert 0.25 * fac[0] > 0.75 and 0.729 * tol < err[1] <= tol and fac[1] < 1.0
+    y = np.array([1.0, 0.0])
+    h = np.array([0.25], dtype=np.float32)
+    assert oracle.linear_advance(A, y, h, 1.0, tol, 1e-3) == (0, 2)
+    assert h[0] == pytest.approx(0.75 * fac[1], rel=1e-7)
+    assert y[0] == pytest.approx(_taylor3(-0.25) * _taylor3(-0.75), rel=1e-14)
+
+
+def test_controller_retries_at_one_fifth_after_a_non_positive_stage():
+    """A trial whose stage radius goes non-positive is rejected and retried at 0.2 h_try,
+    whatever its error norm allows.  On R' = -R with dt = 1.5 and tol = 100 the Euler stage
+    1 - h goes negative for h > 1 while the error (9 at h = 1.5) would allow fac = 2; the
+    sequence by hand: reject 1.5 -> accept 0.3 (fac 5) -> reject the clipped 1.2 -> accept
+    0.24 (fac 5) -> accept the clipped 0.96 (fac 5 >= 1, so the unclipped 1.2 is carried)."""
+    A = np.array([[-1.0, 0.0], [0.0, 0.0]])
+    assert 0.9 * (100.0 / 9.0) ** (1.0 / 3.0) > 0.2      # the error alone would not force 0.2
+    y = np.array([1.0, 0.0])
+    h = np.zeros(1, dtype=np.float32)
+    assert oracle.linear_advance(A, y, h, 1.5, 100.0, 1e-3, max_attempts=50) == (0, 5)
+    assert y[0] == pytest.approx(_taylor3(-0.3) * _taylor3(-0.24) * _taylor3(-0.96), rel=1e-14)
+    assert h[0] == pytest.approx(1.2, rel=1e-7)
+
+
 # ----------------------------------------------------------------------------
 # Whole-path pins: fixed point, linear frequency, Rayleigh collapse, order
 # ----------------------------------------------------------------------------
