@@ -105,6 +105,42 @@ def _mixed_roofline(bin_steps_per_s, batched=False):
             "fma_pipe_active_ncu": fma, "counters": prof, "counters_build": build}
 
 
+# FP32 and FP64 flops (FFMA/DFMA = 2, FADD/FMUL/DADD/DMUL = 1) of the mixed step kernel per FP32
+# trial, per FP64 (collapse) trial and per bin-step outside the trial loop: least-squares fit of
+# ncu's smsp__sass_thread_inst_executed_op_{f,d}{fma,add,mul}_pred_on over traced launches
+# (profiles/step_kernel_mixed.md).  None until that capture exists for the current build.
+MIXED_FLOPS = None   # {"fp32_per_trial": .., "fp64_per_trial": .., "fp32_per_binstep": .., "fp64_per_binstep": ..}
+BATCH_FLOPS = None   # the same for batch_kernel<MIXED> (profiles/batch_kernel_mixed_16inst.md)
+
+
+def _fp64_peak_derived():
+    return NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * SM_MAX_MHZ * 1e6
+
+
+def _fp32_peak_derived():
+    return NOMINAL_FP32_FLOPS_PER_CLK_PER_SM * N_SM * SM_MAX_MHZ * 1e6
+
+
+def _mixed_compute_roofline(bin_steps_per_s, trials_per_bin_step, fp64_fraction, batched=False):
+    """A mixed kernel against both compute ceilings: its FP32 and FP64 flops per second (the
+    ncu-fitted flops per trial and per bin-step applied to the counted trials) over the derived
+    FP32 and FP64 peaks, beside the HBM and issue figures of _mixed_roofline."""
+    roof = _mixed_roofline(bin_steps_per_s, batched=batched)
+    fit = BATCH_FLOPS if batched else MIXED_FLOPS
+    if not fit:
+        roof.update({"fp32_tflops": None, "fp64_tflops": None, "fp32_frac": None, "fp64_frac": None})
+        return roof
+    t32 = trials_per_bin_step * (1.0 - fp64_fraction)
+    t64 = trials_per_bin_step * fp64_fraction
+    f32 = bin_steps_per_s * (t32 * fit["fp32_per_trial"] + fit["fp32_per_binstep"])
+    f64 = bin_steps_per_s * (t32 * fit["fp64_per_trial"] + t64 * fit["fp64_per_fp64_trial"]
+                             + fit["fp64_per_binstep"])
+    roof.update({"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12,
+                 "fp32_frac": f32 / _fp32_peak_derived(), "fp64_frac": f64 / _fp64_peak_derived(),
+                 "flops_fit": fit.get("source")})
+    return roof
+
+
 def make_workload(name, rank, edge=0):
     if name == "grid128":
         return workloads.config_grid128(seed=pdist.rank_seed(2, rank), edge=edge or 128)
@@ -499,6 +535,183 @@ def _bench_serving(args, n_requests=16, rate=200.0):
                        "bins_per_grab": tune["bins_per_grab"], "autotuned": True}}
 
 
+def _bench_serving_sweep(args, rates, n_requests):
+    """The seeded Poisson request stream at several offered rates (n_requests each), served on the
+    wall clock: per rate the p50/p99 latency, the throughput, the GPU's busy share and the mean
+    concurrency, to place the knee between idle and saturated serving."""
+    from paper_2511_21031_gb300 import autotune
+    from paper_2511_21031_gb300.serve import ServingEngine
+    out = []
+    tune = None
+    for rate in rates:
+        reqs = workloads.request_stream(n=n_requests, rate=rate)
+        if tune is None:
+            tune = autotune.tune_batch([r.work for r in reqs], precision="mixed", sample=8)
+        eng = ServingEngine(capacity_bins=2_000_000_000, max_slots=256,
+                            launch=(tune["block_warps"], tune["ctas_per_sm"], tune["bins_per_grab"]))
+        rep = eng.run(reqs, clock="wall")
+        eng.close()
+        out.append({"rate": rate, "requests": n_requests, "completed": rep["completed"],
+                    "latency_s": rep["latency_s"], "throughput": rep["throughput_bin_steps_per_s"],
+                    "gpu_busy": rep["gpu_busy_s"] / rep["elapsed_s"], "concurrency": rep["concurrency"],
+                    "elapsed_s": rep["elapsed_s"], "flags": rep["flags"]})
+    return {"workload": f"serving sweep, {n_requests} requests per rate", "label": "serving sweep mixed",
+            "precision": "mixed", "unit": "bin-steps/s", "rates": out,
+            "launch": {"block_warps": tune["block_warps"], "ctas_per_sm": tune["ctas_per_sm"],
+                       "bins_per_grab": tune["bins_per_grab"], "autotuned": True}}
+
+
+def _bench_latency_small(args, stream, dev, block_warps=0):
+    """The 64-cell x Nb 21 workload (0.5 p0 at 100 kHz, 1000 flow steps of 1e-8 s, adaptive FP64)
+    call by call: the latency the host sees per call through pab_bubble_step (device buffers; the
+    call and a wait on its stream) and through pab_bubble_step_host (host buffers; the call copies
+    the pressure in and the moments out and waits), each over the whole 1000-step run from
+    equilibrium, with the kernel's own duration from CUDA events beside them."""
+    import torch
+
+    from paper_2511_21031_gb300 import pab
+    wl = workloads.config_small()
+    out = {"workload": wl.name, "label": "per-call latency, 64 cells x Nb 21 (FP64)", "precision": "fp64",
+           "unit": "bin-steps/s", "steps": wl.n_steps}
+    ph = [torch.as_tensor(wl.pressure_step(n)).pin_memory() for n in range(wl.n_steps)]
+    pd = [x.to(dev) for x in ph]
+    mh = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64).pin_memory()
+    md = torch.empty((pab.N_MOMENTS, wl.n_cells), dtype=torch.float64, device=dev)
+    for api in ("pab_bubble_step", "pab_bubble_step_host"):
+        sol = pab.Solver(wl.n_cells, wl.n_bins, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K,
+                         alpha0=wl.alpha0)
+        if block_warps:
+            sol.set_block_warps(block_warps)
+        # a few calls to load the kernels and warm the driver, then a fresh state
+        start = sol.get_state(stream=stream)
+        for n in range(5):
+            sol.step(pd[n], wl.dt, moments=md, stream=stream)
+        sol.set_state(*start, stream=stream)
+        torch.cuda.synchronize()
+        host_ms, kern_ms = [], []
+        evs = []
+        for n in range(wl.n_steps):
+            t0 = time.perf_counter()
+            if api == "pab_bubble_step":
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sol.step(pd[n], wl.dt, moments=md, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                evs.append((e0, e1))
+            else:
+                sol.step_host(ph[n], wl.dt, moments_host=mh, stream=stream)
+            host_ms.append((time.perf_counter() - t0) * 1e3)
+        kern_ms = [a.elapsed_time(b) for a, b in evs]
+        st = sol.status(stream=stream)
+        sol.close()
+        bs = wl.n_cells * wl.n_bins * wl.n_steps
+        out[api] = {"p50_ms": float(np.percentile(host_ms, 50)), "p99_ms": float(np.percentile(host_ms, 99)),
+                    "mean_ms": float(np.mean(host_ms)), "value": bs / (sum(host_ms) * 1e-3),
+                    "trials_per_bin_step": st["n_attempts"] / bs, "status_flags": st["flags"]}
+        if kern_ms:
+            out[api]["kernel_p50_ms"] = float(np.percentile(kern_ms, 50))
+            out[api]["kernel_p99_ms"] = float(np.percentile(kern_ms, 99))
+    out["value"] = out["pab_bubble_step"]["value"]
+    out["block_warps"] = block_warps or "default"
+    return out
+
+
+def _bench_collapse(args, stream, dev, precision, sample_cells=64):
+    """The collapse-stress workload (64^3 cells x Nb 31, s = 0.5; plane wave of 1.2 p0 at 21.4 kHz
+    with 5 % seeded phase jitter; 5e-9 s flow steps) over one forcing period (10,000 steps) from
+    equilibrium: every cell is driven into tension, grows and collapses once, so the window holds
+    the regime of the paper's Ohl-type case (Sec. 5).  Every step launch is timed with CUDA events
+    on its stream; the pressure fields are made on the device between chunks of steps, outside the
+    events.  The errors of every output against the FP64 oracle come from seeded sample cells run
+    through the oracle after the timed steps, on the pressures the GPU used."""
+    import torch
+
+    from paper_2511_21031_gb300 import pab
+    wl = workloads.config_collapse(edge=args.collapse_edge, n_steps=args.collapse_steps)
+    C, B = wl.n_cells, wl.n_bins
+    cells = np.sort(np.random.default_rng(13).choice(C, min(sample_cells, C), replace=False))
+    cells_d = torch.as_tensor(cells, device=dev)
+    sol = pab.Solver(C, B, precision=precision, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K,
+                     alpha0=wl.alpha0)
+    mom = torch.empty((pab.N_MOMENTS, C), dtype=torch.float64, device=dev)
+    p_sample = []
+    launch_ms = []
+    n_att = n64 = 0
+    flags = 0
+    chunk = 250
+    torch.cuda.synchronize()
+    for c0 in range(0, wl.n_steps, chunk):
+        n1 = min(wl.n_steps, c0 + chunk)
+        with torch.cuda.stream(stream):
+            ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(c0, n1)]
+            p_sample.append(torch.stack([p.index_select(0, cells_d) for p in ps]).cpu())
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in ps]
+        with torch.cuda.stream(stream):
+            for p, (e0, e1) in zip(ps, evs):
+                e0.record(stream)
+                sol.step(p, wl.dt, moments=mom, stream=stream)
+                e1.record(stream)
+        st = sol.status(stream=stream)
+        torch.cuda.synchronize()
+        launch_ms += [a.elapsed_time(b) for a, b in evs]
+        n_att += st["n_attempts"]
+        n64 += st["n_fp64"]
+        flags |= st["flags"]
+        del ps
+    R, V, _ = sol.get_state(stream=stream)
+    torch.cuda.synchronize()
+    gR = R[:, cells_d].cpu().numpy()
+    gV = V[:, cells_d].cpu().numpy()
+    gm = mom[:, cells_d].cpu().numpy()
+    w = np.array(sol.w)
+    sol.close()
+    del R, V, mom
+    torch.cuda.synchronize()
+    bs = C * B * wl.n_steps
+    total_ms = float(sum(launch_ms))
+    out = {"workload": wl.name + ("_mixed" if precision == "mixed" else "_fp64"),
+           "label": f"collapse stress, one period ({precision})", "precision": precision,
+           "cells": C, "bins": B, "steps": wl.n_steps, "value": bs / (total_ms * 1e-3),
+           "unit": "bin-steps/s", "ms_per_step": total_ms / wl.n_steps,
+           "latency_ms": {"p50": float(np.percentile(launch_ms, 50)),
+                          "p99": float(np.percentile(launch_ms, 99))},
+           "trials_per_bin_step": n_att / bs, "fp64_trial_fraction": n64 / max(1, n_att),
+           "status_flags": flags}
+    if precision == "fp64":
+        flops = bs * (out["trials_per_bin_step"] * FP64_FLOPS_PER_TRIAL + FP64_FLOPS_PER_BINSTEP)
+        out["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": flops / (total_ms * 1e-3) / 1e12,
+                           "peak": _fp64_peak_derived() / 1e12, "unit": "TFLOP/s",
+                           "frac": flops / (total_ms * 1e-3) / _fp64_peak_derived()}
+    else:
+        out["roofline"] = _mixed_compute_roofline(out["value"], out["trials_per_bin_step"],
+                                                  out["fp64_trial_fraction"])
+    # the oracle on the sample cells, from equilibrium on the same pressures (outside any timing)
+    try:
+        import oracle
+        sub = wl.subset(cells)
+        P = oracle.Params(**sub.fluid)
+        R0o, wo = oracle.bins(B, sub.R0ref, sub.s, sub.span_K)
+        Ro = np.repeat(R0o[:, None], len(cells), axis=1).copy()
+        Vo = np.zeros_like(Ro)
+        ho = np.zeros(Ro.shape, dtype=np.float32)
+        pall = torch.cat(p_sample).numpy()
+        for n in range(wl.n_steps):
+            oracle.step(P, R0o, np.ascontiguousarray(pall[n]), wl.dt, Ro, Vo, ho)
+        nb = np.full(len(cells), oracle.equilibrium_nb(sub.alpha0, R0o, wo))
+        om = oracle.moments(P, R0o, wo, nb, Ro, Vo)
+        v_floor = 1e-3 * math.sqrt(sub.fluid["p0"] / sub.fluid["rho"])
+        err = _mixed_errors(gm, om, gR, gV, Ro, Vo, wo, v_floor)
+        err["sample"] = f"{len(cells)} seeded cells x {B} bins x {wl.n_steps} steps"
+        err["min_R_over_R0"] = float(np.min(Ro / R0o[:, None]))
+        out["error_vs_oracle"] = err
+    except Exception as e:   # the line stands without its error sample
+        out["error_vs_oracle"] = {"error": repr(e)[:200]}
+    return out
+
+
 # Algorithmic HBM bytes of the carrier-coupling kernels (FP64): per cell and per (bin, cell).
 CLOSURE_BYTES = {
     # alpha, <R^3 p_bw>/<R^3>, <R^3 Rdot^2>/<R^3> and p_l in, p out
@@ -624,6 +837,48 @@ def _bench_el(args, stream, dev):
             "status_flags": st["flags"]}
 
 
+def _summary(line):
+    """The line's headline figures in a few hundred characters (3 significant digits): the
+    default line, the end-to-end figure, the FMA probe and each extra line's value with its
+    distinguishing figures."""
+    def g(x):
+        return float(f"{x:.3g}") if isinstance(x, (int, float)) and x == x else x
+    out = {"value": g(line["value"]), "frac": g(line["roofline"].get("frac")),
+           "frac_meas": g(line["roofline"].get("frac_of_measured")), "e2e": g(line["e2e"]["value"])}
+    fma = line.get("fma_probe") or {}
+    if "fp64_tflops" in fma:
+        out["fma_tflops"] = [g(fma["fp64_tflops"]), g(fma["fp32_tflops"])]
+    for v in line.get("variants", []):
+        key = v.get("workload", "?")
+        if "error" in v:
+            out[key] = "error"
+            continue
+        e = {"v": g(v.get("value"))}
+        if "trials_per_bin_step" in v:
+            e["tr"] = g(v["trials_per_bin_step"])
+        if v.get("fp64_trial_fraction"):
+            e["f64"] = g(v["fp64_trial_fraction"])
+        r = v.get("roofline") or {}
+        for k_src, k_dst in (("frac", "frac"), ("fp64_frac", "f64frac"), ("fp32_frac", "f32frac")):
+            if r.get(k_src) is not None:
+                e[k_dst] = g(r[k_src])
+        eo = v.get("error_vs_oracle") or v.get("error_vs_fp64_kernel") or {}
+        if "alpha" in eo:
+            e["err_a"] = g(eo["alpha"])
+            e["err_R"] = g(eo["R"])
+        if "pab_bubble_step" in v:
+            e = {"dev_p50_p99_ms": [g(v["pab_bubble_step"]["p50_ms"]), g(v["pab_bubble_step"]["p99_ms"])],
+                 "host_p50_p99_ms": [g(v["pab_bubble_step_host"]["p50_ms"]),
+                                     g(v["pab_bubble_step_host"]["p99_ms"])]}
+        if "latency_s" in v:
+            e["p50_p99_s"] = [g(v["latency_s"]["p50"]), g(v["latency_s"]["p99"])]
+        if "rates" in v:
+            e = {str(x["rate"]): [g(x["latency_s"]["p50"]), g(x["latency_s"]["p99"]), g(x["gpu_busy"])]
+                 for x in v["rates"]}
+        out[key] = e
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -726,7 +981,8 @@ def run_ours(args):
             r = _time_steps(vs, vwl, vps, args, stream)
             vbs = vwl.n_cells * vwl.n_bins * args.steps
             variants.append({
-                "workload": vwl.name, "label": name, "precision": "mixed",
+                "workload": vwl.name.replace("_fp64", "_mixed").replace("_mixed_mixed", "_mixed"),
+                "label": name, "precision": "mixed",
                 "value": vbs / (r["ms_total"] * 1e-3), "unit": "bin-steps/s",
                 "ms_per_step": r["ms_total"] / args.steps,
                 "latency_ms": {"p50": float(np.percentile(r["launch_ms"], 50)),
@@ -735,7 +991,9 @@ def run_ours(args):
                 "fp64_trial_fraction": r["status"]["n_fp64"] / max(1, r["status"]["n_attempts"]),
                 "speedup_vs_fp64_grid128": (vbs / (r["ms_total"] * 1e-3)) / value,
                 "error_vs_fp64_kernel": _mixed_error_sample(vwl, min(total, 40)),
-                "roofline": _mixed_roofline(vbs / (r["ms_total"] * 1e-3)),
+                "roofline": _mixed_compute_roofline(
+                    vbs / (r["ms_total"] * 1e-3), r["status"]["n_attempts"] / vbs,
+                    r["status"]["n_fp64"] / max(1, r["status"]["n_attempts"])),
             })
             vs.close()
             del vps
@@ -746,13 +1004,18 @@ def run_ours(args):
         try:
             variants.append(fn())
         except Exception as e:
-            variants.append({"workload": name, "error": repr(e)[:300]})
-            torch.cuda.synchronize()
+            entry = {"workload": name, "error": repr(e)[:300]}
+            try:
+                torch.cuda.synchronize()
+            except Exception as e2:    # a sticky CUDA error: recorded, the line still prints
+                entry["sync_error"] = repr(e2)[:300]
+            variants.append(entry)
 
     def batched():
         bv = _bench_batched(args, stream, dev, n_instances=args.batch_instances)
         bv["speedup_vs_fp64_grid128"] = bv["value"] / value
-        bv["roofline"] = _mixed_roofline(bv["value"], batched=True)
+        bv["roofline"] = _mixed_compute_roofline(bv["value"], bv["trials_per_bin_step"],
+                                                 bv["fp64_trial_fraction"], batched=True)
         return bv
 
     if args.variants and args.transfer and ws == 1:
@@ -765,15 +1028,43 @@ def run_ours(args):
         extra("strang closure", lambda: _bench_closure(args, stream, dev))
     if args.variants and args.serving and ws == 1:
         extra("serving", lambda: _bench_serving(args))
+    if args.variants and args.collapse and ws == 1:
+        extra("collapse fp64", lambda: _bench_collapse(args, stream, dev, "fp64"))
+        extra("collapse mixed", lambda: _bench_collapse(args, stream, dev, "mixed"))
+    if args.variants and args.latency and ws == 1:
+        extra("latency small", lambda: _bench_latency_small(args, stream, dev))
+    if args.serving_sweep and ws == 1:
+        extra("serving sweep", lambda: _bench_serving_sweep(args, args.sweep_rates, args.sweep_requests))
 
     fma = None
     if args.peak_probe:
-        sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
-        ms, n = pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 2000, sink.data_ptr(), int(stream.cuda_stream))
-        ms, n = pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 2000, sink.data_ptr(), int(stream.cuda_stream))
-        ms32, n32 = pab.pab_peak_fma(pab.PAB_MIXED, N_SM * 16, 256, 20000, sink.data_ptr(),
-                                     int(stream.cuda_stream))
-        fma = {"fp64_tflops": 2 * n / (ms * 1e-3) / 1e12, "fp32_tflops": 2 * n32 / (ms32 * 1e-3) / 1e12}
+        # dependent-FMA throughput on every SM, FP64 and FP32 (measured beside the derived peaks)
+        try:
+            sink = torch.empty(N_SM * 16 * 256, dtype=torch.float64, device=dev)
+            sp = int(stream.cuda_stream)
+            pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 200, sink.data_ptr(), sp)   # warm
+            ms, n = pab.pab_peak_fma(pab.PAB_FP64, N_SM * 16, 256, 2000, sink.data_ptr(), sp)
+            ms32, n32 = pab.pab_peak_fma(pab.PAB_MIXED, N_SM * 16, 256, 20000, sink.data_ptr(), sp)
+            fma = {"fp64_tflops": 2 * n / (ms * 1e-3) / 1e12, "fp32_tflops": 2 * n32 / (ms32 * 1e-3) / 1e12,
+                   "fp64_derived_tflops": _fp64_peak_derived() / 1e12,
+                   "fp32_derived_tflops": _fp32_peak_derived() / 1e12,
+                   "how": "pab_peak_fma: 8 dependent FMA chains per thread, 2432 CTAs of 256 threads"}
+            del sink
+        except Exception as e:
+            fma = {"error": repr(e)[:200]}
+    if fma and "fp64_tflops" in fma and roof.get("achieved"):
+        roof["peak_measured"] = fma["fp64_tflops"]
+        roof["frac_of_measured"] = roof["achieved"] / fma["fp64_tflops"]
+        roof["peak_measured_source"] = "pab_peak_fma in this run (fma_probe)"
+    for v in variants:
+        r = v.get("roofline") if isinstance(v, dict) else None
+        if not (r and fma and "fp64_tflops" in fma):
+            continue
+        if r.get("pipe") == "fp64" and r.get("achieved"):
+            r["frac_of_measured"] = r["achieved"] / fma["fp64_tflops"]
+        if r.get("fp64_tflops") is not None:
+            r["fp64_frac_of_measured"] = r["fp64_tflops"] / fma["fp64_tflops"]
+            r["fp32_frac_of_measured"] = r["fp32_tflops"] / fma["fp32_tflops"]
 
     if rank == 0:
         line = {
@@ -804,6 +1095,7 @@ def run_ours(args):
             line["variants"] = variants
         if fma:
             line["fma_probe"] = fma
+        line["summary"] = _summary(line)   # last, so that a record keeping the line's tail keeps it
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -821,7 +1113,18 @@ def main():
     ap.add_argument("--block-warps", type=int, default=0)
     ap.add_argument("--edge", type=int, default=0, help="grid edge override (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--peak-probe", action="store_true")
+    ap.add_argument("--no-peak-probe", dest="peak_probe", action="store_false",
+                    help="skip the FP64/FP32 FMA-throughput probe")
+    ap.add_argument("--no-collapse", dest="collapse", action="store_false",
+                    help="skip the collapse-stress lines (64^3 x 31, 21.4 kHz, one period)")
+    ap.add_argument("--collapse-edge", type=int, default=64)
+    ap.add_argument("--collapse-steps", type=int, default=10000)
+    ap.add_argument("--no-latency", dest="latency", action="store_false",
+                    help="skip the per-call latency line of the 64-cell workload")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="serve the request stream at several rates (minutes of wall time)")
+    ap.add_argument("--sweep-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
+    ap.add_argument("--sweep-requests", type=int, default=64)
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision and batched lines")
     ap.add_argument("--no-batched", dest="batched", action="store_false",

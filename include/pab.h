@@ -257,10 +257,13 @@ pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
  * shares the block, so calls that overlap on the GPU (other streams, other
  * threads) race on it and may report each other's counts; the state and the
  * moments, which live in caller buffers, are not affected.
- * The first call on a device looks up the block's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.
- * Errors: PAB_EINVAL (bad cfg, NULL pointers, dt <= 0 or non-finite),
+ * The first call in each CUDA context (the device's primary context, normally)
+ * looks up the block's device address with that context current
+ * (cudaGetSymbolAddress) and caches it under the context's id; a context made
+ * anew, after cudaDeviceReset for instance, looks it up again on its first
+ * call.  Make the first call in a context before any stream capture.
+ * Errors: PAB_EINVAL (bad cfg, explicit weights summing to zero, NULL
+ * pointers, dt <= 0 or non-finite),
  * PAB_ECUDA (symbol lookup or launch failure).
  */
 #define PAB_NOALLOC_SCRATCH_BYTES 256

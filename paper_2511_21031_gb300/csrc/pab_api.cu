@@ -2,6 +2,7 @@
 // the lognormal bin table, device state ownership and the stream-ordered
 // entry points.  No compute happens here; every step of the path runs in the
 // kernels of pab_kernels.cu.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -800,35 +801,79 @@ pab_status pab_stiffened_gas(int64_t n, const double *rho_l_dev, const double *e
 // Allocation-free entry point.  Its only scratch, the status block of the
 // step kernel, lives in this static device array instead of a handle's
 // cudaMalloc'ed memory.  Host code cannot use the array's name as a device
-// address, so each device's address is looked up once, with that device
-// current, and cached.
+// address, so its address is looked up (cudaGetSymbolAddress) once per CUDA
+// context, with that context current, and cached under the context's id: a
+// context created anew (after cudaDeviceReset, say) reloads the module, and its
+// first call looks the address up again instead of reusing a stale one.
 // ---------------------------------------------------------------------------
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PAB_NOALLOC_SCRATCH_BYTES];
 static_assert(sizeof(pab::Counters) <= PAB_NOALLOC_SCRATCH_BYTES, "status block exceeds the scratch");
 
-constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocCacheSlots = 64;
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    void *addr;
+};
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kNoallocMaxDevices] = {};
+NoallocSlot g_noalloc_cache[kNoallocCacheSlots] = {};
+int g_noalloc_next = 0;
+CUresult (*g_cu_ctx_get_current)(CUcontext *) = nullptr;
+CUresult (*g_cu_ctx_get_id)(CUcontext, unsigned long long *) = nullptr;
+
+// The current context's id, through the driver entry points the runtime hands out (the
+// library links no driver library of its own).  A thread with no current context yet gets
+// the device's primary context from the runtime first (the symbol lookup does that).
+cudaError_t current_context_id(unsigned long long *id)
+{
+    if (!g_cu_ctx_get_current || !g_cu_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                         cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess)
+            return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        g_cu_ctx_get_current = (CUresult(*)(CUcontext *))f1;
+        g_cu_ctx_get_id = (CUresult(*)(CUcontext, unsigned long long *))f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_cu_ctx_get_current(&ctx) != CUDA_SUCCESS)
+        return cudaErrorDeviceUninitialized;
+    if (!ctx) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return e;
+        if (g_cu_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx)
+            return cudaErrorDeviceUninitialized;
+    }
+    return g_cu_ctx_get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 cudaError_t noalloc_scratch(pab::Counters **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kNoallocMaxDevices)
-        return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = (pab::Counters *)g_noalloc_addr[dev];
+    for (int i = 0; i < kNoallocCacheSlots; ++i)
+        if (g_noalloc_cache[i].addr && g_noalloc_cache[i].ctx_id == id) {
+            *out = (pab::Counters *)g_noalloc_cache[i].addr;
+            return cudaSuccess;
+        }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+        return e;
+    g_noalloc_cache[g_noalloc_next] = NoallocSlot{id, p};
+    g_noalloc_next = (g_noalloc_next + 1) % kNoallocCacheSlots;
+    *out = (pab::Counters *)p;
     return cudaSuccess;
 }
 
@@ -855,12 +900,8 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
         return PAB_EINVAL;
     }
     double R0[PAB_MAX_BINS], w[PAB_MAX_BINS];
-    if (cfg->R0_host) {
-        for (int i = 0; i < cfg->n_bins; ++i) {
-            R0[i] = cfg->R0_host[i];
-            w[i] = cfg->w_host[i];
-        }
-    } else if (!lognormal_table(cfg->n_bins, cfg->R0ref, cfg->s_lognormal, cfg->span_K, R0, w)) {
+    if (!pab::bin_table(cfg, R0, w)) {
+        fprintf(stderr, "pab_bubble_step_noalloc: invalid bin table (explicit weights summing to zero?)\n");
         return PAB_EINVAL;
     }
     pab::StepConst K;

@@ -189,3 +189,40 @@ def test_closure_line_times_each_kernel_group(monkeypatch):
     assert k["set_conservative"]["algorithmic_gbs"] == pytest.approx((16.0 * C + 32.0 * C * B) / 3e-3 / 1e9)
     assert k["set_conservative"]["hbm_frac"] == pytest.approx(k["set_conservative"]["algorithmic_gbs"] / d["hbm_peak_gbs"])
     assert d["status_flags"] == 0 and d["workload"].endswith("strang")
+
+
+def test_mixed_compute_roofline_applies_the_flop_fit(monkeypatch):
+    """FP32 and FP64 flops per second from the fitted flops per trial and per bin-step: FP32
+    trials carry the FP32 and the FP64 bookkeeping of a trial, collapse trials the FP64 trial's."""
+    bench = _bench()
+    fit = {"fp32_per_trial": 100.0, "fp64_per_trial": 20.0, "fp64_per_fp64_trial": 130.0,
+           "fp32_per_binstep": 10.0, "fp64_per_binstep": 5.0, "source": "test"}
+    monkeypatch.setattr(bench, "MIXED_FLOPS", fit)
+    d = bench._mixed_compute_roofline(1e10, 1.5, 0.1)
+    t32, t64 = 1.5 * 0.9, 1.5 * 0.1
+    assert d["fp32_tflops"] == pytest.approx(1e10 * (t32 * 100.0 + 10.0) / 1e12)
+    assert d["fp64_tflops"] == pytest.approx(1e10 * (t32 * 20.0 + t64 * 130.0 + 5.0) / 1e12)
+    assert d["fp32_frac"] == pytest.approx(d["fp32_tflops"] * 1e12 / bench._fp32_peak_derived())
+    assert d["fp64_frac"] == pytest.approx(d["fp64_tflops"] * 1e12 / bench._fp64_peak_derived())
+    monkeypatch.setattr(bench, "MIXED_FLOPS", None)
+    assert bench._mixed_compute_roofline(1e10, 1.5, 0.1)["fp64_frac"] is None
+
+
+def test_summary_keeps_every_line_within_the_recorded_tail():
+    """The summary closes the JSON line and names every extra line's value, so a record that
+    keeps only the line's last 1500 characters keeps the headline figures of every line."""
+    bench = _bench()
+    lat = {"p50_ms": 0.05, "p99_ms": 0.07}
+    line = {"value": 4.2e9, "roofline": {"frac": 0.65, "frac_of_measured": 0.77},
+            "e2e": {"value": 4.1e9}, "fma_probe": {"fp64_tflops": 1.05, "fp32_tflops": 70.1},
+            "variants": [
+                {"workload": f"w{i}", "value": 1.23456e9 * (i + 1), "trials_per_bin_step": 1.05,
+                 "fp64_trial_fraction": 0.011, "roofline": {"fp64_frac": 0.5, "fp32_frac": 0.05},
+                 "error_vs_oracle": {"alpha": 1e-7, "R": 3e-5}} for i in range(8)]
+            + [{"workload": "lat", "value": 1.0, "pab_bubble_step": lat, "pab_bubble_step_host": lat},
+               {"workload": "bad", "error": "RuntimeError('x')"}]}
+    s = bench._summary(line)
+    assert s["value"] == 4.2e9 and s["frac_meas"] == 0.77 and s["fma_tflops"] == [1.05, 70.1]
+    assert s["w3"]["v"] == 4.94e9 and s["w0"]["f64"] == 0.011 and s["w0"]["err_a"] == 1e-7
+    assert s["lat"]["dev_p50_p99_ms"] == [0.05, 0.07] and s["bad"] == "error"
+    assert len(json.dumps({"summary": s})) < 1500

@@ -63,7 +63,13 @@ def test_mixed_collapse_uses_fp64_fallback_and_stays_close():
     assert st["n_fp64"] > 0
     r = o["R"] / o["R0"][:, None]
     assert r.min() < 0.3 and np.abs(o["V"]).max() > 75.0   # a collapse was reached
-    assert e["alpha"] <= 1e-3
+    assert e["alpha"] <= ALPHA_TOL
+    # the other outputs, a few times above their errors on this build (alpha 3.8e-7,
+    # R 3.1e-5, Rdot 2.9e-3, <R^2 Rdot> and S_alpha 7.7e-6, <R^3 p_bw>/<R^3> 2.3e-5,
+    # <R^3 Rdot^2>/<R^3> 1.2e-5): a weaker FP64 fallback fails here
+    assert e["R"] <= 1e-4 and e["Rdot"] <= 1e-2
+    assert e["R2Rdot"] <= 5e-5 and e["S_alpha"] <= 5e-5
+    assert e["pbw"] <= 1e-4 and e["rdot2"] <= 1e-4
 
 
 def test_compensated_alpha_sum_keeps_bins_below_half_an_ulp():

@@ -124,6 +124,30 @@ def test_full_size_grid128_sampled_cells():
     assert np.all(np.isfinite(g["moments"])) and np.all(g["moments"][1] > 0)
 
 
+def test_adaptive_parity_through_growth_and_collapse():
+    """The collapse-stress forcing (1.2 p0 plane wave at 21.4 kHz, 5e-9 s steps) on 64 cells
+    spread along the wave x 31 bins, through the first growth and collapse (11000 steps):
+    the regime of the paper's Ohl-type validation case (Sec. 5), with sub-step cascades and
+    rejections near collapse and the gas term far from equilibrium.  FP64
+    kernel against the oracle at the adaptive tolerance on R, Rdot and every moment, with at
+    most 0.1 % of bins taking a different number of trials."""
+    base = workloads.config_collapse(edge=8)
+    cells = np.arange(0, base.n_cells, 8)
+    wl = base.subset(cells)
+    n = 11000
+    g = run_gpu(wl, n)
+    o = run_oracle(wl, n)
+    x = o["R"] / o["R0"][:, None]
+    per_bin = o["attempts"] / n
+    print(f"collapse FP64 parity: R/R0 in [{x.min():.3f}, {x.max():.3f}], max |Rdot| "
+          f"{np.abs(o['V']).max():.1f} m/s, trials per bin-step mean {per_bin.mean():.3f} max "
+          f"{per_bin.max():.3f}, GPU trials {g['status']['n_attempts']} oracle {int(o['attempts'].sum())}")
+    assert g["status"]["flags"] == 0 and o["flags"] == 0
+    assert x.min() < 0.3 and np.abs(o["V"]).max() > 75.0      # bins are collapsing at the end
+    eR, eV, em = _check(g, o, wl.fluid, TOL_ADAPT)
+    print("errors: R", eR, "Rdot", eV, {pab.MOMENT_NAMES[k]: e for k, e in em.items()})
+
+
 def test_rayleigh_collapse_and_incompressible_limit_on_gpu():
     """Empty cavity, inviscid, c = inf: GPU equals the oracle (which is pinned to
     the Rayleigh collapse time)."""
