@@ -440,7 +440,13 @@ def _bench_batched(args, stream, dev, n_instances=512):
     from paper_2511_21031_gb300 import autotune
     from paper_2511_21031_gb300.batch import Batch
     insts = workloads.batched_instances(n=n_instances)
-    tune = autotune.tune_batch(insts, precision="mixed")
+    if getattr(args, "batch_launch", None):
+        # profiling aid: a fixed launch shape instead of the autotuner's
+        w_, c_, g_ = args.batch_launch
+        tune = {"block_warps": w_, "ctas_per_sm": c_, "bins_per_grab": g_, "cached": False,
+                "candidates": 0, "fixed": True}
+    else:
+        tune = autotune.tune_batch(insts, precision="mixed")
     bins = sum(w.n_cells * w.n_bins for w in insts)
     cells = sum(w.n_cells for w in insts)
     b = Batch(max_slots=len(insts), precision="mixed", capacity_bins=bins, max_bins=51)
@@ -635,6 +641,12 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
     cells_d = torch.as_tensor(cells, device=dev)
     sol = pab.Solver(C, B, precision=precision, s_lognormal=wl.s, R0ref=wl.R0ref, span_K=wl.span_K,
                      alpha0=wl.alpha0)
+    first = 0
+    if getattr(args, "collapse_load", None):
+        # profiling aid: continue from a state saved by --collapse-save (no oracle comparison)
+        ck = torch.load(args.collapse_load)
+        first = int(ck["steps"])
+        sol.set_state(ck["R"].to(dev), ck["V"].to(dev), ck["h"].to(dev), stream=stream)
     mom = torch.empty((pab.N_MOMENTS, C), dtype=torch.float64, device=dev)
     p_sample = []
     launch_ms = []
@@ -642,8 +654,8 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
     flags = 0
     chunk = 250
     torch.cuda.synchronize()
-    for c0 in range(0, wl.n_steps, chunk):
-        n1 = min(wl.n_steps, c0 + chunk)
+    for c0 in range(first, first + wl.n_steps, chunk):
+        n1 = min(first + wl.n_steps, c0 + chunk)
         with torch.cuda.stream(stream):
             ps = [wl.pressure_step(n, xp=torch, device=dev) for n in range(c0, n1)]
             p_sample.append(torch.stack([p.index_select(0, cells_d) for p in ps]).cpu())
@@ -661,8 +673,12 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
         n64 += st["n_fp64"]
         flags |= st["flags"]
         del ps
-    R, V, _ = sol.get_state(stream=stream)
+    R, V, hh = sol.get_state(stream=stream)
     torch.cuda.synchronize()
+    if getattr(args, "collapse_save", None):
+        torch.save({"R": R.cpu(), "V": V.cpu(), "h": hh.cpu(), "steps": first + wl.n_steps},
+                   args.collapse_save)
+    del hh
     gR = R[:, cells_d].cpu().numpy()
     gV = V[:, cells_d].cpu().numpy()
     gm = mom[:, cells_d].cpu().numpy()
@@ -690,6 +706,8 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
                                                   out["fp64_trial_fraction"])
     # the oracle on the sample cells, from equilibrium on the same pressures (outside any timing)
     try:
+        if first:
+            raise RuntimeError("continued from a saved state: no oracle comparison")
         import oracle
         sub = wl.subset(cells)
         P = oracle.Params(**sub.fluid)
@@ -1029,8 +1047,10 @@ def run_ours(args):
     if args.variants and args.serving and ws == 1:
         extra("serving", lambda: _bench_serving(args))
     if args.variants and args.collapse and ws == 1:
-        extra("collapse fp64", lambda: _bench_collapse(args, stream, dev, "fp64"))
-        extra("collapse mixed", lambda: _bench_collapse(args, stream, dev, "mixed"))
+        if args.collapse_precision in ("both", "fp64"):
+            extra("collapse fp64", lambda: _bench_collapse(args, stream, dev, "fp64"))
+        if args.collapse_precision in ("both", "mixed"):
+            extra("collapse mixed", lambda: _bench_collapse(args, stream, dev, "mixed"))
     if args.variants and args.latency and ws == 1:
         extra("latency small", lambda: _bench_latency_small(args, stream, dev))
     if args.serving_sweep and ws == 1:
@@ -1119,6 +1139,11 @@ def main():
                     help="skip the collapse-stress lines (64^3 x 31, 21.4 kHz, one period)")
     ap.add_argument("--collapse-edge", type=int, default=64)
     ap.add_argument("--collapse-steps", type=int, default=10000)
+    ap.add_argument("--collapse-precision", default="both", choices=("both", "fp64", "mixed"))
+    ap.add_argument("--collapse-save", default=None,
+                    help="profiling aid: save the collapse line's final state to this file")
+    ap.add_argument("--collapse-load", default=None,
+                    help="profiling aid: start the collapse line from a saved state")
     ap.add_argument("--no-latency", dest="latency", action="store_false",
                     help="skip the per-call latency line of the 64-cell workload")
     ap.add_argument("--serving-sweep", action="store_true",
@@ -1141,6 +1166,8 @@ def main():
                     help="skip the single-instance mixed-precision lines")
     ap.add_argument("--trace-trials", action="store_true",
                     help="profiling aid: print the trials of every step launch (no timing)")
+    ap.add_argument("--batch-launch", type=int, nargs=3, default=None, metavar=("WARPS", "CTAS_PER_SM", "GRAB"),
+                    help="profiling aid: the batched line's launch shape, instead of the autotuner's")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="instances of the batched line (profiling runs use fewer)")
     args = ap.parse_args()

@@ -106,8 +106,8 @@ typedef struct {
     double alpha0;          /* default n_b = alpha0 / (4/3 pi sum_i w_i R0_i^3) */
     double Rdot0_ref;       /* initial Rdot_i = Rdot0_ref * R0_i / R0ref (0: rest) */
     int32_t record_attempts;/* non-zero: keep per-bin trial counts of the last call */
-    int32_t block_warps;    /* warps per CTA, 1..16 (0: the default, 4 in PAB_FP64 and
-                               1 in PAB_MIXED); cells per CTA is 32 */
+    int32_t block_warps;    /* warps per CTA, 1..16 (0: the default, 4); a CTA of w warps
+                               owns 32 w cells (32 when a small grid is split by bins) */
     /* Contents with heat and mass transfer (gas_mode PAB_GAS_TRANSFER; FP64 only;
      * pab_transfer.h): gas constants of the gas and of the vapour, wall (liquid)
      * temperature, thermal conductivity of the contents, vapour-gas diffusion
@@ -222,8 +222,9 @@ pab_status pab_get_bins(const pab_t *h, double *R0_host, double *w_host, double 
  */
 pab_status pab_bin_table(const pab_config *cfg, double *R0_host, double *w_host, double *nb_default);
 
-/* Launch shape: warps per CTA (1..16; each warp covers 32 cells and strides
- * over the bins).  Used by the autotuner. */
+/* Launch shape: warps per CTA (1..16).  A CTA of w warps owns 32 w cells and
+ * its warps take the (bin, cell) items of those cells from one shared pool;
+ * the results are the same bits for every value.  Used by the autotuner. */
 pab_status pab_set_block_warps(pab_t *h, int32_t block_warps);
 
 /*

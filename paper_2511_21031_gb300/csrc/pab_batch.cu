@@ -30,6 +30,7 @@
 #include "pab_batch.h"
 #include "pab_device.cuh"
 #include "pab_internal.h"
+#include "pab_stream.cuh"
 
 namespace pab {
 namespace {
@@ -165,53 +166,6 @@ __device__ __forceinline__ void advance_one(const StepConst &K, const BinConst &
     n64 += nd;
 }
 
-// Running quadrature sums of one cell, in bin order: w R^3 (compensated in
-// MIXED), and the other three terms (FP32 sums in MIXED, FP64 otherwise).
-struct TermSums {
-    double m3 = 0.0, m3c = 0.0, m2v = 0.0, m3p = 0.0, m3v2 = 0.0;
-    float m2vf = 0.0f, m3pf = 0.0f, m3v2f = 0.0f;
-};
-template <bool MIXED>
-__device__ __forceinline__ void add_terms(TermSums &S, double x, const float *tf, const double *td)
-{
-    if (MIXED) {
-        neumaier_add(S.m3, S.m3c, x);
-        S.m2vf = __fadd_rn(S.m2vf, tf[0]);
-        S.m3pf = __fadd_rn(S.m3pf, tf[1]);
-        S.m3v2f = __fadd_rn(S.m3v2f, tf[2]);
-    } else {
-        S.m3 = __dadd_rn(S.m3, x);
-        S.m2v = __dadd_rn(S.m2v, td[0]);
-        S.m3p = __dadd_rn(S.m3p, td[1]);
-        S.m3v2 = __dadd_rn(S.m3v2, td[2]);
-    }
-}
-
-// The 7 moments of cell c from its sums.
-template <bool MIXED>
-__device__ __forceinline__ void write_moments(const StepConst &K, const SlotDesc &d, long long c,
-                                              const TermSums &S)
-{
-    double m3 = S.m3, m2v = S.m2v, m3p = S.m3p, m3v2 = S.m3v2;
-    if (MIXED) {
-        m3 += S.m3c;
-        m2v = f2d(S.m2vf);
-        m3p = fma(K.p0, m3, f2d(S.m3pf));  // p0 sum w R^3 + sum w R^3 (p_bw - p0)
-        m3v2 = f2d(S.m3v2f);
-    }
-    const double nb = d.nb ? d.nb[c] : K.nb_default;
-    const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
-    const double inv_m3 = 1.0 / m3;
-    const long long C = d.C;
-    d.out[0 * C + c] = nb;
-    d.out[1 * C + c] = alpha;
-    d.out[2 * C + c] = m3;
-    d.out[3 * C + c] = m2v;
-    d.out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
-    d.out[5 * C + c] = (MIXED ? m3p : K.rho * m3p) * inv_m3;  // FP64 terms are over rho
-    d.out[6 * C + c] = m3v2 * inv_m3;
-}
-
 // One tile's status counts into the slot's counters.
 __device__ __forceinline__ void flush_slot(SlotCounters *sc, uint32_t f, unsigned long long a,
                                            unsigned long long t, unsigned long long e)
@@ -232,13 +186,17 @@ __device__ __forceinline__ void flush_slot(SlotCounters *sc, uint32_t f, unsigne
 // Persistent batch kernel.  A CTA of one warp sums its tile's terms itself and
 // needs only the slot's constants in shared memory; wider CTAs stage the terms.
 // ---------------------------------------------------------------------------
-template <bool MIXED>
-// At most 72 registers.  One-warp CTAs (the autotuner's choice) are bounded by
-// registers alone: 28 fit on an SM at 72, 24 at 80, 32 at 64 with spills
-// (batched line 15.8e9 against 15.5e9 and 15.5e9 bin-steps/s).  Wider CTAs stage
-// the per-bin terms in shared memory (about 37 KB per CTA at Nb = 51), which
-// leaves room for 6 CTAs of 4 warps per SM at either count.
-__global__ void __maxnreg__(72)
+// ONE_WARP: CTAs of one warp (the autotuner's usual choice) stream the tile's items lane by
+// lane; wider CTAs take bins from a shared counter and stage the terms.  Each is its own
+// instantiation with its own registers.  At most 72 registers: one-warp CTAs are bounded by
+// registers alone (28 fit on an SM at 72); wider CTAs stage the per-bin terms in shared memory
+// (about 37 KB per CTA at Nb = 51), which leaves room for 6 CTAs of 4 warps per SM.
+#ifndef PAB_BATCH_MAXNREG
+#define PAB_BATCH_MAXNREG 72
+#endif
+
+template <bool MIXED, bool ONE_WARP>
+__global__ void __maxnreg__(PAB_BATCH_MAXNREG)
     batch_kernel(const SlotDesc *__restrict__ slots, const int *__restrict__ order,
                  const long long *__restrict__ start, Queue *q, SlotCounters *cnt,
                  int bins_per_grab, int max_bins)
@@ -301,33 +259,28 @@ __global__ void __maxnreg__(72)
         uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
         TermSums S;
 
-        if (nw == 1) {
-            // one warp: the tile's bins in order, each bin's terms summed as they come,
-            // in the order and with the arithmetic of the staged sum below (the same
-            // results for every launch shape), without shared terms or barriers
+        if constexpr (ONE_WARP) {
+            // one warp: the tile's bins in order, each bin's terms summed as they come, in the
+            // order and with the arithmetic of the staged sum below and of the step kernel's
+            // closing pass (the same results for every launch shape).  (Streaming the items lane
+            // by lane, as the step kernel does, measured slower here: 16.0e9 against 17.6e9
+            // bin-steps/s on the 512-instance line, and 11.2e9 with each lane walking its own
+            // cell's bins.)
+            TileCounts tc;
             for (int b = 0; b < d.B && valid; ++b) {
                 const BinConst &bc = K.bins[b];
                 double R, V;
                 GasBase g;
-                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, fl_or, n_flag, n_att, n64);
-                if (d.out) {
-                    if (MIXED) {
-                        float tf[3];
-                        const double x = quad_terms_mixed(K, bc, R, V, tf);
-                        add_terms<MIXED>(S, x, tf, nullptr);
-                    } else {
-                        double t[4];
-                        quad_terms64(K, bc, R, V, t, g);
-                        add_terms<MIXED>(S, t[0], nullptr, t + 1);
-                    }
-                }
+                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, tc.fl_or, tc.n_flag, tc.n_att, tc.n64);
+                if (d.out)
+                    add_bin_terms<MIXED>(K, b, R, V, S);
             }
-            fl_or = __reduce_or_sync(0xffffffffu, fl_or);
-            n_flag = __reduce_add_sync(0xffffffffu, n_flag);
-            n_att = __reduce_add_sync(0xffffffffu, n_att);
-            n64 = __reduce_add_sync(0xffffffffu, n64);
+            fl_or = __reduce_or_sync(0xffffffffu, tc.fl_or);
+            n_flag = __reduce_add_sync(0xffffffffu, tc.n_flag);
+            n_att = __reduce_add_sync(0xffffffffu, tc.n_att);
+            n64 = __reduce_add_sync(0xffffffffu, tc.n64);
             if (d.out && valid)
-                write_moments<MIXED>(K, d, c, S);
+                write_moments<MIXED>(K, d.nb ? d.nb[c] : K.nb_default, d.C, c, S, d.out);
             if (lane == 0)
                 flush_slot(cnt + slot, fl_or, n_flag, n_att, n64);
             __syncwarp();
@@ -391,7 +344,7 @@ __global__ void __maxnreg__(72)
                     add_terms<MIXED>(S, x, nullptr, td);
                 }
             }
-            write_moments<MIXED>(K, d, c, S);
+            write_moments<MIXED>(K, d.nb ? d.nb[c] : K.nb_default, d.C, c, S, d.out);
         }
         if (threadIdx.x == 0) {
             uint32_t f = 0;
@@ -411,8 +364,22 @@ __global__ void __maxnreg__(72)
 template <bool MIXED>
 cudaError_t set_smem_limit(size_t bytes)
 {
-    return cudaFuncSetAttribute(batch_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<MIXED, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<MIXED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+    return e;
+}
+
+// The batch kernel of a precision and CTA width.
+typedef void (*BatchKernelFn)(const SlotDesc *, const int *, const long long *, Queue *, SlotCounters *,
+                              int, int);
+inline BatchKernelFn batch_kernel_fn(bool mixed, bool one_warp)
+{
+    if (mixed)
+        return one_warp ? batch_kernel<true, true> : batch_kernel<true, false>;
+    return one_warp ? batch_kernel<false, true> : batch_kernel<false, false>;
 }
 
 }  // namespace
@@ -534,7 +501,9 @@ void arena_give(pab_batch_t *b, long long off, long long n)
 // than one warp the per-bin terms of a tile too.
 size_t launch_smem(const pab_batch_t *b)
 {
-    return b->block_warps == 1 ? pab::const_bytes() : b->smem_bytes;
+    if (b->block_warps == 1)
+        return pab::const_bytes();
+    return b->smem_bytes;
 }
 
 int resident_ctas(const pab_batch_t *b)
@@ -542,12 +511,9 @@ int resident_ctas(const pab_batch_t *b)
     int per_sm = 0;
     const int threads = b->block_warps * 32;
     cudaError_t e;
-    if (b->cfg.precision == PAB_MIXED)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pab::batch_kernel<true>, threads,
-                                                          launch_smem(b));
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pab::batch_kernel<false>, threads,
-                                                          launch_smem(b));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, pab::batch_kernel_fn(b->cfg.precision == PAB_MIXED, b->block_warps == 1), threads,
+        launch_smem(b));
     if (e != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int want = b->ctas_per_sm > 0 ? b->ctas_per_sm : 4;
@@ -568,12 +534,9 @@ cudaError_t enqueue_step(pab_batch_t *b, cudaStream_t s, int grid)
         return e;
     const int threads = b->block_warps * 32;
     const int maxb = b->cfg.max_bins;
-    if (b->cfg.precision == PAB_MIXED)
-        pab::batch_kernel<true><<<grid, threads, launch_smem(b), s>>>(
-            b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
-    else
-        pab::batch_kernel<false><<<grid, threads, launch_smem(b), s>>>(
-            b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
+    pab::batch_kernel_fn(b->cfg.precision == PAB_MIXED, b->block_warps == 1)<<<grid, threads,
+                                                                              launch_smem(b), s>>>(
+        b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
     return cudaGetLastError();
 }
 
@@ -706,8 +669,9 @@ pab_status pab_batch_create(const pab_batch_config *cfg, void *stream, pab_batch
         b->smem_bytes = pab::const_bytes() + (size_t)b->cfg.max_bins * pab::kTile * sizeof(double) +
                         (size_t)3 * b->cfg.max_bins * pab::kTile *
                             (cfg->precision == PAB_MIXED ? sizeof(float) : sizeof(double));
-        e = cfg->precision == PAB_MIXED ? pab::set_smem_limit<true>(b->smem_bytes)
-                                        : pab::set_smem_limit<false>(b->smem_bytes);
+        const size_t limit = b->smem_bytes;
+        e = cfg->precision == PAB_MIXED ? pab::set_smem_limit<true>(limit)
+                                        : pab::set_smem_limit<false>(limit);
     }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);

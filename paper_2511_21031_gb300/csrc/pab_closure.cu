@@ -4,13 +4,13 @@
 // Eq. (eos_liquid).  All are memory-bound elementwise or per-cell passes.
 #include <cuda_runtime.h>
 
+#include "pab_check.cuh"
 #include "pab_internal.h"
+
+PAB_CHECK_UNIT(closure)
 
 namespace pab {
 namespace {
-
-constexpr int kTile = 32;
-constexpr int kWarps = 8;
 
 // qR = n_b R, qV = n_b Rdot; grid.y walks the bins, grid.x the cells.
 __global__ void cons_from_prim_kernel(long long C, const double *__restrict__ nb, double nb_default,
@@ -21,56 +21,65 @@ __global__ void cons_from_prim_kernel(long long C, const double *__restrict__ nb
     if (c >= C)
         return;
     const size_t k = (size_t)blockIdx.y * (size_t)C + (size_t)c;
-    const double n = nb ? nb[c] : nb_default;
-    qR[k] = n * R[k];
-    qV[k] = n * V[k];
+    const long long ns = (long long)gridDim.y * C;
+    const double n = nb ? PAB_LD(nb, c, C) : nb_default;
+    PAB_ST(qR, k, ns, n * PAB_LD(R, k, ns));
+    PAB_ST(qV, k, ns, n * PAB_LD(V, k, ns));
 }
 
-// Per 32-cell tile: the warps sum w qR^3 over a strided subset of bins, the
-// partial sums meet in shared memory, n_b = sqrt(4/3 pi S / alpha), then every
-// warp rescales its bins.
-__global__ void __launch_bounds__(kWarps * 32)
+// One thread per cell: the sum of w qR^3 over the bins, n_b = sqrt(4/3 pi S / alpha), then the
+// rescale of every bin.  Consecutive threads read consecutive cells of one bin row (coalesced),
+// and the bin loops are unrolled so that each thread keeps kUnroll loads in flight: a 32-cell
+// CTA whose warps walked four bins each with a dependent sum held too few bytes in flight to
+// cover HBM latency.  The second read of qR comes from L2 (a CTA's rows were just read).
+constexpr int kCellsPerCta = 256;
+constexpr int kUnroll = 8;
+__global__ void __launch_bounds__(kCellsPerCta)
     prim_from_cons_kernel(const __grid_constant__ StepConst K, const double *__restrict__ alpha,
                           const double *__restrict__ qR, const double *__restrict__ qV,
                           double *__restrict__ R, double *__restrict__ V, double *__restrict__ nb_out)
 {
-    __shared__ double part[kWarps][kTile];
-    __shared__ double inv_nb[kTile];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const long long c = (long long)blockIdx.x * kTile + lane;
-    const bool valid = c < K.C;
-    double s = 0.0;
-    for (int b = warp; b < K.B; b += kWarps) {
-        if (valid) {
-            const double q = qR[(size_t)b * (size_t)K.C + (size_t)c];
-            s += K.bins[b].w * q * q * q;
-        }
-    }
-    part[warp][lane] = s;
-    __syncthreads();
-    if (warp == 0) {
-        double S = 0.0;
-        for (int w = 0; w < kWarps; ++w)
-            S += part[w][lane];
-        double n = (double)NAN;
-        if (valid) {
-            const double a = alpha[c];
-            if (a > 0.0 && a <= 1.0e300)
-                n = sqrt((4.0 / 3.0 * 3.14159265358979323846) * S / a);
-            if (nb_out)
-                nb_out[c] = n;
-        }
-        inv_nb[lane] = 1.0 / n;
-    }
-    __syncthreads();
-    if (!valid)
+    const long long c = (long long)blockIdx.x * kCellsPerCta + threadIdx.x;
+    if (c >= K.C)
         return;
-    const double in = inv_nb[lane];
-    for (int b = warp; b < K.B; b += kWarps) {
-        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        R[k] = qR[k] * in;
-        V[k] = qV[k] * in;
+    const size_t C = (size_t)K.C;
+    const long long ns = (long long)K.B * K.C;
+    // the bins in chunks of kUnroll, every load of a chunk issued before its arithmetic (the
+    // last chunk predicated), so that a thread keeps kUnroll loads in flight throughout
+    double s = 0.0;
+    for (int b = 0; b < K.B; b += kUnroll) {
+        double q[kUnroll];
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i)
+            q[i] = b + i < K.B ? PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns) : 0.0;
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i)
+            if (b + i < K.B)
+                s += K.bins[b + i].w * q[i] * q[i] * q[i];
+    }
+    double n = (double)NAN;
+    const double a = PAB_LD(alpha, c, K.C);
+    if (a > 0.0 && a <= 1.0e300)
+        n = sqrt((4.0 / 3.0 * 3.14159265358979323846) * s / a);
+    if (nb_out)
+        PAB_ST(nb_out, c, K.C, n);
+    const double in = 1.0 / n;
+    for (int b = 0; b < K.B; b += kUnroll) {
+        double qr[kUnroll], qv[kUnroll];
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i) {
+            const size_t k = (size_t)(b + i) * C + (size_t)c;
+            qr[i] = b + i < K.B ? PAB_LD(qR, k, ns) : 0.0;
+            qv[i] = b + i < K.B ? PAB_LD(qV, k, ns) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i) {
+            const size_t k = (size_t)(b + i) * C + (size_t)c;
+            if (b + i < K.B) {
+                PAB_ST(R, k, ns, qr[i] * in);
+                PAB_ST(V, k, ns, qv[i] * in);
+            }
+        }
     }
 }
 
@@ -81,9 +90,9 @@ __global__ void mixture_pressure_kernel(long long C, const double *__restrict__ 
 {
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C;
          c += (long long)gridDim.x * blockDim.x) {
-        const double a = m[1 * C + c];
-        const double rho = rho_l ? rho_l[c] : rho_default;
-        p[c] = (1.0 - a) * p_l[c] + a * (m[5 * C + c] - rho * m[6 * C + c]);
+        const double a = PAB_LD(m, 1 * C + c, 7 * C);
+        const double rho = rho_l ? PAB_LD(rho_l, c, C) : rho_default;
+        PAB_ST(p, c, C, (1.0 - a) * PAB_LD(p_l, c, C) + a * (PAB_LD(m, 5 * C + c, 7 * C) - rho * PAB_LD(m, 6 * C + c, 7 * C)));
     }
 }
 
@@ -93,7 +102,7 @@ __global__ void stiffened_gas_kernel(long long n, const double *__restrict__ rho
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        p[i] = gm1 * rho[i] * e[i] - gpi;
+        PAB_ST(p, i, n, gm1 * PAB_LD(rho, i, n) * PAB_LD(e, i, n) - gpi);
 }
 
 unsigned grid_for(long long n, int threads)
@@ -117,8 +126,8 @@ cudaError_t launch_prim_from_cons(const StepConst &K, const double *alpha, const
                                   const double *qV, double *R, double *V, double *nb_out,
                                   cudaStream_t s)
 {
-    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    prim_from_cons_kernel<<<grid, kWarps * 32, 0, s>>>(K, alpha, qR, qV, R, V, nb_out);
+    const dim3 grid((unsigned)((K.C + kCellsPerCta - 1) / kCellsPerCta));
+    prim_from_cons_kernel<<<grid, kCellsPerCta, 0, s>>>(K, alpha, qR, qV, R, V, nb_out);
     return cudaGetLastError();
 }
 

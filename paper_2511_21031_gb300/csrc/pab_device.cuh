@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "pab_bits.cuh"
+#include "pab_check.cuh"
 #include "pab_internal.h"
 
 namespace pab {
@@ -57,9 +58,11 @@ __device__ __forceinline__ double gas_factor(const StepConst &K, const BinConst 
         const int j = __float2int_rn(__log2f(xf) * K.gas_inv_log2q);
         if (j >= -K.gas_J && j <= K.gas_J) {
             // {x_j, c_0}, {c_1, c_2}, {c_3, 0}
-            const double2 *e = reinterpret_cast<const double2 *>(K.gas_tab) + 3 * (j + K.gas_J);
-            const double2 n0 = __ldg(e), n1 = __ldg(e + 1);
-            const double c3 = __ldg(reinterpret_cast<const double *>(e + 2));
+            const double2 *tab = reinterpret_cast<const double2 *>(K.gas_tab);
+            const int e = 3 * (j + K.gas_J);
+            const int ne = 3 * (2 * K.gas_J + 1);
+            const double2 n0 = PAB_LDG(tab, e, ne), n1 = PAB_LDG(tab, e + 1, ne);
+            const double c3 = PAB_LDG(K.gas_tab, 2 * (e + 2), 2 * ne);
             const double d = fma(R, bc.invR0, -n0.x);
             double s = fma(c3, d, n1.y);
             s = fma(s, d, n1.x);
@@ -190,7 +193,9 @@ __device__ __forceinline__ float pow_m1_32(float u, float a)
     return __fmaf_rn(sc, __fmul_rn(r, q), __fsub_rn(sc, 1.0f));
 }
 
-__device__ __forceinline__ float gas_dev32(const StepConst &K, const BinConst &bc, float u)
+// (BC: BinConst, or any bin type with the FP32 fields R0f, invR0f and pg0f.)
+template <class BC>
+__device__ __forceinline__ float gas_dev32(const StepConst &K, const BC &bc, float u)
 {
     return __fmul_rn(bc.pg0f, pow_m1_32(u, K.three_gammaf));
 }
@@ -199,7 +204,8 @@ __device__ __forceinline__ float gas_dev32(const StepConst &K, const BinConst &b
 //   P = L (A + pgdev) - 3 gamma (1/c)/rho p_g Rdot - 3/2 Rdot^2 (1 - Rdot/(3c)),
 //   Q = L (2 sigma u - 4 mu Rdot) + (1/c)/rho Rdot (2 sigma + 4 mu Rdot),
 // with L = (1 + Rdot/c)/rho, so Rddot = (P R + Q) / (R den): one division.
-__device__ __forceinline__ float accel32(const StepConst &K, const BinConst &bc, float A, float xi,
+template <class BC>
+__device__ __forceinline__ float accel32(const StepConst &K, const BC &bc, float A, float xi,
                                          float V)
 {
     const float R = __fadd_rn(bc.R0f, xi);
@@ -280,7 +286,8 @@ struct Incr32 {
     float d3R, d3V;  // y3 - y
     bool ok;
 };
-__device__ __forceinline__ Incr32 incr32(const StepConst &K, const BinConst &bc, float A, float xi,
+template <class BC>
+__device__ __forceinline__ Incr32 incr32(const StepConst &K, const BC &bc, float A, float xi,
                                          float v, float hf)
 {
     Incr32 t;

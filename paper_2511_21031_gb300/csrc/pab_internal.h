@@ -28,13 +28,13 @@ struct BinConst {
     float dpeqf;   // peq - p0 in FP32 (0 up to rounding for the polytropic gas)
 };
 
-// Warps per CTA of the step kernels when the configuration leaves it open,
-// measured on the 128^3 x 31 lines: in FP64 1, 2, 4 and 8 warps lie within 1 %
-// (4 is kept); in mixed precision one warp per CTA is 5 % faster than 2 or 4
-// (25.6e9 against 24.4e9 and 24.5e9 bin-steps/s): the warp sums its tile's bins
-// itself, without the cross-warp reduction and its barrier.
+// Warps per CTA of the step kernels when the configuration leaves it open.  A CTA of w warps
+// owns w tiles of 32 cells and streams their items from one pool (pab_stream.cuh), parking the
+// mixed path's FP64 trials in one lot.  Measured on the 128^3 x 31 line and on the collapse
+// window of the 64^3 x 31 stress workload (1, 4 and 8 warps): FP64 4.93/5.00/5.01e9 and
+// 4.45/4.46/4.28e9 bin-steps/s; mixed 25.5/26.0/25.7e9 and 8.85/9.27/8.93e9.  4 in both.
 constexpr int kDefaultWarps = 4;
-constexpr int kDefaultWarpsMixed = 1;
+constexpr int kDefaultWarpsMixed = 4;
 inline int default_warps(int precision) { return precision == PAB_MIXED ? kDefaultWarpsMixed : kDefaultWarps; }
 
 constexpr int kGasTerms = 12;    // binomial series of the gas term: degree 11
@@ -103,6 +103,15 @@ struct Counters {
     unsigned long long n_fp64;
 };
 
+// A mixed-precision item parked in a CTA's lot: the controller state of one (bin, cell) part
+// way through its flow step.
+struct Parked {
+    double xi64, V, h, rem;
+    float xi, v;
+    int32_t b, n, n64, pad;
+    int64_t c;
+};
+
 struct StepArgs {
     const double *p_inf;   // [C]
     const double *nb;      // [C] or nullptr
@@ -117,6 +126,21 @@ struct StepArgs {
     double *pb = nullptr;  // [B][C] bubble pressure (PAB_GAS_TRANSFER)
     double *mv = nullptr;  // [B][C] vapour mass (PAB_GAS_TRANSFER)
 };
+
+// The first out-of-bounds index a checked build (PAB_CHECKED, pab_check.cuh) met in one
+// translation unit: how many were met, the source line, the index and the buffer's length.
+struct CheckRecord {
+    unsigned int count;
+    int line;
+    long long index;
+    long long bound;
+};
+// Readers of each unit's record (zeros in an unchecked build); clear: reset it after reading.
+void check_fetch_kernels(CheckRecord *r, bool clear);
+void check_fetch_batch(CheckRecord *r, bool clear);
+void check_fetch_closure(CheckRecord *r, bool clear);
+void check_fetch_el(CheckRecord *r, bool clear);
+void check_fetch_transfer(CheckRecord *r, bool clear);
 
 // Configuration helpers (pab_api.cu): validation as pab_create does it, the
 // bin table of a configuration, and the kernel constants.

@@ -1,202 +1,151 @@
 // Kernels of the bubble source update on sm_103a.
 //
-// Work decomposition: a CTA owns a tile of 32 consecutive cells (one per
-// lane) and all Nb bins of those cells; its warps stride over the bins.  All
-// lanes of a warp therefore advance the same bin of 32 neighbouring cells:
-// loads and stores of the bin-major state are 256-byte coalesced, the bin
-// constants are warp-uniform constant-bank reads, and neighbouring cells
-// (similar pressure) need similar sub-step counts, which keeps the adaptive
-// loop's divergence low.  Each lane keeps running quadrature sums for its
-// cell over the bins its warp visits; the warps' partial sums are combined in
-// shared memory and one warp writes the 7 moments of the 32 cells.  No
-// atomics touch the state: every (bin, cell) has one owner (Sec. 4).
+// Work decomposition: a CTA owns a tile of 32 consecutive cells and a range of
+// their bins (all Nb bins, except where a small grid is split over more SMs:
+// then a range per CTA, the moments from a second launch).  Its warps advance
+// the tile's (bin, cell) items lane by lane (pab_stream.cuh): bin-major, so the
+// loads and stores of the bin-major state stay coalesced while the lanes run
+// together, and a lane that finishes an item takes the next one instead of
+// waiting for its neighbours' stiffer items.  After the items, one warp reads
+// the tile's new state back and writes the 7 moments of its 32 cells, summing
+// each cell's bins in bin order.  No atomics touch the state: every (bin, cell)
+// has one owner (Sec. 4).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+
+#include "pab_check.cuh"
 #include "pab_device.cuh"
 #include "pab_internal.h"
 #include "pab_reduce.cuh"
+#include "pab_stream.cuh"
+
+PAB_CHECK_UNIT(kernels)
 
 namespace pab {
 namespace {
 
-// FP64 mode (and the reduce-only kernel in both modes): terms from the FP64 state.
+// Fixed mode: n equal trials per item, the same for every item, so each thread carries one
+// cell of the CTA through the bin range.
 template <bool MIXED>
-__device__ __forceinline__ void accumulate(const StepConst &K, const BinConst &bc, double R,
-                                           double V, MomAcc<MIXED> &acc, GasBase &g)
+__device__ __forceinline__ void fixed_items(const StepConst &K, const StepArgs &a, const TileIO &io,
+                                            TileCounts &tc)
 {
-    const double wr2 = bc.w * R * R;
-    const double wr3 = wr2 * R;
-    if (MIXED) {
-        const float xi = d2f(R - bc.R0);
-        const float Rf = d2f(R);
-        const float Vf = d2f(V);
-        const float u = xi * bc.invR0f;
-        const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-        const float dev = pgdev + div32(K.two_sigmaf * u - K.four_muf * Vf, Rf);
-        const float wr3f = d2f(wr3);
-        acc.add_m3(wr3);
-        acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
-        acc.m2vf = fmaf(d2f(wr2), Vf, acc.m2vf);
-        acc.m3v2f = fmaf(wr3f * Vf, Vf, acc.m3v2f);
-    } else {
-        // w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho, s = 4 mu Rdot + 2 sigma
-        acc.add_m3(wr3);
-        acc.m2v = fma(wr2, V, acc.m2v);
-        acc.m3p = fma(wr3, bubble_pressure_rho64(K, bc, R, g), acc.m3p);
-        acc.m3p = fma(-wr2, fma(K.fmu_rho, V, K.tsig_rho), acc.m3p);
-        acc.m3v2 = fma(wr3 * V, V, acc.m3v2);
-    }
-}
-
-// MIXED step kernel: the FP32 images xi = R - R0 and Rdot the advance left
-// behind spare their conversions; w R^3 stays FP64 for the compensated sum.
-template <bool MIXED>
-__device__ __forceinline__ void accumulate_mixed(const StepConst &K, const BinConst &bc, double R,
-                                                 float xi, float v, MomAcc<MIXED> &acc)
-{
-    const float Rf = bc.R0f + xi;
-    const float u = xi * bc.invR0f;
-    const float pgdev = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_dev32(K, bc, u) : 0.0f;
-    const float iRf = rcp32(Rf);
-    const float dev = pgdev + (K.two_sigmaf * u - K.four_muf * v) * iRf;
-    const double wr3 = bc.w * R * R * R;
-    const float wr3f = d2f(wr3);
-    const float wr2f = wr3f * iRf;  // w R^2 = w R^3 / R
-    acc.add_m3(wr3);
-    acc.m3pf = fmaf(wr3f, bc.dpeqf + dev, acc.m3pf);
-    acc.m2vf = fmaf(wr2f, v, acc.m2vf);
-    acc.m3v2f = fmaf(wr3f * v, v, acc.m3v2f);
-}
-
-template <bool MIXED>
-__device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
-    const bool valid = c < K.C;
-    const double p_inf = valid ? a.p_inf[c] : K.p0;
+    if ((int)threadIdx.x >= io.nc)
+        return;
+    const long long c = io.c0 + threadIdx.x;
+    const long long ns = (long long)K.B * K.C;
+    const double p_inf = PAB_LD(a.p_inf, c, K.C);
     const bool p_ok = finite64(p_inf);
-    const double nb = valid ? (a.nb ? a.nb[c] : K.nb_default) : 0.0;
-
-    MomAcc<MIXED> acc;
-    uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
-    const float dp_cell = MIXED ? d2f(K.p0 - p_inf) : 0.0f;  // p_eq - p_inf = dpeq + dp_cell
-    for (int b = warp; b < K.B; b += nw) {
-        if (!valid)
-            continue;
+    for (int b = io.b0; b < io.b1; ++b) {
         const BinConst &bc = K.bins[b];
         const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        double R = a.R[k];
-        double V = a.V[k];
+        double R = PAB_LD(a.R, k, ns), V = PAB_LD(a.V, k, ns);
         uint32_t fl = 0;
         int na = 0;
-        GasBase g;
-        g.reset();
         if (!p_ok || !finite64(R) || !finite64(V)) {
             fl = PAB_FLAG_NONFINITE;
-        } else if (MIXED && K.n_fixed == 0) {  // (only reachable in the MIXED instantiation)
-            const float A = bc.dpeqf + dp_cell;
-            float hc = a.h[k];
-            int nd = 0;
-            float xi, v;
-            fl = advance_mixed(K, bc, p_inf, A, a.dt, R, V, hc, na, nd, xi, v);
-            a.h[k] = hc;
-            n64 += nd;
-            // the checks read the FP32 images of the new state
-            if (!isfinite(xi) || !isfinite(v))
-                fl |= PAB_FLAG_NONFINITE;
-            else if (!(bc.R0f + xi > 0.0f))
-                fl |= PAB_FLAG_NONPOS;
-            if (fabsf(v) >= K.cf)
-                fl |= PAB_FLAG_SUPERSONIC;
-            a.R[k] = R;
-            a.V[k] = V;
-            // a finite state has finite FP32 images (|R - R0| and |Rdot| are far below the
-            // FP32 range) and a non-finite one gives NaN moments either way
-            if (a.out)
-                accumulate_mixed<MIXED>(K, bc, R, xi, v, acc);
-            if (a.attempts)
-                a.attempts[k] = na;
-            fl_or |= fl;
-            n_flag += (fl != 0);
-            n_att += na;
-            continue;
         } else {
-            const float A = MIXED ? bc.dpeqf + dp_cell : 0.0f;
-            if (K.n_fixed > 0) {
-                advance_fixed<MIXED>(K, bc, p_inf, A, a.dt_sub, R, V, g);
-                na = K.n_fixed;
-            } else {
-                float hc = a.h[k];
-                fl = advance_adaptive(K, bc, p_inf, a.dt, R, V, hc, na, g);
-                a.h[k] = hc;
-            }
+            GasBase g;
+            g.reset();
+            const float A = MIXED ? bc.dpeqf + d2f(K.p0 - p_inf) : 0.0f;
+            advance_fixed<MIXED>(K, bc, p_inf, A, a.dt_sub, R, V, g);
+            na = K.n_fixed;
             if (!finite64(R) || !finite64(V))
                 fl |= PAB_FLAG_NONFINITE;
             else if (!gt0(R))
                 fl |= PAB_FLAG_NONPOS;
             if (abs_ge(V, K.c))
                 fl |= PAB_FLAG_SUPERSONIC;
-            a.R[k] = R;
-            a.V[k] = V;
+            PAB_ST(a.R, k, ns, R);
+            PAB_ST(a.V, k, ns, V);
         }
         if (a.attempts)
-            a.attempts[k] = na;
-        fl_or |= fl;
-        n_flag += (fl != 0);
-        n_att += na;
-        if (a.out)
-            accumulate<MIXED>(K, bc, R, V, acc, g);
+            PAB_ST(a.attempts, k, ns, na);
+        tc.fl_or |= fl;
+        tc.n_flag += (fl != 0);
+        tc.n_att += na;
     }
-    if (a.out)
-        reduce_and_store<MIXED>(K, acc, nb, c, valid, a.out);
-    flush_counters(fl_or, n_flag, n_att, n64, a.counters);
 }
 
-// One kernel per precision with its own register bound.  MIXED: 64 registers
-// (kMaxWarps x 32 threads x 2 CTAs), so 8 CTAs of the default 4 warps fit on an
-// SM; left to itself the compiler takes 110 and 4 CTAs fit (13.2e9 against
-// 17.5e9 bin-steps/s on the 128^3 x 31 line).  FP64: no minimum, where the
-// compiler settles on 64 registers itself (3 % faster than 64 under the bound).
+// One CTA of nw warps.  With one bin range (gridDim.y == 1) it owns nw tiles (32 nw cells from
+// blockIdx.x * 32 nw) and all their bins, and ends with their moments (warp w: tile w);
+// otherwise one tile (blockIdx.x) and bin range blockIdx.y.  Dynamic shared memory: the lot of
+// parked items (32 per warp) in adaptive mixed precision, nothing otherwise.
+template <bool MIXED>
+__device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PoolCounters sh;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int cells = gridDim.y == 1 ? kTile * nw : kTile;
+    TileIO io;
+    io.p_inf = a.p_inf;
+    io.R = a.R;
+    io.V = a.V;
+    io.h = a.h;
+    io.attempts = a.attempts;
+    io.C = K.C;
+    io.c0 = (long long)blockIdx.x * cells;
+    io.nc = (int)min((long long)cells, K.C - io.c0);
+    const int per = (K.B + (int)gridDim.y - 1) / (int)gridDim.y;
+    io.b0 = min(K.B, (int)blockIdx.y * per);
+    io.b1 = min(K.B, io.b0 + per);
+    io.dt = a.dt;
+    TileCounts tc;
+    if (K.n_fixed > 0) {
+        fixed_items<MIXED>(K, a, io, tc);
+    } else {
+        if (threadIdx.x == 0)
+            sh = PoolCounters{0, 0, 0};
+        __syncthreads();
+        if (MIXED) {
+            stream_mixed(K, io, sh, reinterpret_cast<Parked *>(smem), kLotPerWarp * nw, tc);
+        } else {
+            stream_fp64(K, io, sh, tc);
+        }
+    }
+    // block-wide counters; the barrier inside also orders the state writes before the reads below
+    flush_counters(tc.fl_or, tc.n_flag, tc.n_att, tc.n64, a.counters);
+    const long long c = io.c0 + (long long)kTile * warp + lane;
+    if (a.out && gridDim.y == 1 && c < io.c0 + io.nc)
+        cell_moments<MIXED>(K, a.R, a.V, K.C, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out);
+}
+
+#ifndef PAB_STEP64_MAXNREG
+#define PAB_STEP64_MAXNREG 96
+#endif
+#ifndef PAB_STEPMX_MAXNREG
+#define PAB_STEPMX_MAXNREG 64
+#endif
 template <bool MIXED>
 __global__ void step_kernel(const __grid_constant__ StepConst K, const StepArgs a);
 template <>
-__global__ void __launch_bounds__(kMaxWarps * 32)
+__global__ void __maxnreg__(PAB_STEP64_MAXNREG)
     step_kernel<false>(const __grid_constant__ StepConst K, const StepArgs a)
 {
     step_body<false>(K, a);
 }
 template <>
-__global__ void __launch_bounds__(kMaxWarps * 32, 2)
+__global__ void __maxnreg__(PAB_STEPMX_MAXNREG)
     step_kernel<true>(const __grid_constant__ StepConst K, const StepArgs a)
 {
     step_body<true>(K, a);
 }
 
+// Reduce-only: one warp per tile, one lane per cell, the bins in order (the pass the step
+// kernel ends with).
 template <bool MIXED>
-__global__ void __launch_bounds__(kMaxWarps * 32)
+__global__ void __launch_bounds__(32)
     moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
-                   const double *__restrict__ Rp, const double *__restrict__ Vp,
-                   double *__restrict__ out)
+                   const double *R, const double *V, double *out)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
-    const bool valid = c < K.C;
-    const double nb = valid ? (nbp ? nbp[c] : K.nb_default) : 0.0;
-    MomAcc<MIXED> acc;
-    for (int b = warp; b < K.B; b += nw) {
-        if (!valid)
-            continue;
-        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        GasBase g;
-        g.reset();
-        accumulate<MIXED>(K, K.bins[b], Rp[k], Vp[k], acc, g);
-    }
-    reduce_and_store<MIXED>(K, acc, nb, c, valid, out);
+    const long long c = (long long)blockIdx.x * kTile + threadIdx.x;
+    if (c < K.C)
+        cell_moments<MIXED>(K, R, V, K.C, c, nbp ? PAB_LD(nbp, c, K.C) : K.nb_default, out);
 }
 
 __global__ void init_kernel(const __grid_constant__ StepConst K, double rdot_scale, double *R,
@@ -207,37 +156,72 @@ __global__ void init_kernel(const __grid_constant__ StepConst K, double rdot_sca
          i += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / (size_t)K.C);
         const double R0 = K.bins[b].R0;
-        R[i] = R0;
-        V[i] = rdot_scale * R0;
-        h[i] = 0.0f;
+        PAB_ST(R, i, n, R0);
+        PAB_ST(V, i, n, rdot_scale * R0);
+        PAB_ST(h, i, n, 0.0f);
     }
 }
 
 
 }  // namespace
 
-cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,
-                        cudaStream_t s)
+// SMs of the current device (cached per device).
+static int sm_count()
 {
-    const int nw = clamp_warps(block_warps, K.B);
-    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    if (precision == PAB_MIXED)
-        step_kernel<true><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
-    else
-        step_kernel<false><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
-    return cudaGetLastError();
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return 152;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, const double *R,
-                           const double *V, double *out, int block_warps, cudaStream_t s)
+                           const double *V, double *out, int /*block_warps*/, cudaStream_t s)
 {
-    const int nw = clamp_warps(block_warps, K.B);
     const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
     if (precision == PAB_MIXED)
-        moments_kernel<true><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, out);
+        moments_kernel<true><<<grid, kTile, 0, s>>>(K, nb, R, V, out);
     else
-        moments_kernel<false><<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, out);
+        moments_kernel<false><<<grid, kTile, 0, s>>>(K, nb, R, V, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, int block_warps,
+                        cudaStream_t s)
+{
+    int nw = block_warps <= 0 ? default_warps(precision) : std::min(block_warps, kMaxWarps);
+    const long long tiles = (K.C + kTile - 1) / kTile;
+    // A CTA of nw warps owns nw tiles.  A grid of fewer tiles than SMs is instead split by bins
+    // over more CTAs of one tile each (a latency-bound call: each CTA's trials are serial on its
+    // SM's FP64 pipe), one warp per 32 items, and its moments come from the reduce-only kernel
+    // afterwards.
+    int groups = 1;
+    long long ctas = (tiles + nw - 1) / nw;
+    const int n_sm = sm_count();
+    if (tiles < n_sm && K.B > 1) {
+        groups = (int)std::min((long long)K.B, ((long long)n_sm + tiles - 1) / tiles);
+        const int per = (K.B + groups - 1) / groups;
+        groups = (K.B + per - 1) / per;
+        nw = std::min(nw, per);
+        ctas = tiles;
+    }
+    const dim3 grid((unsigned)ctas, (unsigned)groups);
+    const bool mixed_adaptive = precision == PAB_MIXED && K.n_fixed == 0;
+    const size_t smem = mixed_adaptive ? lot_bytes(kLotPerWarp * nw) : 0;
+    if (precision == PAB_MIXED)
+        step_kernel<true><<<grid, nw * 32, smem, s>>>(K, a);
+    else
+        step_kernel<false><<<grid, nw * 32, smem, s>>>(K, a);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && groups > 1 && a.out)
+        e = launch_moments(K, precision, a.nb, a.R, a.V, a.out, 0, s);
+    return e;
 }
 
 cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
