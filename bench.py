@@ -45,31 +45,30 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel executes per trial
 # (one sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination,
-# error norm, controller) and per bin-step outside the trial loop (load, bubble
-# pressure and quadrature sums): least-squares fit of ncu's
-# smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over six launches
-# of the 64^3 x 31 grid with traced trial counts (residual 6e-4).
-FP64_FLOPS_PER_TRIAL = 129.45
-FP64_FLOPS_PER_BINSTEP = 26.1
+# error norm, controller) and per bin-step outside the trial loop (load, start of
+# the step, the closing pass's bubble pressure and quadrature sums): least-squares
+# fit of ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over nine
+# launches of the 64^3 x 31 grid with traced trial counts (residual 7e-4).
+FP64_FLOPS_PER_TRIAL = 129.51
+FP64_FLOPS_PER_BINSTEP = 28.23
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
 # on the 64^3 x 31 grid, 285.6 MB / 8.13M bin-steps); scaled by bin-steps.
 FP64_DRAM_BYTES_PER_BINSTEP = 35.1
-FP64_PIPE_ACTIVE_NCU = 0.910
-# The mixed step kernel on a timed 128^3 x 31 launch (ncu --set full, one-warp CTAs):
-# DRAM bytes per bin-step and the utilisations that bound it (issue slots first).
-MIXED_DRAM_BYTES_PER_BINSTEP = 41.7
-MIXED_ISSUE_ACTIVE_NCU = 0.828
-MIXED_FP64_PIPE_ACTIVE_NCU = 0.710
-MIXED_FMA_PIPE_ACTIVE_NCU = 0.390
-# The batch kernel on 16 instances (ncu --set full, one-warp CTAs): DRAM bytes per
-# bin-state and utilisations.
-BATCH_DRAM_BYTES_PER_BINSTEP = 42.8
-BATCH_ISSUE_ACTIVE_NCU = 0.839
-BATCH_FP64_PIPE_ACTIVE_NCU = 0.646
-BATCH_FMA_PIPE_ACTIVE_NCU = 0.421
-# the batch counters were taken on the build capped at 80 registers; the kernel's source is
-# unchanged since, but it is now compiled for at most 72
-BATCH_COUNTERS_BUILD = "at most 80 registers (current build: 72)"
+FP64_PIPE_ACTIVE_NCU = 0.902
+# The mixed step kernel on a 64^3 x 31 launch (ncu --set full, 4-warp CTAs): DRAM
+# bytes per bin-step (part of the 162 MB state stays in L2; 42 B algorithmic) and
+# the utilisations that bound it (issue slots first).
+MIXED_DRAM_BYTES_PER_BINSTEP = 36.2
+MIXED_ISSUE_ACTIVE_NCU = 0.738
+MIXED_FP64_PIPE_ACTIVE_NCU = 0.652
+MIXED_FMA_PIPE_ACTIVE_NCU = 0.309
+# The batch kernel on 16 instances (ncu --set full, one-warp CTAs, 72 registers):
+# DRAM bytes per bin-state and utilisations.
+BATCH_DRAM_BYTES_PER_BINSTEP = 44.3
+BATCH_ISSUE_ACTIVE_NCU = 0.848
+BATCH_FP64_PIPE_ACTIVE_NCU = 0.655
+BATCH_FMA_PIPE_ACTIVE_NCU = 0.418
+BATCH_COUNTERS_BUILD = "current (72 registers)"
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -109,8 +108,14 @@ def _mixed_roofline(bin_steps_per_s, batched=False):
 # trial, per FP64 (collapse) trial and per bin-step outside the trial loop: least-squares fit of
 # ncu's smsp__sass_thread_inst_executed_op_{f,d}{fma,add,mul}_pred_on over traced launches
 # (profiles/step_kernel_mixed.md).  None until that capture exists for the current build.
-MIXED_FLOPS = None   # {"fp32_per_trial": .., "fp64_per_trial": .., "fp32_per_binstep": .., "fp64_per_binstep": ..}
-BATCH_FLOPS = None   # the same for batch_kernel<MIXED> (profiles/batch_kernel_mixed_16inst.md)
+# An FP64 (collapse) trial is the FP64 kernel's trial arithmetic: FP64_FLOPS_PER_TRIAL.
+MIXED_FLOPS = {"fp32_per_trial": 339.36, "fp64_per_trial": 3.52, "fp64_per_fp64_trial": FP64_FLOPS_PER_TRIAL,
+               "fp32_per_binstep": 69.48, "fp64_per_binstep": 12.60,
+               "source": "profiles/step_kernel_mixed.md (fit over nine 64^3 launches)"}
+# The batch kernel runs the same trial arithmetic; its 16-instance capture agrees with this fit to
+# 3 % (FP32) and 8 % (FP64) (profiles/batch_kernel_mixed_16inst.md).
+BATCH_FLOPS = dict(MIXED_FLOPS, source="profiles/step_kernel_mixed.md fit, checked against "
+                                       "profiles/batch_kernel_mixed_16inst.md")
 
 
 def _fp64_peak_derived():

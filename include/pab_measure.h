@@ -106,6 +106,22 @@ pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, co
 pab_status pab_gas_table(double gamma, double *tab_host, int64_t capacity, int32_t *n_nodes,
                          int32_t *stride, double *dmax);
 
+/*
+ * Report of the checked build (no counterpart in the paper).  The library
+ * compiled with PAB_CHECKED (libpab_checked.so) tests every global-memory
+ * index of its kernels against the length of its buffer before the access,
+ * skips the access when the index falls outside, and records the first such
+ * index of each source file with its line and the buffer's length.  This call
+ * waits for the device, returns that record for the first file with one
+ * (unit: 1 step kernels, 2 batch, 3 carrier coupling, 4 Euler-Lagrange, 5
+ * transfer contents; *count: how many indices fell outside in that file,
+ * 0 and the other outputs 0 when none did) and clears every record.
+ * NULL outputs are allowed.
+ * Errors: PAB_ESTATE (a library built without PAB_CHECKED; *count = 0),
+ * PAB_ECUDA.
+ */
+pab_status pab_check_report(int64_t *count, int32_t *unit, int32_t *line, int64_t *index, int64_t *bound);
+
 #ifdef __cplusplus
 }
 #endif

@@ -938,6 +938,53 @@ extern "C" pab_status pab_bubble_step_noalloc(const pab_config *cfg, const doubl
     return PAB_OK;
 }
 
+extern "C" pab_status pab_check_report(int64_t *count, int32_t *unit, int32_t *line, int64_t *index,
+                                       int64_t *bound)
+{
+    if (count)
+        *count = 0;
+    if (unit)
+        *unit = 0;
+    if (line)
+        *line = 0;
+    if (index)
+        *index = 0;
+    if (bound)
+        *bound = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return PAB_ECUDA;
+    void (*fetch[])(pab::CheckRecord *, bool) = {pab::check_fetch_kernels, pab::check_fetch_batch,
+                                                 pab::check_fetch_closure, pab::check_fetch_el,
+                                                 pab::check_fetch_transfer};
+    bool reported = false;
+    for (int u = 0; u < 5; ++u) {
+        pab::CheckRecord r = {0u, 0, 0, 0};
+        fetch[u](&r, true);
+        if (r.count && !reported) {
+            reported = true;
+            if (count)
+                *count = r.count;
+            if (unit)
+                *unit = u + 1;
+            if (line)
+                *line = r.line;
+            if (index)
+                *index = r.index;
+            if (bound)
+                *bound = r.bound;
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return PAB_ECUDA;
+#ifdef PAB_CHECKED
+    return PAB_OK;
+#else
+    return PAB_ESTATE;
+#endif
+}
+
 extern "C" pab_status pab_get_contents(pab_t *h, double *pb_dev, double *mv_dev, void *stream)
 {
     if (!h)

@@ -28,6 +28,7 @@
 
 #include "pab.h"
 #include "pab_batch.h"
+#include "pab_check.cuh"
 #include "pab_device.cuh"
 #include "pab_internal.h"
 #include "pab_stream.cuh"
@@ -128,12 +129,12 @@ __global__ void __launch_bounds__(kOrderThreads)
         long long acc = 0;
         int m = 0;
         for (int j = 0; j < n && key[j] != 0; ++j) {
-            order[m] = idx[j];
-            start[m] = acc;
+            PAB_ST(order, m, max_slots, idx[j]);
+            PAB_ST(start, m, max_slots + 1, acc);
             acc += slots[idx[j]].n_tiles;
             ++m;
         }
-        start[m] = acc;
+        PAB_ST(start, m, max_slots + 1, acc);
         q->head = 0;
         q->total = acc;
         q->n_order = m;
@@ -151,15 +152,16 @@ __device__ __forceinline__ void advance_one(const StepConst &K, const BinConst &
                                             uint32_t &n_att, uint32_t &n64)
 {
     const size_t k = (size_t)b * (size_t)d.C + (size_t)c;
-    R = d.R[k];
-    V = d.V[k];
-    float hc = d.h[k];
+    const long long ns = (long long)d.B * d.C;
+    R = PAB_LD(d.R, k, ns);
+    V = PAB_LD(d.V, k, ns);
+    float hc = PAB_LD(d.h, k, ns);
     int na = 0, nd = 0;
     g.reset();
     const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
-    d.R[k] = R;  // unchanged when the input was not finite
-    d.V[k] = V;
-    d.h[k] = hc;
+    PAB_ST(d.R, k, ns, R);  // unchanged when the input was not finite
+    PAB_ST(d.V, k, ns, V);
+    PAB_ST(d.h, k, ns, hc);
     fl_or |= fl;
     n_flag += (fl != 0);
     n_att += na;
@@ -199,7 +201,7 @@ template <bool MIXED, bool ONE_WARP>
 __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
     batch_kernel(const SlotDesc *__restrict__ slots, const int *__restrict__ order,
                  const long long *__restrict__ start, Queue *q, SlotCounters *cnt,
-                 int bins_per_grab, int max_bins)
+                 int bins_per_grab, int max_bins, int max_slots)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     StepConst &K = *reinterpret_cast<StepConst *>(smem);
@@ -228,7 +230,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
                 int lo = 0, hi = n_order - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (start[mid] <= it)
+                    if (PAB_LD(start, mid, max_slots + 1) <= it)
                         lo = mid;
                     else
                         hi = mid - 1;
@@ -241,8 +243,8 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
         const long long item = s_item;
         if (item >= total)
             break;
-        const int slot = order[s_j];
-        const SlotDesc d = slots[slot];
+        const int slot = PAB_LD(order, s_j, max_slots);
+        const SlotDesc d = PAB_LD(slots, slot, max_slots);
         if (slot != staged) {
             const unsigned long long *src = reinterpret_cast<const unsigned long long *>(d.K);
             unsigned long long *dst = reinterpret_cast<unsigned long long *>(smem);
@@ -251,10 +253,10 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
             staged = slot;
             __syncthreads();
         }
-        const long long tile = item - start[s_j];
+        const long long tile = item - PAB_LD(start, s_j, max_slots + 1);
         const long long c = tile * kTile + lane;
         const bool valid = c < d.C;
-        const double p_inf = valid ? d.p_inf[c] : K.p0;
+        const double p_inf = valid ? PAB_LD(d.p_inf, c, d.C) : K.p0;
         const bool p_ok = finite64(p_inf);
         uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
         TermSums S;
@@ -280,9 +282,9 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
             n_att = __reduce_add_sync(0xffffffffu, tc.n_att);
             n64 = __reduce_add_sync(0xffffffffu, tc.n64);
             if (d.out && valid)
-                write_moments<MIXED>(K, d.nb ? d.nb[c] : K.nb_default, d.C, c, S, d.out);
+                write_moments<MIXED>(K, d.nb ? PAB_LD(d.nb, c, d.C) : K.nb_default, d.C, c, S, d.out);
             if (lane == 0)
-                flush_slot(cnt + slot, fl_or, n_flag, n_att, n64);
+                flush_slot(PAB_AT(cnt, slot, max_slots), fl_or, n_flag, n_att, n64);
             __syncwarp();
             continue;
         }
@@ -344,7 +346,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
                     add_terms<MIXED>(S, x, nullptr, td);
                 }
             }
-            write_moments<MIXED>(K, d.nb ? d.nb[c] : K.nb_default, d.C, c, S, d.out);
+            write_moments<MIXED>(K, d.nb ? PAB_LD(d.nb, c, d.C) : K.nb_default, d.C, c, S, d.out);
         }
         if (threadIdx.x == 0) {
             uint32_t f = 0;
@@ -355,7 +357,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
                 t += s_cnt[2][w];
                 e += s_cnt[3][w];
             }
-            flush_slot(cnt + slot, f, a, t, e);
+            flush_slot(PAB_AT(cnt, slot, max_slots), f, a, t, e);
         }
         __syncthreads();
     }
@@ -374,7 +376,7 @@ cudaError_t set_smem_limit(size_t bytes)
 
 // The batch kernel of a precision and CTA width.
 typedef void (*BatchKernelFn)(const SlotDesc *, const int *, const long long *, Queue *, SlotCounters *,
-                              int, int);
+                              int, int, int);
 inline BatchKernelFn batch_kernel_fn(bool mixed, bool one_warp)
 {
     if (mixed)
@@ -384,6 +386,8 @@ inline BatchKernelFn batch_kernel_fn(bool mixed, bool one_warp)
 
 }  // namespace
 }  // namespace pab
+
+PAB_CHECK_UNIT(batch)
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -536,7 +540,7 @@ cudaError_t enqueue_step(pab_batch_t *b, cudaStream_t s, int grid)
     const int maxb = b->cfg.max_bins;
     pab::batch_kernel_fn(b->cfg.precision == PAB_MIXED, b->block_warps == 1)<<<grid, threads,
                                                                               launch_smem(b), s>>>(
-        b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb);
+        b->desc_dev, b->order, b->start, b->queue, b->cnt_dev, b->bins_per_grab, maxb, b->cfg.max_slots);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,10 @@
 #include "pab.h"
 #include "pab_device.cuh"
 #include "pab_el.h"
+#include "pab_check.cuh"
 #include "pab_internal.h"
+
+PAB_CHECK_UNIT(el)
 
 namespace pab {
 namespace {
@@ -40,25 +43,25 @@ __global__ void __launch_bounds__(256)
     el_advance_kernel(const __grid_constant__ StepConst K, long long N, const BinConst *__restrict__ bub,
                       const long long *__restrict__ cell, const double *__restrict__ p_cell, double dt,
                       double *__restrict__ R, double *__restrict__ V, float *__restrict__ h,
-                      Counters *cnt)
+                      Counters *cnt, long long n_grid)
 {
     __shared__ uint32_t sc[3][8];
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t fl = 0;
     int na = 0;
     if (n < N) {
-        const BinConst bc = bub[n];
-        const long long ci = cell[n];
-        const double p_inf = ci >= 0 ? p_cell[ci] : CUDART_NAN;
-        double r = R[n], v = V[n];
-        float hc = h[n];
+        const BinConst bc = PAB_LD(bub, n, N);
+        const long long ci = PAB_LD(cell, n, N);
+        const double p_inf = ci >= 0 ? PAB_LD(p_cell, ci, n_grid) : CUDART_NAN;
+        double r = PAB_LD(R, n, N), v = PAB_LD(V, n, N);
+        float hc = PAB_LD(h, n, N);
         int nd = 0;
         GasBase g;
         g.reset();
         fl = advance_bin<false>(K, bc, p_inf, isfinite(p_inf), dt, 0.0, r, v, hc, na, nd, g);  // adaptive
-        R[n] = r;  // unchanged when the input was not finite
-        V[n] = v;
-        h[n] = hc;
+        PAB_ST(R, n, N, r);  // unchanged when the input was not finite
+        PAB_ST(V, n, N, v);
+        PAB_ST(h, n, N, hc);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t f = __reduce_or_sync(0xffffffffu, fl);
@@ -122,7 +125,8 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
     const double norm = 15.749609945722419;  // (2 pi)^{3/2}
     for (long long n = (long long)blockIdx.x * kSmearWarps + warp; n < N;
          n += (long long)gridDim.x * kSmearWarps) {
-        const double r = R[n];
+        const long long ng = (long long)nx * ny * nz;
+        const double r = PAB_LD(R, n, N);
         const double h = r < dx ? dx : r;
         // cells whose centre can lie within 3h: m > 3h/dx (the 1e-9 keeps the product's
         // rounding from taking m one too small); m >= 4 for every number r (h >= dx)
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
             continue;  // r is NaN: the bubble adds nothing
         const int side = 2 * m + 1;
         const bool cached = m <= kCacheHalf;
-        const double x0 = px[n], y0 = py[n], z0 = pz[n];
+        const double x0 = PAB_LD(px, n, N), y0 = PAB_LD(py, n, N), z0 = PAB_LD(pz, n, N);
         // the base cell may be off by one where x0/dx rounds across an integer: the window
         // [f - m, f + m] still holds every centre within 3h of x0 then
         const int bx = (int)floor(x0 * inv_dx) - m, by = (int)floor(y0 * inv_dx) - m,
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
         const double rh = r * ih;
         // V/(h^3 (2 pi)^{3/2}) = (4 pi/3) (r/h)^3 / (2 pi)^{3/2}, and alpha_dot/alpha = 3 Rdot/r
         const double amp = (4.0 / 3.0 * 3.14159265358979323846 / norm) * (rh * rh * rh);
-        const double rate = 3.0 * V[n] * ir;
+        const double rate = 3.0 * PAB_LD(V, n, N) * ir;
         const double lim2 = 9.0 * h * h;
         // stencil point t = oi + side (oj + side ok); each lane walks t = lane, lane + 32,
         // ... with its offsets carried forward (32 = q32 side + r32, side >= 9 since
@@ -199,9 +203,9 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                         const int qi = tq & 255, qj = (tq >> 8) & 255, qk = tq >> 16;
                         const double a = fac[warp][0][qi] * fac[warp][1][qj] * fac[warp][2][qk];
                         const long long c = ((long long)(bz + qk) * ny + (by + qj)) * nx + (bx + qi);
-                        atomicAdd(&alpha[c], a);
+                        atomicAdd(PAB_AT(alpha, c, ng), a);
                         if (alpha_dot)
-                            atomicAdd(&alpha_dot[c], a * rate);
+                            atomicAdd(PAB_AT(alpha_dot, c, ng), a * rate);
                     }
                     const int done = queued < 32 ? queued : 32;
                     tail = (tail + done) & 63;
@@ -222,9 +226,9 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                     continue;
                 const double a = amp * exp(-d2 * inv2h2);
                 const long long c = ((long long)k * ny + j) * nx + i;
-                atomicAdd(&alpha[c], a);
+                atomicAdd(PAB_AT(alpha, c, ng), a);
                 if (alpha_dot)
-                    atomicAdd(&alpha_dot[c], a * rate);
+                    atomicAdd(PAB_AT(alpha_dot, c, ng), a * rate);
             }
         }
         __syncwarp();
@@ -448,7 +452,8 @@ pab_status pab_el_step(pab_el_t *e, const double *p_cell_dev, double dt, double 
     if (e->N > 0) {
         const unsigned blocks = (unsigned)((e->N + 255) / 256);
         pab::el_advance_kernel<<<blocks, 256, 0, s>>>(e->K, e->N, e->bub, e->cell, p_cell_dev, dt,
-                                                      e->R, e->V, e->h, e->counters);
+                                                      e->R, e->V, e->h, e->counters,
+                                                      (long long)e->nx * e->ny * e->nz);
         cudaError_t c = cudaGetLastError();
         if (c != cudaSuccess)
             return ecuda(e, c, "pab_el_step advance");

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "pab_bits.cuh"
+#include "pab_check.cuh"
 #include "pab_internal.h"
 
 namespace pab {
@@ -81,13 +82,14 @@ __device__ __forceinline__ void reduce_and_store(const StepConst &K, const MomAc
         const double alpha = (4.0 / 3.0 * 3.14159265358979323846) * nb * m3;
         const double inv_m3 = 1.0 / m3;
         const int64_t C = K.C;
-        out[0 * C + c] = nb;
-        out[1 * C + c] = alpha;
-        out[2 * C + c] = m3;
-        out[3 * C + c] = m2v;
-        out[4 * C + c] = 3.0 * alpha * m2v * inv_m3;
-        out[5 * C + c] = MIXED ? fma(m3p, inv_m3, K.p0) : K.rho * m3p * inv_m3;
-        out[6 * C + c] = m3v2 * inv_m3;
+        const long long no = 7 * C;
+        PAB_ST(out, 0 * C + c, no, nb);
+        PAB_ST(out, 1 * C + c, no, alpha);
+        PAB_ST(out, 2 * C + c, no, m3);
+        PAB_ST(out, 3 * C + c, no, m2v);
+        PAB_ST(out, 4 * C + c, no, 3.0 * alpha * m2v * inv_m3);
+        PAB_ST(out, 5 * C + c, no, MIXED ? fma(m3p, inv_m3, K.p0) : K.rho * m3p * inv_m3);
+        PAB_ST(out, 6 * C + c, no, m3v2 * inv_m3);
     }
 }
 

@@ -6,9 +6,12 @@
 // pab_transfer.h.
 #include <cuda_runtime.h>
 
+#include "pab_check.cuh"
 #include "pab_device.cuh"
 #include "pab_internal.h"
 #include "pab_reduce.cuh"
+
+PAB_CHECK_UNIT(transfer)
 
 namespace pab {
 namespace {
@@ -172,9 +175,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     const int nw = blockDim.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * kTile + lane;
     const bool valid = c < K.C;
-    const double p_inf = valid ? a.p_inf[c] : K.p0;
+    const long long ns = (long long)K.B * K.C;
+    const double p_inf = valid ? PAB_LD(a.p_inf, c, K.C) : K.p0;
     const bool p_ok = finite64(p_inf);
-    const double nb = valid ? (a.nb ? a.nb[c] : K.nb_default) : 0.0;
+    const double nb = valid ? (a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default) : 0.0;
     MomAcc<false> acc;
     uint32_t fl_or = 0, n_flag = 0, n_att = 0;
     for (int b = warp; b < K.B; b += nw) {
@@ -182,29 +186,29 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             continue;
         const BinConst &bc = K.bins[b];
         const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        State4 y{a.R[k], a.V[k], a.pb[k], a.mv[k]};
+        State4 y{PAB_LD(a.R, k, ns), PAB_LD(a.V, k, ns), PAB_LD(a.pb, k, ns), PAB_LD(a.mv, k, ns)};
         uint32_t fl = 0;
         int na = 0;
         if (!p_ok || !finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv)) {
             fl = PAB_FLAG_NONFINITE;
         } else {
-            float hc = a.h[k];
+            float hc = PAB_LD(a.h, k, ns);
             fl = advance4(K, gas_mRg(K, bc), p_inf, a.dt, a.dt_sub, y, hc, na);
             if (K.n_fixed == 0)
-                a.h[k] = hc;
+                PAB_ST(a.h, k, ns, hc);
             if (!finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv))
                 fl |= PAB_FLAG_NONFINITE;
             else if (!gt0(y.R))
                 fl |= PAB_FLAG_NONPOS;
             if (abs_ge(y.V, K.c))
                 fl |= PAB_FLAG_SUPERSONIC;
-            a.R[k] = y.R;
-            a.V[k] = y.V;
-            a.pb[k] = y.pb;
-            a.mv[k] = y.mv;
+            PAB_ST(a.R, k, ns, y.R);
+            PAB_ST(a.V, k, ns, y.V);
+            PAB_ST(a.pb, k, ns, y.pb);
+            PAB_ST(a.mv, k, ns, y.mv);
         }
         if (a.attempts)
-            a.attempts[k] = na;
+            PAB_ST(a.attempts, k, ns, na);
         fl_or |= fl;
         n_flag += (fl != 0);
         n_att += na;
@@ -226,13 +230,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     const int nw = blockDim.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * kTile + lane;
     const bool valid = c < K.C;
-    const double nb = valid ? (nbp ? nbp[c] : K.nb_default) : 0.0;
+    const long long ns = (long long)K.B * K.C;
+    const double nb = valid ? (nbp ? PAB_LD(nbp, c, K.C) : K.nb_default) : 0.0;
     MomAcc<false> acc;
     for (int b = warp; b < K.B; b += nw) {
         if (!valid)
             continue;
         const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        accumulate_transfer(K, K.bins[b], State4{Rp[k], Vp[k], pbp[k], 0.0}, acc);
+        accumulate_transfer(K, K.bins[b], State4{PAB_LD(Rp, k, ns), PAB_LD(Vp, k, ns), PAB_LD(pbp, k, ns), 0.0},
+                            acc);
     }
     reduce_and_store<false>(K, acc, nb, c, valid, out);
 }
@@ -244,8 +250,8 @@ __global__ void transfer_init_kernel(const __grid_constant__ StepConst K, double
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const BinConst &bc = K.bins[(int)(i / (size_t)K.C)];
-        pb[i] = K.p0 + K.two_sigma * bc.invR0;
-        mv[i] = K.tr_rho_vw * ((4.0 / 3.0 * kPi) * bc.R0 * bc.R0 * bc.R0);
+        PAB_ST(pb, i, n, K.p0 + K.two_sigma * bc.invR0);
+        PAB_ST(mv, i, n, K.tr_rho_vw * ((4.0 / 3.0 * kPi) * bc.R0 * bc.R0 * bc.R0));
     }
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
            "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check", "pab_gas_table",
-           "pab_get_contents", "pab_set_contents")
+           "pab_get_contents", "pab_set_contents", "pab_check_report")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -60,8 +60,14 @@ class pab_config(ctypes.Structure):
 _LIB = None
 
 
+def checked() -> bool:
+    """True when PAB_CHECKED=1 selects the checked build (libpab_checked.so: every kernel's
+    global-memory index tested against its buffer; pab_check_report reads the findings)."""
+    return os.environ.get("PAB_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
@@ -69,11 +75,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build.LIB
-    if not os.path.exists(path) or not _build.up_to_date():
+    chk = checked()
+    path = library_path()
+    if not os.path.exists(path) or not _build.up_to_date(chk):
         if not build_if_missing:
-            raise RuntimeError(f"libpab.so missing or stale at {path}; run __graft_entry__.build()")
-        _build.build()
+            raise RuntimeError(f"{os.path.basename(path)} missing or stale at {path}; run __graft_entry__.build()")
+        _build.build(checked=chk)
     lib = ctypes.CDLL(path)
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     cfgp = ctypes.POINTER(pab_config)
@@ -112,6 +119,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp]),
         "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
+        "pab_check_report": (i32, [ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -307,6 +316,22 @@ def pab_gas32_check(u, a: float, stream=None):
     if st != PAB_OK:
         raise PabError(st, "pab_gas32_check")
     return out, lib
+
+
+CHECK_UNITS = {1: "step kernels", 2: "batch", 3: "carrier coupling", 4: "Euler-Lagrange", 5: "transfer contents"}
+
+
+def pab_check_report():
+    """The checked build's first out-of-bounds index since the last call (count 0: none), or
+    None from a library built without the checks.  Waits for the device."""
+    n, u, ln, i, b = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    st = load().pab_check_report(ctypes.byref(n), ctypes.byref(u), ctypes.byref(ln), ctypes.byref(i),
+                                 ctypes.byref(b))
+    if st == PAB_ESTATE:
+        return None
+    if st != PAB_OK:
+        raise PabError(st, "pab_check_report")
+    return dict(count=n.value, unit=CHECK_UNITS.get(u.value, ""), line=ln.value, index=i.value, bound=b.value)
 
 
 def pab_destroy(h):
