@@ -4,6 +4,7 @@
 // Eq. (eos_liquid).  All are memory-bound elementwise or per-cell passes.
 #include <cuda_runtime.h>
 
+#include "pab_bits.cuh"
 #include "pab_check.cuh"
 #include "pab_internal.h"
 
@@ -29,41 +30,55 @@ __global__ void cons_from_prim_kernel(long long C, const double *__restrict__ nb
 
 // One thread per cell: the sum of w qR^3 over the bins, n_b = sqrt(4/3 pi S / alpha), then the
 // rescale of every bin.  Consecutive threads read consecutive cells of one bin row (coalesced),
-// and the bin loops are unrolled so that each thread keeps kUnroll loads in flight: a 32-cell
-// CTA whose warps walked four bins each with a dependent sum held too few bytes in flight to
-// cover HBM latency.  The second read of qR comes from L2 (a CTA's rows were just read).
+// and the bin loops are unrolled so that each thread keeps a chunk of loads in flight; the
+// second read of qR comes from L2 (a CTA's rows were just read).  The bound is GB300's FP64
+// pipe, not HBM: 3 FP64 operations per summed value, 1 per rescaled one and a few per cell,
+// against 2 per clock and SM, take longer than the 32 bytes per (bin, cell) take to stream.
 constexpr int kCellsPerCta = 256;
-constexpr int kUnroll = 8;
+constexpr int kUnroll = 8;     // rescale: qR and qV of 8 bins in flight per thread
+constexpr int kUnrollSum = 16;  // sum: qR of 16 bins in flight per thread
 __global__ void __launch_bounds__(kCellsPerCta)
     prim_from_cons_kernel(const __grid_constant__ StepConst K, const double *__restrict__ alpha,
                           const double *__restrict__ qR, const double *__restrict__ qV,
                           double *__restrict__ R, double *__restrict__ V, double *__restrict__ nb_out)
 {
+    // the weights in shared memory: read per bin by every thread, they would otherwise be indexed
+    // constant-bank loads on the sum's critical path
+    __shared__ double sw[PAB_MAX_BINS];
+    for (int b = threadIdx.x; b < K.B; b += blockDim.x)
+        sw[b] = K.bins[b].w;
+    __syncthreads();
     const long long c = (long long)blockIdx.x * kCellsPerCta + threadIdx.x;
     if (c >= K.C)
         return;
     const size_t C = (size_t)K.C;
     const long long ns = (long long)K.B * K.C;
-    // the bins in chunks of kUnroll, every load of a chunk issued before its arithmetic (the
-    // last chunk predicated), so that a thread keeps kUnroll loads in flight throughout
+    // the bins in chunks, every load of a chunk issued before its arithmetic (the last chunk
+    // predicated), so that a thread keeps a chunk of loads in flight throughout
     double s = 0.0;
-    for (int b = 0; b < K.B; b += kUnroll) {
-        double q[kUnroll];
+    for (int b = 0; b < K.B; b += kUnrollSum) {
+        double q[kUnrollSum];
 #pragma unroll
-        for (int i = 0; i < kUnroll; ++i)
+        for (int i = 0; i < kUnrollSum; ++i)
             q[i] = b + i < K.B ? PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns) : 0.0;
 #pragma unroll
-        for (int i = 0; i < kUnroll; ++i)
+        for (int i = 0; i < kUnrollSum; ++i)
             if (b + i < K.B)
-                s += K.bins[b + i].w * q[i] * q[i] * q[i];
+                s = fma(sw[b + i] * q[i], q[i] * q[i], s);
     }
-    double n = (double)NAN;
+    // n_b = sqrt(4/3 pi S / alpha) and 1/n_b from one reciprocal and one inverse square root:
+    // the kernel is bound by GB300's FP64 pipe (a multiply of each rescaled value and three
+    // operations of each summed one already match the HBM time), so an IEEE square root and two
+    // divisions per cell are worth avoiding
+    double n = (double)NAN, in = (double)NAN;
     const double a = PAB_LD(alpha, c, K.C);
-    if (a > 0.0 && a <= 1.0e300)
-        n = sqrt((4.0 / 3.0 * 3.14159265358979323846) * s / a);
+    if (a > 0.0 && a <= 1.0e300) {
+        const double x = (4.0 / 3.0 * 3.14159265358979323846) * s * rcp64(a);
+        in = rsqrt64(x);
+        n = x * in;
+    }
     if (nb_out)
         PAB_ST(nb_out, c, K.C, n);
-    const double in = 1.0 / n;
     for (int b = 0; b < K.B; b += kUnroll) {
         double qr[kUnroll], qv[kUnroll];
 #pragma unroll

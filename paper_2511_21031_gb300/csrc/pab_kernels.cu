@@ -136,16 +136,17 @@ __global__ void __maxnreg__(PAB_STEPMX_MAXNREG)
     step_body<true>(K, a);
 }
 
-// Reduce-only: one warp per tile, one lane per cell, the bins in order (the pass the step
-// kernel ends with).
+// Reduce-only: one lane per cell, the bins in order (the pass the step kernel ends with), eight
+// bins of loads in flight; 128-thread CTAs.
+constexpr int kMomThreads = 128;
 template <bool MIXED>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kMomThreads)
     moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
                    const double *R, const double *V, double *out)
 {
-    const long long c = (long long)blockIdx.x * kTile + threadIdx.x;
+    const long long c = (long long)blockIdx.x * kMomThreads + threadIdx.x;
     if (c < K.C)
-        cell_moments<MIXED>(K, R, V, K.C, c, nbp ? PAB_LD(nbp, c, K.C) : K.nb_default, out);
+        cell_moments<MIXED, 8>(K, R, V, K.C, c, nbp ? PAB_LD(nbp, c, K.C) : K.nb_default, out);
 }
 
 __global__ void init_kernel(const __grid_constant__ StepConst K, double rdot_scale, double *R,
@@ -184,11 +185,11 @@ static int sm_count()
 cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, const double *R,
                            const double *V, double *out, int /*block_warps*/, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
+    const dim3 grid((unsigned)((K.C + kMomThreads - 1) / kMomThreads));
     if (precision == PAB_MIXED)
-        moments_kernel<true><<<grid, kTile, 0, s>>>(K, nb, R, V, out);
+        moments_kernel<true><<<grid, kMomThreads, 0, s>>>(K, nb, R, V, out);
     else
-        moments_kernel<false><<<grid, kTile, 0, s>>>(K, nb, R, V, out);
+        moments_kernel<false><<<grid, kMomThreads, 0, s>>>(K, nb, R, V, out);
     return cudaGetLastError();
 }
 

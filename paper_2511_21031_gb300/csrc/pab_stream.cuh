@@ -546,13 +546,15 @@ __device__ __forceinline__ void write_moments(const StepConst &K, double nb, lon
 
 // Sums and moments of cell c over all B bins of the state (R, V), in bin order.  The state
 // is read through L2 (__ldcg): the same kernel may have written it from other lanes.
-// The loads run kMomAhead bins ahead of the arithmetic, so that a lane's dependent sums do not
-// wait on one L2 round trip per bin.
-constexpr int kMomAhead = 4;
-template <bool MIXED>
+// The loads run AHEAD bins ahead of the arithmetic, so that a lane's dependent sums do not wait
+// on one round trip per bin (4 in the step kernel's closing pass, whose reads hit L2 behind other
+// CTAs' trials; 8 in the reduce-only kernel, whose reads come from HBM).  The order of the sums
+// does not depend on it.
+template <bool MIXED, int AHEAD = 4>
 __device__ __forceinline__ void cell_moments(const StepConst &K, const double *R, const double *V,
                                              long long C, long long c, double nb, double *out)
 {
+    constexpr int kMomAhead = AHEAD;
     TermSums S;
     double rb[kMomAhead], vb[kMomAhead];
 #pragma unroll

@@ -1,15 +1,17 @@
 // The bubble source update with heat and mass transfer in the contents
 // (gas_mode PAB_GAS_TRANSFER, FP64): four states per (bin, cell), R, Rdot, the
 // bubble pressure p_b and the vapour mass m_v.  The work decomposition is the
-// one of step_kernel (a CTA owns 32 cells, its warps stride over the bins, the
-// moments are reduced in the same launch); the model is stated in
-// pab_transfer.h.
+// one of step_kernel (pab_stream.cuh: a CTA of w warps owns w tiles of 32 cells
+// and streams their (bin, cell) items lane by lane from one pool; the moments
+// come from a closing pass that sums each cell's bins in bin order); the model
+// is stated in pab_transfer.h.
 #include <cuda_runtime.h>
 
 #include "pab_check.cuh"
 #include "pab_device.cuh"
 #include "pab_internal.h"
 #include "pab_reduce.cuh"
+#include "pab_stream.cuh"
 
 PAB_CHECK_UNIT(transfer)
 
@@ -153,49 +155,117 @@ __device__ __forceinline__ uint32_t advance4(const StepConst &K, double mRg, dou
     return flags;
 }
 
-// Quadrature terms with p_bw = p_b - (4 mu Rdot + 2 sigma)/R, the pressure sum over rho.
-__device__ __forceinline__ void accumulate_transfer(const StepConst &K, const BinConst &bc,
-                                                    const State4 &y, MomAcc<false> &acc)
-{
-    const double wr2 = bc.w * y.R * y.R;
-    const double wr3 = wr2 * y.R;
-    // w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho
-    acc.add_m3(wr3);
-    acc.m2v = fma(wr2, y.V, acc.m2v);
-    acc.m3p = fma(wr3, y.pb * K.inv_rho, acc.m3p);
-    acc.m3p = fma(-wr2, fma(K.fmu_rho, y.V, K.tsig_rho), acc.m3p);
-    acc.m3v2 = fma(wr3 * y.V, y.V, acc.m3v2);
-}
+// One lane's item: the four states of one (bin, cell), with the controller of advance4.
+struct ItemT {
+    long long c;
+    size_t k;
+    double mRg, pinf_rho;
+    State4 y;
+    double h, rem;
+    int n;
+    uint32_t fl;
 
-__global__ void __launch_bounds__(kMaxWarps * 32)
-    transfer_step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
+    // The start of the flow step from the stored state; false for a non-finite input (flagged,
+    // counted, left as it is).
+    __device__ __forceinline__ bool start(const StepConst &K, const StepArgs &a, int b, long long c_,
+                                          TileCounts &tc)
+    {
+        c = c_;
+        k = (size_t)b * (size_t)K.C + (size_t)c;
+        const long long ns = (long long)K.B * K.C;
+        const double p_inf = PAB_LD(a.p_inf, c, K.C);
+        y = State4{PAB_LD(a.R, k, ns), PAB_LD(a.V, k, ns), PAB_LD(a.pb, k, ns), PAB_LD(a.mv, k, ns)};
+        n = 0;
+        fl = 0;
+        if (!finite64(p_inf) || !finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv)) {
+            if (a.attempts)
+                PAB_ST(a.attempts, k, ns, 0);
+            tc.fl_or |= PAB_FLAG_NONFINITE;
+            tc.n_flag += 1;
+            return false;
+        }
+        mRg = gas_mRg(K, K.bins[b]);
+        pinf_rho = p_inf * K.inv_rho;
+        h = start_h(PAB_LD(a.h, k, ns), a.dt);
+        rem = a.dt;
+        return true;
+    }
+
+    // One trial and the controller; true when the flow step is done.
+    __device__ __forceinline__ bool trial(const StepConst &K)
+    {
+        if (n >= K.max_attempts) {
+            fl |= PAB_FLAG_STEP_LIMIT;
+            return true;
+        }
+        bool done = false;
+        const bool last = le(rem, h);
+        const double ht = last ? rem : h;
+        const Trial4 tr = trial4(K, mRg, pinf_rho, y, ht);
+        ++n;
+        const Decision vd = decide64(K, Trial{tr.y.R, tr.y.V, tr.eR, tr.eV, tr.ok});
+        const double fac = f2d_fin(vd.fac);
+        if (vd.accept) {
+            y = tr.y;
+            if (last) {
+                const bool clipped = !le(h, rem);
+                h = (clipped && vd.fac >= 1.0f) ? h : ht * fac;
+                done = true;
+            } else {
+                rem -= ht;
+                h = ht * fac;
+            }
+        } else {
+            h = ht * fac;
+        }
+        if (!done && n >= K.max_attempts) {
+            fl |= PAB_FLAG_STEP_LIMIT;
+            done = true;
+        }
+        return done;
+    }
+
+    __device__ __forceinline__ void finish(const StepConst &K, const StepArgs &a, TileCounts &tc)
+    {
+        if (!finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv))
+            fl |= PAB_FLAG_NONFINITE;
+        else if (!gt0(y.R))
+            fl |= PAB_FLAG_NONPOS;
+        if (abs_ge(y.V, K.c))
+            fl |= PAB_FLAG_SUPERSONIC;
+        const long long ns = (long long)K.B * K.C;
+        PAB_ST(a.R, k, ns, y.R);
+        PAB_ST(a.V, k, ns, y.V);
+        PAB_ST(a.pb, k, ns, y.pb);
+        PAB_ST(a.mv, k, ns, y.mv);
+        PAB_ST(a.h, k, ns, d2f(h));
+        if (a.attempts)
+            PAB_ST(a.attempts, k, ns, n);
+        tc.fl_or |= fl;
+        tc.n_flag += (fl != 0);
+        tc.n_att += n;
+    }
+};
+
+// Fixed mode: n equal trials per item; one thread per cell walks the bins.
+__device__ __forceinline__ void transfer_fixed(const StepConst &K, const StepArgs &a, long long c0, int nc,
+                                               TileCounts &tc)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
-    const bool valid = c < K.C;
+    if ((int)threadIdx.x >= nc)
+        return;
+    const long long c = c0 + threadIdx.x;
     const long long ns = (long long)K.B * K.C;
-    const double p_inf = valid ? PAB_LD(a.p_inf, c, K.C) : K.p0;
-    const bool p_ok = finite64(p_inf);
-    const double nb = valid ? (a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default) : 0.0;
-    MomAcc<false> acc;
-    uint32_t fl_or = 0, n_flag = 0, n_att = 0;
-    for (int b = warp; b < K.B; b += nw) {
-        if (!valid)
-            continue;
-        const BinConst &bc = K.bins[b];
+    const double p_inf = PAB_LD(a.p_inf, c, K.C);
+    for (int b = 0; b < K.B; ++b) {
         const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
         State4 y{PAB_LD(a.R, k, ns), PAB_LD(a.V, k, ns), PAB_LD(a.pb, k, ns), PAB_LD(a.mv, k, ns)};
         uint32_t fl = 0;
         int na = 0;
-        if (!p_ok || !finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv)) {
+        if (!finite64(p_inf) || !finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv)) {
             fl = PAB_FLAG_NONFINITE;
         } else {
-            float hc = PAB_LD(a.h, k, ns);
-            fl = advance4(K, gas_mRg(K, bc), p_inf, a.dt, a.dt_sub, y, hc, na);
-            if (K.n_fixed == 0)
-                PAB_ST(a.h, k, ns, hc);
+            float hc = 0.0f;
+            fl = advance4(K, gas_mRg(K, K.bins[b]), p_inf, a.dt, a.dt_sub, y, hc, na);
             if (!finite64(y.R) || !finite64(y.V) || !finite64(y.pb) || !finite64(y.mv))
                 fl |= PAB_FLAG_NONFINITE;
             else if (!gt0(y.R))
@@ -209,38 +279,97 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         }
         if (a.attempts)
             PAB_ST(a.attempts, k, ns, na);
-        fl_or |= fl;
-        n_flag += (fl != 0);
-        n_att += na;
-        if (a.out)
-            accumulate_transfer(K, bc, y, acc);
+        tc.fl_or |= fl;
+        tc.n_flag += (fl != 0);
+        tc.n_att += na;
     }
-    if (a.out)
-        reduce_and_store<false>(K, acc, nb, c, valid, a.out);
-    flush_counters(fl_or, n_flag, n_att, 0u, a.counters);
 }
 
-__global__ void __launch_bounds__(kMaxWarps * 32)
-    transfer_moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
-                            const double *__restrict__ Rp, const double *__restrict__ Vp,
-                            const double *__restrict__ pbp, double *__restrict__ out)
+// The moments of cell c from the four-state contents, its bins summed in bin order (FP64), with
+// p_bw = p_b - (4 mu Rdot + 2 sigma)/R and the pressure sum over rho.
+__device__ __forceinline__ void transfer_cell_moments(const StepConst &K, const double *R, const double *V,
+                                                      const double *pb, long long c, double nb, double *out)
 {
+    const long long ns = (long long)K.B * K.C;
+    TermSums S;
+    for (int b = 0; b < K.B; ++b) {
+        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
+        const double r = PAB_LDCG(R, k, ns), v = PAB_LDCG(V, k, ns), p = PAB_LDCG(pb, k, ns);
+        const double w = K.bins[b].w;
+        const double wr2 = __dmul_rn(__dmul_rn(w, r), r);
+        const double wr3 = __dmul_rn(wr2, r);
+        const double t[3] = {__dmul_rn(wr2, v),
+                             fma(wr3, p * K.inv_rho, -__dmul_rn(wr2, fma(K.fmu_rho, v, K.tsig_rho))),
+                             __dmul_rn(__dmul_rn(wr3, v), v)};
+        add_terms<false>(S, wr3, nullptr, t);
+    }
+    write_moments<false>(K, nb, K.C, c, S, out);
+}
+
+// One CTA of nw warps owns nw tiles (32 nw cells) and streams their items lane by lane.
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    transfer_step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    __shared__ PoolCounters sh;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * kTile + lane;
-    const bool valid = c < K.C;
-    const long long ns = (long long)K.B * K.C;
-    const double nb = valid ? (nbp ? PAB_LD(nbp, c, K.C) : K.nb_default) : 0.0;
-    MomAcc<false> acc;
-    for (int b = warp; b < K.B; b += nw) {
-        if (!valid)
-            continue;
-        const size_t k = (size_t)b * (size_t)K.C + (size_t)c;
-        accumulate_transfer(K, K.bins[b], State4{PAB_LD(Rp, k, ns), PAB_LD(Vp, k, ns), PAB_LD(pbp, k, ns), 0.0},
-                            acc);
+    const long long c0 = (long long)blockIdx.x * kTile * nw;
+    const int nc = (int)min((long long)kTile * nw, K.C - c0);
+    TileCounts tc;
+    if (K.n_fixed > 0) {
+        transfer_fixed(K, a, c0, nc, tc);
+    } else {
+        if (threadIdx.x == 0)
+            sh = PoolCounters{0, 0, 0};
+        __syncthreads();
+        TileIO io;  // the pool's layout (item j: bin j / nc, cell c0 + j mod nc)
+        io.C = K.C;
+        io.c0 = c0;
+        io.nc = nc;
+        io.b0 = 0;
+        io.b1 = K.B;
+        const int total = K.B * nc;
+        bool exhausted = total <= 0;
+        bool have = false;
+        ItemT it;
+        for (;;) {
+            const unsigned want = __ballot_sync(0xffffffffu, !have);
+            if (want && !exhausted) {
+                const int j = grab(want, total, &sh.next, exhausted);
+                if (j >= 0 && j < total) {
+                    int b, cl;
+                    size_t k;
+                    item_of(io, j, b, cl, k);
+                    have = it.start(K, a, b, c0 + cl, tc);
+                }
+            }
+            if (!__any_sync(0xffffffffu, have)) {
+                if (exhausted)
+                    break;
+                continue;
+            }
+            if (have && it.trial(K)) {
+                it.finish(K, a, tc);
+                have = false;
+            }
+        }
     }
-    reduce_and_store<false>(K, acc, nb, c, valid, out);
+    // block-wide counters; the barrier inside orders the state writes before the reads below
+    flush_counters(tc.fl_or, tc.n_flag, tc.n_att, 0u, a.counters);
+    const long long c = c0 + (long long)kTile * warp + lane;
+    if (a.out && c < c0 + nc)
+        transfer_cell_moments(K, a.R, a.V, a.pb, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out);
+}
+
+// Reduce-only: one lane per cell, the closing pass of the step kernel.
+__global__ void __launch_bounds__(128)
+    transfer_moments_kernel(const __grid_constant__ StepConst K, const double *__restrict__ nbp,
+                            const double *Rp, const double *Vp, const double *pbp, double *out)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < K.C)
+        transfer_cell_moments(K, Rp, Vp, pbp, c, nbp ? PAB_LD(nbp, c, K.C) : K.nb_default, out);
 }
 
 // Equilibrium contents: p_b = p0 + 2 sigma/R0, m_v = (pv/(R_v T_w)) V0.
@@ -261,9 +390,10 @@ cudaError_t launch_transfer_step(const StepConst &K, const StepArgs &a, int bloc
 {
     if (!a.pb || !a.mv || !a.h)
         return cudaErrorInvalidValue;
-    const int nw = clamp_warps(block_warps, K.B);
-    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    transfer_step_kernel<<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, a);
+    const int nw = block_warps <= 0 ? kDefaultWarps : (block_warps > kMaxWarps ? kMaxWarps : block_warps);
+    const long long cells = (long long)kTile * nw;
+    const dim3 grid((unsigned)((K.C + cells - 1) / cells));
+    transfer_step_kernel<<<grid, nw * 32, 0, s>>>(K, a);
     return cudaGetLastError();
 }
 
@@ -271,9 +401,9 @@ cudaError_t launch_transfer_moments(const StepConst &K, const double *nb, const 
                                     const double *V, const double *pb, double *out, int block_warps,
                                     cudaStream_t s)
 {
-    const int nw = clamp_warps(block_warps, K.B);
-    const dim3 grid((unsigned)((K.C + kTile - 1) / kTile));
-    transfer_moments_kernel<<<grid, nw * 32, reduce_smem_bytes(nw), s>>>(K, nb, R, V, pb, out);
+    (void)block_warps;
+    const dim3 grid((unsigned)((K.C + 127) / 128));
+    transfer_moments_kernel<<<grid, 128, 0, s>>>(K, nb, R, V, pb, out);
     return cudaGetLastError();
 }
 

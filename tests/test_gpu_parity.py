@@ -349,3 +349,53 @@ def test_calls_on_other_streams_give_the_create_streams_bits():
     assert a.status(stream=s_create)["n_attempts"] == b.status(stream=legacy)["n_attempts"]
     a.close()
     b.close()
+
+
+def test_mixed_parked_items_and_lot_overflow_give_the_same_bits_in_every_launch_shape():
+    """Every bin starts near collapse (R = 0.18 R0, below the FP64 threshold of 0.2 R0), so every
+    item parks in its CTA's lot (32 per warp) until the lot is full and the rest take their FP64
+    trials where they are (5000 cells: 157 tiles, no split by bins); the state and moments are the
+    same bits for CTAs of 1, 4 and 16 warps, and match the oracle at the adaptive tolerance."""
+    import torch
+    wl = workloads.config_small().subset(np.arange(5000) % 64)
+    wl.n_bins = 31
+    wl.s = 0.5
+    R0, _ = oracle.bins(wl.n_bins, wl.R0ref, wl.s, wl.span_K)
+    R = np.repeat(0.18 * R0[:, None], wl.n_cells, axis=1)
+    V = np.zeros_like(R)
+    h = np.zeros(R.shape, dtype=np.float32)
+    steps = 3
+    outs = []
+    for bw in (1, 4, 16):
+        s = pab.Solver(wl.n_cells, wl.n_bins, precision="mixed", s_lognormal=wl.s, R0ref=wl.R0ref,
+                       span_K=wl.span_K, alpha0=wl.alpha0, **wl.fluid)
+        s.set_block_warps(bw)
+        s.set_state(torch.as_tensor(R, device="cuda"), torch.as_tensor(V, device="cuda"),
+                    torch.as_tensor(h, device="cuda"))
+        g = run_gpu(wl, steps, solver=s, record=False)
+        assert g["status"]["n_fp64"] > 0 and g["status"]["flags"] == 0
+        outs.append(g)
+        s.close()
+    for g in outs[1:]:
+        for k in ("R", "V", "h", "moments"):
+            np.testing.assert_array_equal(g[k], outs[0][k])
+    o = run_oracle(wl, steps, state=(R, V, h))
+    assert rel_err_R(outs[0]["R"], o["R"]) <= TOL_ADAPT
+    assert rel_err_V(outs[0]["V"], o["V"], wl.fluid) <= TOL_ADAPT
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_grid_split_by_bins_gives_the_bits_of_a_large_grid(precision):
+    """A grid of fewer tiles than SMs is split by bins over more CTAs, its moments from the
+    reduce-only kernel; the same cells inside a large grid (one CTA per 128 cells, moments from the
+    closing pass) give the same state and moments, bit for bit."""
+    big = workloads.config_grid128(edge=32)               # 32768 cells: 256 CTAs
+    small = big.subset(np.arange(96))                      # 96 cells: 3 tiles, split by bins
+    n = 30
+    ps = [big.pressure_step(k) for k in range(n)]
+    gb = run_gpu(big, n, pressures=ps, precision=precision, record=False)
+    gs = run_gpu(small, n, pressures=[p[:96] for p in ps], precision=precision, record=False)
+    np.testing.assert_array_equal(gs["R"], gb["R"][:, :96])
+    np.testing.assert_array_equal(gs["V"], gb["V"][:, :96])
+    np.testing.assert_array_equal(gs["h"], gb["h"][:, :96])
+    np.testing.assert_array_equal(gs["moments"], gb["moments"][:, :96])
