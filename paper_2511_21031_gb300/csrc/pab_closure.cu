@@ -53,18 +53,32 @@ __global__ void __launch_bounds__(kCellsPerCta)
         return;
     const size_t C = (size_t)K.C;
     const long long ns = (long long)K.B * K.C;
-    // the bins in chunks, every load of a chunk issued before its arithmetic (the last chunk
-    // predicated), so that a thread keeps a chunk of loads in flight throughout
+    // the bins in whole chunks, every load of a chunk issued before its arithmetic, then the rest
+    // in fours and ones (a predicated last chunk would run its FP64 operations for the missing
+    // bins too)
     double s = 0.0;
-    for (int b = 0; b < K.B; b += kUnrollSum) {
+    int b = 0;
+    for (; b + kUnrollSum <= K.B; b += kUnrollSum) {
         double q[kUnrollSum];
 #pragma unroll
         for (int i = 0; i < kUnrollSum; ++i)
-            q[i] = b + i < K.B ? PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns) : 0.0;
+            q[i] = PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns);
 #pragma unroll
         for (int i = 0; i < kUnrollSum; ++i)
-            if (b + i < K.B)
-                s = fma(sw[b + i] * q[i], q[i] * q[i], s);
+            s = fma(sw[b + i] * q[i], q[i] * q[i], s);
+    }
+    for (; b + 4 <= K.B; b += 4) {
+        double q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            q[i] = PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            s = fma(sw[b + i] * q[i], q[i] * q[i], s);
+    }
+    for (; b < K.B; ++b) {
+        const double q = PAB_LD(qR, (size_t)b * C + (size_t)c, ns);
+        s = fma(sw[b] * q, q * q, s);
     }
     // n_b = sqrt(4/3 pi S / alpha) and 1/n_b from one reciprocal and one inverse square root:
     // the kernel is bound by GB300's FP64 pipe (a multiply of each rescaled value and three
@@ -79,22 +93,27 @@ __global__ void __launch_bounds__(kCellsPerCta)
     }
     if (nb_out)
         PAB_ST(nb_out, c, K.C, n);
-    for (int b = 0; b < K.B; b += kUnroll) {
+    b = 0;
+    for (; b + kUnroll <= K.B; b += kUnroll) {
         double qr[kUnroll], qv[kUnroll];
 #pragma unroll
         for (int i = 0; i < kUnroll; ++i) {
             const size_t k = (size_t)(b + i) * C + (size_t)c;
-            qr[i] = b + i < K.B ? PAB_LD(qR, k, ns) : 0.0;
-            qv[i] = b + i < K.B ? PAB_LD(qV, k, ns) : 0.0;
+            qr[i] = PAB_LD(qR, k, ns);
+            qv[i] = PAB_LD(qV, k, ns);
         }
 #pragma unroll
         for (int i = 0; i < kUnroll; ++i) {
             const size_t k = (size_t)(b + i) * C + (size_t)c;
-            if (b + i < K.B) {
-                PAB_ST(R, k, ns, qr[i] * in);
-                PAB_ST(V, k, ns, qv[i] * in);
-            }
+            PAB_ST(R, k, ns, qr[i] * in);
+            PAB_ST(V, k, ns, qv[i] * in);
         }
+    }
+    for (; b < K.B; ++b) {
+        const size_t k = (size_t)b * C + (size_t)c;
+        const double qr = PAB_LD(qR, k, ns), qv = PAB_LD(qV, k, ns);
+        PAB_ST(R, k, ns, qr * in);
+        PAB_ST(V, k, ns, qv * in);
     }
 }
 
