@@ -446,15 +446,17 @@ def _bench_transfer(args, stream, dev, fp64_value):
             "parity": "tests/test_gpu_transfer.py (against the oracle)"}
 
 
-def _bench_batched(args, stream, dev, n_instances=512):
+def _bench_batched(args, stream, dev, n_instances=512, insts=None, name=None):
     """512 independent instances (edge U{16..96}, Nb in {11,21,31,51}, amplitude
     U(0.3,1.5) p0, s U(0.2,0.7)) in one persistent mixed-precision launch per
-    step, replayed from a CUDA graph, launch shape from the autotuner."""
+    step, replayed from a CUDA graph, launch shape from the autotuner.  Given
+    `insts` (instances sharing one forcing frequency and step), those instead."""
     import torch
 
     from paper_2511_21031_gb300 import autotune
     from paper_2511_21031_gb300.batch import Batch
-    insts = workloads.batched_instances(n=n_instances)
+    if insts is None:
+        insts = workloads.batched_instances(n=n_instances)
     if getattr(args, "batch_launch", None):
         # profiling aid: a fixed launch shape instead of the autotuner's
         w_, c_, g_ = args.batch_launch
@@ -518,7 +520,7 @@ def _bench_batched(args, stream, dev, n_instances=512):
     b.close()
     del ps, mom
     torch.cuda.synchronize()
-    return {"workload": f"batched {len(insts)} instances", "label": "batched mixed (graph)",
+    return {"workload": name or f"batched {len(insts)} instances", "label": "batched mixed (graph)",
             "precision": "mixed", "instances": len(insts), "cells": cells, "bins": bins,
             "value": bins * args.steps / (sum(ms) * 1e-3), "unit": "bin-steps/s",
             "ms_per_step": sum(ms) / args.steps,
@@ -906,6 +908,8 @@ def _summary(line):
             e["tr"] = g(v["trials_per_bin_step"])
         if v.get("fp64_trial_fraction"):
             e["f64"] = g(v["fp64_trial_fraction"])
+        if v.get("vs_single_instance_same_work") is not None:
+            e["vs1"] = g(v["vs_single_instance_same_work"])
         r = v.get("roofline") or {}
         for k_src, k_dst in (("frac", "frac"), ("fp64_frac", "f64frac"), ("fp32_frac", "f32frac")):
             if r.get(k_src) is not None:
@@ -1066,10 +1070,25 @@ def run_ours(args):
                                                  bv["fp64_trial_fraction"], batched=True)
         return bv
 
+    def batched_slices():
+        # the batch on exactly the single-instance mixed line's work: the 128^3 grid cut into
+        # 512 instances of 16^3 cells, so the ratio of the two rates is the batch's own cost
+        n = 512 if wl.n_cells % 512 == 0 else 1
+        insts = workloads.sliced_instances(wl, n)
+        bv = _bench_batched(args, stream, dev, insts=insts,
+                            name=f"batched {n} slices of {wl.name.replace('_fp64', '_mixed')}")
+        single = next((v for v in variants if v.get("label") == "grid128 mixed"
+                       and "value" in v), None)
+        bv["vs_single_instance_same_work"] = bv["value"] / single["value"] if single else None
+        bv["roofline"] = _mixed_compute_roofline(bv["value"], bv["trials_per_bin_step"],
+                                                 bv["fp64_trial_fraction"], batched=True)
+        return bv
+
     if args.variants and args.transfer and ws == 1:
         extra("transfer", lambda: _bench_transfer(args, stream, dev, value))
     if args.variants and args.batched and ws == 1:
         extra("batched", batched)
+        extra("batched slices", batched_slices)
     if args.variants and args.el and ws == 1:
         extra("el", lambda: _bench_el(args, stream, dev))
     if args.variants and args.closure and ws == 1:

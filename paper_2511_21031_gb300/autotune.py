@@ -62,6 +62,26 @@ def _time_events(fn, n):
     return a.elapsed_time(b) / n
 
 
+# The sample must hold enough 32-cell tiles to give every resident warp several tiles, as the
+# real batch does: a sample that leaves SMs idle under one-warp CTAs (one tile per CTA at a
+# time) favours wide CTAs that split a tile's bins between their warps.
+TILES_PER_RESIDENT_WARP = 8
+MAX_WARPS_PER_SM = 64
+
+
+def sample_instances(instances, sample, min_tiles, seed=0):
+    """Indices of the tuning sample: at least `sample` instances drawn in a seeded order, and more
+    until their tiles reach `min_tiles` (or every instance is in)."""
+    order = np.random.default_rng(seed).permutation(len(instances))
+    pick, tiles = [], 0
+    for i in order:
+        if len(pick) >= sample and tiles >= min_tiles:
+            break
+        pick.append(int(i))
+        tiles += -(-instances[int(i)].n_cells // 32)
+    return sorted(pick)
+
+
 def tune_batch(instances, precision="mixed", sample=24, steps=2, warmup=1, seed=0,
                cache_path=DEFAULT_CACHE, candidates=BATCH_CANDIDATES, use_cache=True, verbose=False):
     """Pick (block_warps, ctas_per_sm, bins_per_grab) for a batch of these instances."""
@@ -72,10 +92,11 @@ def tune_batch(instances, precision="mixed", sample=24, steps=2, warmup=1, seed=
     cache = _load(cache_path) if use_cache else {}
     if use_cache and key in cache:
         return dict(cache[key], cached=True)
-    g = np.random.default_rng(seed)
-    pick = sorted(g.choice(len(instances), min(sample, len(instances)), replace=False))
-    insts = [instances[i] for i in pick]
     dev = torch.device("cuda", torch.cuda.current_device())
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    warps = min(MAX_WARPS_PER_SM, max(c * w for w, c, _ in candidates))
+    pick = sample_instances(instances, sample, TILES_PER_RESIDENT_WARP * warps * n_sm, seed)
+    insts = [instances[i] for i in pick]
     bins = sum(w.n_cells * w.n_bins for w in insts)
     b = Batch(max_slots=len(insts), precision=precision, capacity_bins=bins,
               max_bins=max(w.n_bins for w in insts))

@@ -155,6 +155,16 @@ def batched_instances(n: int = 512, seed: int = 4, edge_lo: int = 16, edge_hi: i
     return out
 
 
+def sliced_instances(wl: Workload, n: int, precision: str = "mixed") -> List[Workload]:
+    """The workload's cells cut into n contiguous, equal instances (the same forcing, bins and
+    steps): a batch of them does exactly the single instance's work."""
+    if n <= 0 or wl.n_cells % n:
+        raise ValueError("n must divide the workload's cell count")
+    m = wl.n_cells // n
+    return [dataclasses.replace(wl.subset(np.arange(i * m, (i + 1) * m), name=f"{wl.name}[slice {i}]"),
+                                precision=precision) for i in range(n)]
+
+
 @dataclasses.dataclass
 class Request:
     rid: int

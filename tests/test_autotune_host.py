@@ -1,6 +1,7 @@
 """Host logic of the launch-shape autotuner on the CPU: the cache key names the GPU, the
 precision, the Nb mix and the size class of the work; the cache file is replaced atomically
-and survives a damaged file; a cached choice is returned without timing anything."""
+and survives a damaged file; a cached choice is returned without timing anything; the tuning
+sample holds enough tiles to fill the GPU."""
 import json
 
 from paper_2511_21031_gb300 import autotune, workloads
@@ -50,3 +51,15 @@ def test_candidate_sets_are_within_the_library_ranges():
         assert 1 <= w <= 16 and 1 <= c <= 32 and 1 <= g <= 8
     assert len(set(autotune.BATCH_CANDIDATES)) == len(autotune.BATCH_CANDIDATES) == 28
     assert all(1 <= w <= 16 for w in autotune.SOLVER_CANDIDATES)
+
+
+def test_tuning_sample_grows_until_it_holds_enough_tiles():
+    wl = workloads.config_grid128(edge=32)
+    slices = workloads.sliced_instances(wl, 64)                  # 512 cells = 16 tiles each
+    pick = autotune.sample_instances(slices, 4, 200, seed=1)
+    assert len(pick) == 13 and pick == sorted(set(pick))         # ceil(200 / 16) instances
+    small = autotune.sample_instances(slices, 4, 10, seed=1)
+    assert len(small) == 4 and set(small) <= set(pick)           # the count floor, same order
+    assert len(autotune.sample_instances(slices, 4, 10 ** 9, seed=1)) == 64  # all of them
+    big = _insts()
+    assert len(autotune.sample_instances(big, 3, 0, seed=2)) == 3

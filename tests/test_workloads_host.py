@@ -73,6 +73,17 @@ def test_batched_instances_span_their_ranges():
     assert len({w.seed for w in insts}) == len(insts)
 
 
+def test_sliced_instances_cover_the_workload_in_order():
+    wl = workloads.config_grid128(edge=16)
+    insts = workloads.sliced_instances(wl, 8)
+    assert len(insts) == 8 and all(w.n_cells == 512 for w in insts)
+    assert np.array_equal(np.concatenate([w.theta for w in insts]), wl.theta)
+    assert all(w.precision == "mixed" and (w.n_bins, w.s, w.dt, w.amp, w.freq)
+               == (wl.n_bins, wl.s, wl.dt, wl.amp, wl.freq) for w in insts)
+    with pytest.raises(ValueError):
+        workloads.sliced_instances(wl, 7)
+
+
 def test_request_stream_is_poisson_with_clipped_lognormal_edges():
     reqs = workloads.request_stream(n=4000, rate=200.0)
     t = np.array([r.arrival for r in reqs])
