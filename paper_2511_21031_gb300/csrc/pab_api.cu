@@ -28,6 +28,8 @@ struct pab_s {
     double *V = nullptr;
     float *h = nullptr;
     int32_t *attempts = nullptr;
+    double *terms = nullptr;    // [4][Nb][C] quadrature terms of a grid split by bins
+    unsigned int *tickets = nullptr;  // [tiles] its per-tile counters (zero between steps)
     double *gas_tab = nullptr;  // gas-term nodes (K.gas_tab points here)
     double *pb = nullptr;       // [Nb][C] bubble pressure (PAB_GAS_TRANSFER)
     double *mv = nullptr;       // [Nb][C] vapour mass (PAB_GAS_TRANSFER)
@@ -409,6 +411,17 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
         e = cudaMallocAsync((void **)&h->h, n * sizeof(float), s);
     if (e == cudaSuccess && cfg->record_attempts)
         e = cudaMallocAsync((void **)&h->attempts, n * sizeof(int32_t), s);
+    // a small grid's step is split by bins over more CTAs, which store their items' quadrature
+    // terms and count off each tile (at most 32 x SMs cells x 63 bins x 32 bytes, under 10 MB on
+    // 152 SMs)
+    const bool split = cfg->gas_mode != PAB_GAS_TRANSFER && pab::step_splits_by_bins(h->K);
+    const size_t n_tiles = (size_t)((cfg->n_cells + 31) / 32);
+    if (e == cudaSuccess && split)
+        e = cudaMallocAsync((void **)&h->terms, 4 * n * sizeof(double), s);
+    if (e == cudaSuccess && split)
+        e = cudaMallocAsync((void **)&h->tickets, n_tiles * sizeof(unsigned int), s);
+    if (e == cudaSuccess && split)
+        e = cudaMemsetAsync(h->tickets, 0, n_tiles * sizeof(unsigned int), s);
     if (e == cudaSuccess)
         e = cudaMallocAsync((void **)&h->counters, sizeof(pab::Counters), s);
     if (e == cudaSuccess)
@@ -465,7 +478,7 @@ void pab_destroy(pab_t *h)
         if (h->ev_out[i])
             cudaEventSynchronize(h->ev_out[i]);
     }
-    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
+    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->terms, h->tickets, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
                     h->stage_nb, h->stage_out, h->pipe_p[0], h->pipe_p[1], h->pipe_nb[0], h->pipe_nb[1],
                     h->pipe_out[0], h->pipe_out[1]};
     for (void *b : bufs)
@@ -507,6 +520,8 @@ pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_d
     a.V = h->V;
     a.h = h->h;
     a.attempts = h->attempts;
+    a.terms = h->terms;
+    a.tickets = h->tickets;
     a.out = moments_dev;
     a.counters = h->counters;
     a.pb = h->pb;

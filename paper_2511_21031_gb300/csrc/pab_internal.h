@@ -125,6 +125,11 @@ struct StepArgs {
     double dt_sub = 0.0;   // dt / n_fixed in fixed mode (formed on the host)
     double *pb = nullptr;  // [B][C] bubble pressure (PAB_GAS_TRANSFER)
     double *mv = nullptr;  // [B][C] vapour mass (PAB_GAS_TRANSFER)
+    // A grid split by bins (step_splits_by_bins) ends with its moments when both are given:
+    // terms, [4][B][C] doubles for its items' quadrature terms, and tickets, one zeroed counter
+    // per 32-cell tile (left zeroed).  Without them its moments come from a second launch.
+    double *terms = nullptr;
+    unsigned int *tickets = nullptr;
 };
 
 // The first out-of-bounds index a checked build (PAB_CHECKED, pab_check.cuh) met in one
@@ -157,6 +162,9 @@ cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, in
                         cudaStream_t s);
 cudaError_t launch_moments(const StepConst &K, int precision, const double *nb, const double *R,
                            const double *V, double *out, int block_warps, cudaStream_t s);
+// True when launch_step splits this grid by bins over more CTAs (fewer 32-cell tiles than the
+// current device's SMs, more than one bin): its moments then come from a second launch.
+bool step_splits_by_bins(const StepConst &K);
 cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,
                         float *h, cudaStream_t s);
 // Contents with transfer (pab_transfer.cu): the step, the moments and the equilibrium

@@ -2,7 +2,8 @@
 //
 // Work decomposition: a CTA owns a tile of 32 consecutive cells and a range of
 // their bins (all Nb bins, except where a small grid is split over more SMs:
-// then a range per CTA, the moments from a second launch).  Its warps advance
+// then a range per CTA, and the last CTA of a tile to finish sums its moments
+// from terms the others stored).  Its warps advance
 // the tile's (bin, cell) items lane by lane (pab_stream.cuh): bin-major, so the
 // loads and stores of the bin-major state stay coalesced while the lanes run
 // together, and a lane that finishes an item takes the next one instead of
@@ -69,11 +70,47 @@ __device__ __forceinline__ void fixed_items(const StepConst &K, const StepArgs &
     }
 }
 
+// The moments of a grid split by bins (gridDim.y CTAs per tile, one per bin range), without a
+// second launch.  Each CTA writes the quadrature terms of its items from their new state (every
+// lane at once, after the items: computed where an item finishes they would hold up the warp's
+// other lanes once per finishing item), then takes a ticket of its tile; the CTA that takes the
+// last one sums the tile's terms in bin order and writes its moments (the arithmetic and order
+// of cell_moments, so the bits of an unsplit launch), and resets the ticket for the next step.
+// No CTA waits for another.
+template <bool MIXED>
+__device__ __forceinline__ void split_moments(const StepConst &K, const StepArgs &a, const TileIO &io)
+{
+    __shared__ unsigned int s_last;
+    const long long ns = (long long)K.B * K.C;
+    const int n_items = (io.b1 - io.b0) * io.nc;
+    for (int j = threadIdx.x; j < n_items; j += blockDim.x) {
+        int b, cl;
+        size_t k;
+        item_of(io, j, b, cl, k);
+        store_terms<MIXED>(K, a.terms, b, k, PAB_LDCG(a.R, k, ns), PAB_LDCG(a.V, k, ns));
+    }
+    __threadfence();
+    __syncthreads();
+    const long long tiles = (K.C + kTile - 1) / kTile;
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(PAB_AT(a.tickets, (long long)blockIdx.x, tiles), 1u) == gridDim.y - 1;
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    for (int cl = threadIdx.x; cl < io.nc; cl += blockDim.x) {
+        const long long c = io.c0 + cl;
+        sum_cell_terms<MIXED>(K, a.terms, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out);
+    }
+    if (threadIdx.x == 0)
+        *PAB_AT(a.tickets, (long long)blockIdx.x, tiles) = 0u;
+}
+
 // One CTA of nw warps.  With one bin range (gridDim.y == 1) it owns nw tiles (32 nw cells from
 // blockIdx.x * 32 nw) and all their bins, and ends with their moments (warp w: tile w);
 // otherwise one tile (blockIdx.x) and bin range blockIdx.y.  Dynamic shared memory: the lot of
 // parked items (32 per warp) in adaptive mixed precision, nothing otherwise.
-template <bool MIXED>
+template <bool MIXED, bool TERMS>
 __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -113,6 +150,8 @@ __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
     const long long c = io.c0 + (long long)kTile * warp + lane;
     if (a.out && gridDim.y == 1 && c < io.c0 + io.nc)
         cell_moments<MIXED>(K, a.R, a.V, K.C, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out);
+    if (TERMS)
+        split_moments<MIXED>(K, a, io);
 }
 
 #ifndef PAB_STEP64_MAXNREG
@@ -121,19 +160,31 @@ __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
 #ifndef PAB_STEPMX_MAXNREG
 #define PAB_STEPMX_MAXNREG 64
 #endif
-template <bool MIXED>
+template <bool MIXED, bool TERMS>
 __global__ void step_kernel(const __grid_constant__ StepConst K, const StepArgs a);
 template <>
 __global__ void __maxnreg__(PAB_STEP64_MAXNREG)
-    step_kernel<false>(const __grid_constant__ StepConst K, const StepArgs a)
+    step_kernel<false, false>(const __grid_constant__ StepConst K, const StepArgs a)
 {
-    step_body<false>(K, a);
+    step_body<false, false>(K, a);
 }
 template <>
 __global__ void __maxnreg__(PAB_STEPMX_MAXNREG)
-    step_kernel<true>(const __grid_constant__ StepConst K, const StepArgs a)
+    step_kernel<true, false>(const __grid_constant__ StepConst K, const StepArgs a)
 {
-    step_body<true>(K, a);
+    step_body<true, false>(K, a);
+}
+template <>
+__global__ void __maxnreg__(PAB_STEP64_MAXNREG)
+    step_kernel<false, true>(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    step_body<false, true>(K, a);
+}
+template <>
+__global__ void __maxnreg__(PAB_STEPMX_MAXNREG)
+    step_kernel<true, true>(const __grid_constant__ StepConst K, const StepArgs a)
+{
+    step_body<true, true>(K, a);
 }
 
 // Reduce-only: one lane per cell, the bins in order (the pass the step kernel ends with), eight
@@ -215,14 +266,29 @@ cudaError_t launch_step(const StepConst &K, int precision, const StepArgs &a, in
     const dim3 grid((unsigned)ctas, (unsigned)groups);
     const bool mixed_adaptive = precision == PAB_MIXED && K.n_fixed == 0;
     const size_t smem = mixed_adaptive ? lot_bytes(kLotPerWarp * nw) : 0;
-    if (precision == PAB_MIXED)
-        step_kernel<true><<<grid, nw * 32, smem, s>>>(K, a);
-    else
-        step_kernel<false><<<grid, nw * 32, smem, s>>>(K, a);
+    // a split grid with a terms buffer and tickets ends with its moments (split_moments)
+    const bool terms = groups > 1 && a.out && a.terms && a.tickets;
+    if (precision == PAB_MIXED) {
+        if (terms)
+            step_kernel<true, true><<<grid, nw * 32, smem, s>>>(K, a);
+        else
+            step_kernel<true, false><<<grid, nw * 32, smem, s>>>(K, a);
+    } else {
+        if (terms)
+            step_kernel<false, true><<<grid, nw * 32, smem, s>>>(K, a);
+        else
+            step_kernel<false, false><<<grid, nw * 32, smem, s>>>(K, a);
+    }
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && groups > 1 && a.out)
+    if (e == cudaSuccess && groups > 1 && a.out && !terms)
         e = launch_moments(K, precision, a.nb, a.R, a.V, a.out, 0, s);
     return e;
+}
+
+bool step_splits_by_bins(const StepConst &K)
+{
+    const long long tiles = (K.C + kTile - 1) / kTile;
+    return tiles < sm_count() && K.B > 1;
 }
 
 cudaError_t launch_init(const StepConst &K, double Rdot0_ref, double R0ref, double *R, double *V,

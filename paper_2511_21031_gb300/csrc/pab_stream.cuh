@@ -612,4 +612,68 @@ __device__ __forceinline__ void add_bin_terms(const StepConst &K, int b, double 
     }
 }
 
+// The quadrature terms of the state (R, V) of bin b at state index k into the terms buffer, with
+// the arithmetic of the closing moment pass (cell_moments), so that summing them in bin order
+// gives its bits.
+template <bool MIXED>
+__device__ __forceinline__ void store_terms(const StepConst &K, double *terms, int b, size_t k,
+                                            double R, double V)
+{
+    const long long ns = (long long)K.B * K.C;
+    const BinConst &bc = K.bins[b];
+    if (MIXED) {
+        float tf[3];
+        PAB_ST(terms, k, ns, quad_terms_mixed(K, bc, R, V, tf));
+        float *t32 = reinterpret_cast<float *>(terms + ns);
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            PAB_ST(t32, (long long)m * ns + (long long)k, 3 * ns, tf[m]);
+    } else {
+        double t[4];
+        GasBase g;
+        g.reset();
+        quad_terms64(K, bc, R, V, t, g);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            PAB_ST(terms, (long long)m * ns + (long long)k, 4 * ns, t[m]);
+    }
+}
+
+
+// The moments of cell c from the terms its bins stored (store_terms), summed in bin order as
+// cell_moments sums them.  The terms are read through L2: other CTAs of the launch wrote them.
+template <bool MIXED>
+__device__ __forceinline__ void sum_cell_terms(const StepConst &K, const double *terms, long long c,
+                                               double nb, double *out)
+{
+    const long long ns = (long long)K.B * K.C;
+    const float *t32 = reinterpret_cast<const float *>(terms + ns);
+    TermSums S;
+    constexpr int kAhead = 8;
+    for (int b0 = 0; b0 < K.B; b0 += kAhead) {
+        double x[kAhead], td[kAhead][3];
+        float tf[kAhead][3];
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i) {
+            const long long k = (long long)(b0 + i) * K.C + c;
+            if (b0 + i < K.B) {
+                x[i] = PAB_LDCG(terms, k, ns);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    if (MIXED)
+                        tf[i][m] = PAB_LDCG(t32, m * ns + k, 3 * ns);
+                    else
+                        td[i][m] = PAB_LDCG(terms, (m + 1) * ns + k, 4 * ns);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i) {
+            if (b0 + i < K.B)
+                add_terms<MIXED>(S, x[i], tf[i], td[i]);
+        }
+    }
+    write_moments<MIXED>(K, nb, K.C, c, S, out);
+}
+
 }  // namespace pab
