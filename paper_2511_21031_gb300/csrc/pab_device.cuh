@@ -241,8 +241,11 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
                                          double B0c, double R, double V, double h, GasBase &g)
 {
     const double a1 = accel64(K, bc, B0, B0c, R, V, g);
+    // y1 = y + h f(y) as one FMA (k1 itself is still formed for k1 + k2): every product-sum of
+    // the trial is an explicit fma, so the compiler contracts nothing and the bits do not depend
+    // on the kernel the trial is inlined into or on its register budget
     const double k1R = h * V, k1V = h * a1;
-    const double y1R = R + k1R, y1V = V + k1V;
+    const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
     const double a2 = accel64(K, bc, B0, B0c, y1R, y1V, g);
     const double sR = fma(h, y1V, k1R), sV = fma(h, a2, k1V);   // k1 + k2
     const double y2R = fma(0.25, sR, R), y2V = fma(0.25, sV, V);

@@ -93,11 +93,10 @@ def test_batch_slots_equal_single_instance_steps(precision):
 @pytest.mark.parametrize("launch", [(1, 32, 1), (4, 8, 1)])
 def test_batch_of_slices_matches_the_whole_grid(precision, launch):
     """A grid cut into instances of contiguous cells (the bench's same-work batched line) is
-    advanced by the batch as the single-instance kernel advances the whole grid.  In mixed
-    precision the bits are the same (state, step sizes, moments, trial count): every FP32
-    operation of a trial is an explicit rounding.  The FP64 trial is written with plain
-    operators, and whether the compiler contracts a product and a sum into one FMA depends on
-    the kernel it is inlined into, so there the two kernels may differ by an ulp."""
+    advanced by the batch exactly as the single-instance kernel advances the whole grid: the
+    same state, step sizes, moments and trial count.  Both kernels inline the same trial, whose
+    every FP32 operation is an explicit rounding and every FP64 product-sum an explicit fma, so
+    no contraction choice of the compiler can set them apart."""
     wl = workloads.config_grid128(edge=32)
     insts = workloads.sliced_instances(wl, 8)
     got = _run_batch(insts, 20, precision, launch=launch)
@@ -106,22 +105,11 @@ def test_batch_of_slices_matches_the_whole_grid(precision, launch):
     m = insts[0].n_cells
     for i, g in enumerate(got):
         sl = slice(i * m, (i + 1) * m)
-        if precision == "mixed":
-            for key in ("R", "V", "h"):
-                np.testing.assert_array_equal(g[key], ref[key][:, sl], err_msg=key)
-            np.testing.assert_array_equal(g["moments"], ref["moments"][:, sl])
-        else:
-            assert rel_err_R(g["R"], ref["R"][:, sl]) <= 1e-13
-            assert rel_err_V(g["V"], ref["V"][:, sl], wl.fluid) <= 1e-12
-            for k, e in moment_errors(g["moments"], ref["moments"][:, sl], ref["R"][:, sl],
-                                      ref["V"][:, sl], np.array(_bins(wl))).items():
-                assert e <= 1e-12, (k, e)
+        for key in ("R", "V", "h"):
+            np.testing.assert_array_equal(g[key], ref[key][:, sl], err_msg=key)
+        np.testing.assert_array_equal(g["moments"], ref["moments"][:, sl])
         assert g["status"]["flags"] == 0
-    n_got = sum(g["status"]["n_attempts"] for g in got)
-    if precision == "mixed":
-        assert n_got == ref["status"]["n_attempts"]
-    else:
-        assert abs(n_got / ref["status"]["n_attempts"] - 1) <= 1e-3
+    assert sum(g["status"]["n_attempts"] for g in got) == ref["status"]["n_attempts"]
 
 
 def test_batch_fp64_matches_oracle():
