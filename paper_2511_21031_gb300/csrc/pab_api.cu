@@ -200,6 +200,8 @@ void build_const(const pab_config *c, const double *R0, const double *w, pab::St
     K->v_floorf = (float)K->v_floor;
     K->cbrt_tolf = (float)std::cbrt(c->tol);
     K->tol3f = (float)K->tol3;
+    K->tol_lof = c->tol >= 1e-7 ? (float)(c->tol * (1.0 - 0x1p-16)) : -1.0f;
+    K->tol_hif = c->tol >= 1e-7 ? (float)(c->tol * (1.0 + 0x1p-16)) : INFINITY;
     K->v_collapsef = (float)K->v_collapse;
     K->r_collapsef = (float)K->r_collapse;
     K->cf = (float)c->c;

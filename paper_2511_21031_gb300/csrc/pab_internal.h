@@ -87,6 +87,10 @@ struct StepConst {
     float cbrt_tolf, v_collapsef, r_collapsef, cf;
     float tg_ic_rhof;     // 3 gamma (1/c)/rho
     float tol3f;          // 3 tol
+    // the FP64 accept test's bracket: an FP32 error estimate below tol_lof is accepted and one
+    // above tol_hif rejected without the exact test (tol (1 -/+ 2^-16); -1 and inf, that is never,
+    // for tol below 1e-7)
+    float tol_lof, tol_hif;
     BinConst bins[PAB_MAX_BINS];
 };
 
