@@ -280,6 +280,31 @@ __device__ __forceinline__ double embedded_diff(float k1, float k2, float k3, fl
     return f2d_fin(d) + f2d_fin(__fsub_rn(ed, es));
 }
 
+// The accept test on one component, |2 k3 - (k1 + k2)| <= T with the difference formed as
+// embedded_diff forms it (and d, its FP32 part), deciding in FP32 where the parts' bound settles
+// it.  The correction e = e_d - e_s is at most 2^-24 (|d| + |s|) (1 + 2^-24) (each TwoSum error is
+// at most half an ulp of its sum, and the FP32 subtraction rounds once), so b = 2^-22 (|d| + |s|)
+// bounds it with room for the roundings of the comparisons: |d| + b <= T (1 - 2^-20) means the
+// FP64 sum is below T, |d| - b > T (1 + 2^-20) that it is above.  Only differences inside that
+// bracket (or non-finite operands) take the FP64 addition of the exact test; the decision is the
+// exact test's either way.
+__device__ __forceinline__ bool embedded_within(float k1, float k2, float k3, float T, float &d)
+{
+    float s, es, ed;
+    two_sum(k1, k2, s, es);
+    two_sum(__fmul_rn(2.0f, k3), -s, d, ed);
+    const float e = __fsub_rn(ed, es);
+    const float ad = fabsf(d);
+    const float b = __fmul_rn(0x1p-22f, __fadd_rn(ad, fabsf(s)));
+    if (T <= FLT_MAX) {
+        if (__fadd_rn(ad, b) <= __fmul_rn(T, 1.0f - 0x1p-20f))
+            return true;
+        if (__fsub_rn(ad, b) > __fmul_rn(T, 1.0f + 0x1p-20f))
+            return false;
+    }
+    return le(abs_nn(f2d_fin(d) + f2d_fin(e)), f2d_fin(T));
+}
+
 // The three FP32 right-hand sides of one trial, on increments from the state
 // (xi = R - R0, v) with k_j = h f(stage j):
 //   stage 2 = y + k1,  stage 3 = y + (k1 + k2)/4,  y3 - y = (k1 + k2)/6 + 2/3 k3.
@@ -508,19 +533,19 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             d3R = in.d3R;
             d3V = in.d3V;
             float dR, dV;
-            const double aeR = abs_nn(embedded_diff(in.k1R, in.k2R, in.k3R, dR));
-            const double aeV = abs_nn(embedded_diff(in.k1V, in.k2V, in.k3V, dV));
             const float R3f = __fadd_rn(bc.R0f, __fadd_rn(xi, d3R));
             const float aRf = fabsf(R3f);
             const float aVf = fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf);
             ok = in.ok && (R3f > 0.0f);
             // err <= tol as |e_R| <= 3 tol |R3| and |e_Rdot| <= 3 tol max(|Rdot3|, v_floor):
-            // the FP64 estimate against thresholds formed in FP32 (a relative rounding of
-            // 6e-8 on tol, no FP64 product); the growth factor takes err from the FP32
-            // differences d (they differ from the estimate only where it is tiny, and the
-            // factor is 5 there either way) and the FP32 images of R3, Rdot3
-            accept = ok && le(aeR, f2d_fin(__fmul_rn(K.tol3f, aRf))) &&
-                     le(aeV, f2d_fin(__fmul_rn(K.tol3f, aVf)));
+            // the embedded estimate (FP64 where the FP32 bracket does not settle it) against
+            // thresholds formed in FP32 (a relative rounding of 6e-8 on tol, no FP64 product);
+            // the growth factor takes err from the FP32 differences d (they differ from the
+            // estimate only where it is tiny, and the factor is 5 there either way) and the
+            // FP32 images of R3, Rdot3
+            const bool wR = embedded_within(in.k1R, in.k2R, in.k3R, __fmul_rn(K.tol3f, aRf), dR);
+            const bool wV = embedded_within(in.k1V, in.k2V, in.k3V, __fmul_rn(K.tol3f, aVf), dV);
+            accept = ok && wR && wV;
             errf = fmaxf(__fmul_rn(fabsf(dR), rcp32(__fmul_rn(3.0f, aRf))),
                          __fmul_rn(fabsf(dV), rcp32(__fmul_rn(3.0f, aVf))));
             full64 = false;

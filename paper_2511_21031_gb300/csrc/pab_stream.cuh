@@ -361,16 +361,16 @@ struct ItemMixed {
             d3R = in.d3R;
             d3V = in.d3V;
             float dR, dV;
-            const double aeR = abs_nn(embedded_diff(in.k1R, in.k2R, in.k3R, dR));
-            const double aeV = abs_nn(embedded_diff(in.k1V, in.k2V, in.k3V, dV));
             const float R3f = __fadd_rn(bf.R0f, __fadd_rn(xi, d3R));
             const float aRf = fabsf(R3f);
             const float aVf = fmaxf(fabsf(__fadd_rn(v, d3V)), K.v_floorf);
             ok = in.ok && (R3f > 0.0f);
             // err <= tol as |e_R| <= 3 tol |R3| and |e_Rdot| <= 3 tol max(|Rdot3|, v_floor), the
-            // thresholds formed in FP32; the growth factor from the FP32 differences
-            accept = ok && le(aeR, f2d_fin(__fmul_rn(K.tol3f, aRf))) &&
-                     le(aeV, f2d_fin(__fmul_rn(K.tol3f, aVf)));
+            // thresholds formed in FP32, the estimate's FP64 sum only where the FP32 bracket does
+            // not settle it (embedded_within); the growth factor from the FP32 differences
+            const bool wR = embedded_within(in.k1R, in.k2R, in.k3R, __fmul_rn(K.tol3f, aRf), dR);
+            const bool wV = embedded_within(in.k1V, in.k2V, in.k3V, __fmul_rn(K.tol3f, aVf), dV);
+            accept = ok && wR && wV;
             errf = fmaxf(__fmul_rn(fabsf(dR), rcp32(__fmul_rn(3.0f, aRf))),
                          __fmul_rn(fabsf(dV), rcp32(__fmul_rn(3.0f, aVf))));
         }
