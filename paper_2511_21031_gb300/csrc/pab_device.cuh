@@ -356,15 +356,6 @@ __device__ __forceinline__ Trial trial32(const StepConst &K, const BinConst &bc,
     return t;
 }
 
-// Relative error of a trial: max(|dR|/|R3|, |dRdot|/max(|Rdot3|, v_floor)).
-// Every operand is >= 0; a NaN (only in a trial that failed, whose error is
-// never used) makes the result NaN.
-__device__ __forceinline__ double error_norm(const StepConst &K, const Trial &t)
-{
-    const double vs = max_nn(abs_nn(t.V), K.v_floor);
-    return max_nn(fabs(t.eR) * vs, fabs(t.eV) * fabs(t.R)) * rcp64((3.0 * fabs(t.R)) * vs);
-}
-
 // Growth factor of the controller, clamp(0.9 (tol/err)^(1/3), 0.2, 5), in FP32
 // (a heuristic whose product is stored in FP32 between calls): 0.2 after a
 // failed trial or an error past the FP32 range, 5 for a zero error.
@@ -385,6 +376,7 @@ __device__ __forceinline__ float growth_factor(const StepConst &K, float errf, b
 struct Decision {
     bool accept;
     float fac;
+    float errf;  // the FP32 error estimate the factor was taken from
 };
 // The FP32 estimate errf is within 1e-6 (relative) of err: each image rounds once (2^-24), the
 // approximate quotient is within 2 ulp for the normal denominators required here, and the
@@ -409,6 +401,7 @@ __device__ __forceinline__ Decision decide64(const StepConst &K, const Trial &t)
     else
         v.accept = le(abs_nn(t.eR), K.tol3 * aR) && le(abs_nn(t.eV), K.tol3 * vs);
     v.fac = growth_factor(K, errf, t.ok);
+    v.errf = errf;
     return v;
 }
 
@@ -462,12 +455,13 @@ __device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const B
     return flags;
 }
 
-// The FP64 trial of a bin near collapse in the mixed mode, with its error
-// norm.  (Kept inline: out of line, to spare the FP32 loop its registers, it
-// measured 2 % slower.)
+// The FP64 trial of a bin near collapse in the mixed mode, with the FP64 kernel's accept
+// test and error estimate (decide64).  (Kept inline: out of line, to spare the FP32 loop its
+// registers, it measured 2 % slower.)
 struct Trial64Out {
-    double R, V, err;
-    bool ok;
+    double R, V;
+    bool ok, accept;
+    float errf;
 };
 __device__ __forceinline__ Trial64Out collapse_trial64(const StepConst &K, const BinConst &bc,
                                                        double p_inf, double R, double V, double h)
@@ -476,7 +470,8 @@ __device__ __forceinline__ Trial64Out collapse_trial64(const StepConst &K, const
     g.reset();
     const double B0 = (K.pv - p_inf) * K.inv_rho;
     const Trial tr = trial64(K, bc, B0, B0 * K.inv_c, R, V, h, g);
-    return {tr.R, tr.V, error_norm(K, tr), tr.ok};
+    const Decision vd = decide64(K, tr);
+    return {tr.R, tr.V, tr.ok, vd.accept, vd.errf};
 }
 
 // ---------------------------------------------------------------------------
@@ -523,8 +518,8 @@ __device__ __forceinline__ uint32_t advance_mixed(const StepConst &K, const BinC
             const Trial64Out tr = collapse_trial64(K, bc, p_inf, bc.R0 + xi64, V, ht);
             ++n64;
             ok = tr.ok;
-            accept = ok && le(tr.err, K.tol);
-            errf = d2f(tr.err);
+            accept = tr.accept;
+            errf = tr.errf;
             nR = tr.R;
             nV = tr.V;
             full64 = true;

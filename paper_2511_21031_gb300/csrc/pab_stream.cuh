@@ -352,8 +352,8 @@ struct ItemMixed {
             const Trial64Out tr = collapse_trial64(K, bc, PAB_LD(io.p_inf, c, io.C), bc.R0 + xi64, V, ht);
             ++n64;
             ok = tr.ok;
-            accept = ok && le(tr.err, K.tol);
-            errf = d2f(tr.err);
+            accept = tr.accept;
+            errf = tr.errf;
             nR = tr.R - bc.R0;
             nV = tr.V;
         } else {
