@@ -90,6 +90,27 @@ pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, co
                           double *seed_dev, uint16_t *cmp_dev, void *stream);
 
 /*
+ * The trial accept tests against their exact forms (no counterpart in the
+ * paper; a test hook for the controller of Sec. 3).  For each i:
+ *   out[4i+0]  the FP64 trial's accept decision (an FP32 error estimate decides
+ *              outside tol (1 -/+ 2^-16), the FP64 test inside) on the trial
+ *              trial[4i..4i+3] = {R3, Rdot3, e_R, e_Rdot} (e: three times the
+ *              embedded difference), the trial taken as valid;
+ *   out[4i+1]  the exact FP64 test |e_R| <= 3 tol |R3| and
+ *              |e_Rdot| <= 3 tol max(|Rdot3|, v_floor) on the same trial;
+ *   out[4i+2]  the mixed trial's test on one component (an FP32 bound on the
+ *              TwoSum parts decides outside T (1 -/+ 2^-20), the FP64 sum
+ *              inside) for k[4i..4i+3] = {k1, k2, k3, T};
+ *   out[4i+3]  the exact form: |d + (e_d - e_s)| <= T with the FP64 sum.
+ * trial_dev [4n] double, k_dev [4n] float, out_dev [4n] uint8, on the device;
+ * tol > 0 and v_floor >= 0 as in pab_config.
+ * Errors: PAB_EINVAL (n < 0, NULL pointers with n > 0, tol or v_floor out of
+ * range), PAB_ECUDA.
+ */
+pab_status pab_accept_check(int64_t n, const double *trial_dev, const float *k_dev, double tol,
+                            double v_floor, uint8_t *out_dev, void *stream);
+
+/*
  * The gas-term node table a handle builds for the polytropic exponent gamma,
  * on the host (no handle, no device).  The gas factor (R0/R)^(3 gamma) is
  * x^(-3 gamma) with x = R/R0; the table holds nodes x_j = q^j, j = -J..J

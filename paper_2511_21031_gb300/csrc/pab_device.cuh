@@ -381,18 +381,21 @@ struct Decision {
 // The FP32 estimate errf is within 1e-6 (relative) of err: each image rounds once (2^-24), the
 // approximate quotient is within 2 ulp for the normal denominators required here, and the
 // product by 1/3 rounds once.  Outside err = tol (1 -/+ 2^-16) it therefore decides as the exact
-// test does, which then runs only for estimates in that bracket (or for denominators and
-// estimates outside the FP32 range): the same decisions, without its two FP64 products.  (For
+// test does, which then runs only for estimates in that bracket (or for denominators, error
+// images and estimates outside the FP32 range, NaNs included): the same decisions, without its
+// two FP64 products.  (For
 // tol below 1e-7, where an error image flushed to zero could matter, the bracket is closed.)
 __device__ __forceinline__ Decision decide64(const StepConst &K, const Trial &t)
 {
     const double aR = abs_nn(t.R);
     const double vs = max_nn(abs_nn(t.V), K.v_floor);
     const float aRf = d2f(aR), vsf = d2f(vs);
-    const float errf = (1.0f / 3.0f) * fmaxf(__fdividef(d2f(abs_nn(t.eR)), aRf),
-                                             __fdividef(d2f(abs_nn(t.eV)), vsf));
+    const float eRf = d2f(abs_nn(t.eR)), eVf = d2f(abs_nn(t.eV));
+    const float errf = (1.0f / 3.0f) * fmaxf(__fdividef(eRf, aRf), __fdividef(eVf, vsf));
     Decision v;
+    // (fmaxf drops a NaN operand: the bracket needs both error images finite)
     const bool sure = aRf >= 0x1p-100f && aRf <= 0x1p100f && vsf >= 0x1p-100f && vsf <= 0x1p100f &&
+                      eRf <= FLT_MAX && eVf <= FLT_MAX &&
                       (errf <= K.tol_lof || (errf > K.tol_hif && errf <= FLT_MAX));
     if (!t.ok)
         v.accept = false;

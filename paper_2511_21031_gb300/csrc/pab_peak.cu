@@ -140,6 +140,31 @@ extern "C" pab_status pab_bits_check(int64_t n, const float *f_dev, const double
 }
 
 namespace {
+__global__ void accept_check_kernel(const __grid_constant__ pab::StepConst K, long long n,
+                                    const double *trial, const float *k, uint8_t *out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        pab::Trial t;
+        t.R = trial[4 * i + 0];
+        t.V = trial[4 * i + 1];
+        t.eR = trial[4 * i + 2];
+        t.eV = trial[4 * i + 3];
+        t.ok = true;
+        const double aR = pab::abs_nn(t.R);
+        const double vs = pab::max_nn(pab::abs_nn(t.V), K.v_floor);
+        out[4 * i + 0] = ((uint8_t)pab::decide64(K, t).accept);
+        out[4 * i + 1] =
+            (uint8_t)(pab::le(pab::abs_nn(t.eR), K.tol3 * aR) && pab::le(pab::abs_nn(t.eV), K.tol3 * vs));
+        const float k1 = k[4 * i + 0], k2 = k[4 * i + 1];
+        const float k3 = k[4 * i + 2], T = k[4 * i + 3];
+        float d1, d2;
+        out[4 * i + 2] = ((uint8_t)pab::embedded_within(k1, k2, k3, T, d1));
+        out[4 * i + 3] =
+            (uint8_t)pab::le(pab::abs_nn(pab::embedded_diff(k1, k2, k3, d2)), pab::f2d_fin(T));
+    }
+}
+
 __global__ void gas32_check_kernel(long long n, const float *u, float a, float *out, float *lib)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -149,6 +174,31 @@ __global__ void gas32_check_kernel(long long n, const float *u, float a, float *
     }
 }
 }  // namespace
+
+extern "C" pab_status pab_accept_check(int64_t n, const double *trial_dev, const float *k_dev,
+                                       double tol, double v_floor, uint8_t *out_dev, void *stream)
+{
+    if (n < 0 || (n > 0 && (!trial_dev || !k_dev || !out_dev)) || !(tol > 0.0) || !(tol < 1.0) ||
+        !(v_floor >= 0.0) || !std::isfinite(v_floor))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    pab_config c;
+    pab_config_default(&c);
+    c.n_cells = 1;
+    c.n_bins = 1;
+    c.tol = tol;
+    c.v_floor = v_floor;
+    const double R0 = 1e-5, w = 1.0;
+    pab::StepConst K;
+    pab::make_const(&c, &R0, &w, &K);
+    cudaStream_t s = (cudaStream_t)stream;
+    accept_check_kernel<<<152 * 4, 256, 0, s>>>(K, n, trial_dev, k_dev, out_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
 
 extern "C" pab_status pab_gas32_check(int64_t n, const float *u_dev, float a, float *out_dev,
                                       float *lib_dev, void *stream)

@@ -31,7 +31,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
            "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check", "pab_gas_table",
-           "pab_get_contents", "pab_set_contents", "pab_check_report")
+           "pab_get_contents", "pab_set_contents", "pab_check_report", "pab_accept_check")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_math_check": (i32, [i64, vp, vp, dbl, vp, vp, vp, vp]),
         "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
+        "pab_accept_check": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
         "pab_check_report": (i32, [ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
@@ -316,6 +317,23 @@ def pab_gas32_check(u, a: float, stream=None):
     if st != PAB_OK:
         raise PabError(st, "pab_gas32_check")
     return out, lib
+
+
+def pab_accept_check(trial, k, tol: float, v_floor: float, stream=None):
+    """[n, 4] uint8: the FP64 trial's bracketed accept decision and the exact FP64 test on
+    trial [n, 4] float64 (R3, Rdot3, e_R, e_Rdot), then the mixed trial's bracketed component
+    test and its exact form on k [n, 4] float32 (k1, k2, k3, T)."""
+    import torch
+    n = trial.shape[0]
+    if tuple(trial.shape) != (n, 4) or tuple(k.shape) != (n, 4) or trial.dtype != torch.float64 \
+            or k.dtype != torch.float32 or not trial.is_contiguous() or not k.is_contiguous():
+        raise ValueError("trial must be [n, 4] float64 and k [n, 4] float32, contiguous")
+    out = torch.empty((n, 4), dtype=torch.uint8, device=trial.device)
+    st = load().pab_accept_check(n, trial.data_ptr(), k.data_ptr(), float(tol), float(v_floor),
+                                 out.data_ptr(), _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_accept_check")
+    return out
 
 
 CHECK_UNITS = {1: "step kernels", 2: "batch", 3: "carrier coupling", 4: "Euler-Lagrange", 5: "transfer contents"}

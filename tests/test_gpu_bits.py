@@ -84,3 +84,69 @@ def test_bit_helpers_match_the_hardware():
     assert float(seed_rel.max()) < 2.0 ** -18  # the correction's truncation e0^3 < 2^-54
     bad = ~np.isfinite(x) | (x == 0)
     assert np.all(np.isnan(o["rcp"][bad]))
+
+
+def _near_ties(rng, base, n):
+    """base (1 + delta) with delta at every scale from 2^-60 to 1/2, either sign, and zero."""
+    k = rng.integers(8, 61, size=n)
+    delta = np.where(rng.random(n) < 0.8, np.ldexp(1.0, -k) * rng.choice([-1.0, 1.0], size=n),
+                     rng.uniform(-0.5, 0.5, size=n))
+    delta[rng.random(n) < 0.05] = 0.0
+    return base * (1.0 + delta)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-7, 1e-8, 0.3])
+def test_bracketed_accept_tests_decide_as_the_exact_ones(tol):
+    """The FP64 trial's accept test decided by its FP32 error estimate outside tol (1 -/+ 2^-16),
+    and the mixed trial's component test decided by an FP32 bound on the TwoSum parts outside
+    T (1 -/+ 2^-20), give the exact FP64 tests' decisions on inputs crowded at the tolerance
+    (relative offsets from 2^-60 to 1/2), at every magnitude, and on the edges (zeros,
+    magnitudes outside the bracket's range, infinities, NaNs)."""
+    import torch
+    rng = np.random.default_rng(31)
+    n = 1 << 21
+    v_floor = 1e-3 * np.sqrt(101325.0 / 1000.0)
+    tol3 = 3.0 * tol
+    R = 10.0 ** rng.uniform(-9, -2, size=n)
+    V = rng.normal(size=n) * 10.0 ** rng.uniform(-4, 3, size=n)
+    V[rng.random(n) < 0.05] = 0.0
+    vs = np.maximum(np.abs(V), v_floor)
+    eR = _near_ties(rng, tol3 * R, n) * rng.choice([-1.0, 1.0], size=n)
+    eV = _near_ties(rng, tol3 * vs, n) * rng.choice([-1.0, 1.0], size=n)
+    # one component clearly inside for half of them, so that the other decides
+    inside = rng.random(n) < 0.5
+    eR[inside] *= 0.25
+    eV[~inside & (rng.random(n) < 0.5)] *= 0.25
+    edge = rng.random(n) < 0.02
+    R[edge] = rng.choice([1e-40, 1e-31, 1e31, 1e40], size=edge.sum())
+    eR[edge] = tol3 * R[edge] * rng.choice([0.5, 1.0, 2.0], size=edge.sum())
+    odd = rng.choice(n, 64, replace=False)
+    eR[odd[:16]] = np.inf
+    eR[odd[16:32]] = np.nan
+    eV[odd[32:48]] = 0.0
+    eR[odd[48:]] = 1e300
+    trial = np.stack([R, V, eR, eV], axis=1)
+
+    k1 = (rng.normal(size=n) * 10.0 ** rng.uniform(-12, 0, size=n)).astype(np.float32)
+    k2 = np.where(rng.random(n) < 0.5, k1 * (1 + rng.normal(size=n) * 1e-3),
+                  rng.normal(size=n) * 10.0 ** rng.uniform(-12, 0, size=n)).astype(np.float32)
+    half = (k1.astype(np.float64) + k2.astype(np.float64)) / 2
+    k3 = _near_ties(rng, half, n).astype(np.float32)          # cancellation in 2 k3 - (k1 + k2)
+    D = 2.0 * k3.astype(np.float64) - (k1.astype(np.float64) + k2.astype(np.float64))
+    T = np.abs(_near_ties(rng, D, n)).astype(np.float32)
+    T[rng.random(n) < 0.01] = 0.0
+    kk = np.stack([k1, k2, k3, T], axis=1)
+    kk[odd[:16], 3] = np.inf
+    kk[odd[16:32], 0] = np.nan
+    kk[odd[32:48], 2] = np.inf
+    kk[odd[48:], 3] = np.float32(1e-45)
+
+    out = pab.pab_accept_check(torch.as_tensor(trial, device="cuda"),
+                               torch.as_tensor(np.ascontiguousarray(kk), device="cuda"), tol,
+                               v_floor).cpu().numpy()
+    bad64 = np.flatnonzero(out[:, 0] != out[:, 1])
+    bad32 = np.flatnonzero(out[:, 2] != out[:, 3])
+    assert bad64.size == 0, trial[bad64[:5]]
+    assert bad32.size == 0, kk[bad32[:5]]
+    # the inputs straddle the tolerance: both decisions occur in quantity
+    assert 0.2 < out[:, 1].mean() < 0.8 and 0.2 < out[:, 3].mean() < 0.8
