@@ -1106,7 +1106,7 @@ def run_ours(args):
             extra("collapse mixed", lambda: _bench_collapse(args, stream, dev, "mixed"))
     if args.variants and args.latency and ws == 1:
         extra("latency small", lambda: _bench_latency_small(args, stream, dev))
-    if args.serving_sweep and ws == 1:
+    if args.variants and args.serving and args.serving_sweep and ws == 1:
         extra("serving sweep", lambda: _bench_serving_sweep(args, args.sweep_rates, args.sweep_requests))
 
     fma = None
@@ -1199,9 +1199,10 @@ def main():
                     help="profiling aid: start the collapse line from a saved state")
     ap.add_argument("--no-latency", dest="latency", action="store_false",
                     help="skip the per-call latency line of the 64-cell workload")
-    ap.add_argument("--serving-sweep", action="store_true",
-                    help="serve the request stream at several rates (minutes of wall time)")
-    ap.add_argument("--sweep-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0, 4.0])
+    ap.add_argument("--no-serving-sweep", dest="serving_sweep", action="store_false",
+                    help="skip the serving rate sweep (about 75 s of wall time; --no-serving skips it too)")
+    ap.add_argument("--sweep-rates", type=float, nargs="+", default=[2.0, 3.5, 5.0],
+                    help="offered request rates of the sweep: below, near and above saturation")
     ap.add_argument("--sweep-requests", type=int, default=64)
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the mixed-precision and batched lines")
