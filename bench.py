@@ -673,7 +673,7 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
     launch_ms = []
     n_att = n64 = 0
     flags = 0
-    chunk = 250
+    chunk = max(8, min(250, int(2e9 // (8 * C))))   # about 2 GB of pressure fields at a time
     torch.cuda.synchronize()
     for c0 in range(first, first + wl.n_steps, chunk):
         n1 = min(first + wl.n_steps, c0 + chunk)
