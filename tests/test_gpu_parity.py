@@ -385,17 +385,20 @@ def test_mixed_parked_items_and_lot_overflow_give_the_same_bits_in_every_launch_
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_small_grid_split_by_bins_gives_the_bits_of_a_large_grid(precision):
-    """A grid of fewer tiles than SMs is split by bins over more CTAs, its moments from the
-    reduce-only kernel; the same cells inside a large grid (one CTA per 128 cells, moments from the
-    closing pass) give the same state and moments, bit for bit."""
+@pytest.mark.parametrize("m", [1, 70, 96, 4700])
+def test_small_grid_split_by_bins_gives_the_bits_of_a_large_grid(precision, m):
+    """A grid of fewer tiles than SMs is split by bins over more CTAs, and the last CTA of each
+    tile sums the terms the others stored (one bin per CTA at 1-96 cells, two bin ranges at 147
+    tiles, a ragged last tile at 70 and 4700 cells; the tiles' counters reset by every one of the
+    30 calls); the same cells inside a large grid (one CTA per 128 cells, moments from the closing
+    pass) give the same state and moments, bit for bit."""
     big = workloads.config_grid128(edge=32)               # 32768 cells: 256 CTAs
-    small = big.subset(np.arange(96))                      # 96 cells: 3 tiles, split by bins
+    small = big.subset(np.arange(m))                       # fewer tiles than SMs: split by bins
     n = 30
     ps = [big.pressure_step(k) for k in range(n)]
     gb = run_gpu(big, n, pressures=ps, precision=precision, record=False)
-    gs = run_gpu(small, n, pressures=[p[:96] for p in ps], precision=precision, record=False)
-    np.testing.assert_array_equal(gs["R"], gb["R"][:, :96])
-    np.testing.assert_array_equal(gs["V"], gb["V"][:, :96])
-    np.testing.assert_array_equal(gs["h"], gb["h"][:, :96])
-    np.testing.assert_array_equal(gs["moments"], gb["moments"][:, :96])
+    gs = run_gpu(small, n, pressures=[p[:m] for p in ps], precision=precision, record=False)
+    np.testing.assert_array_equal(gs["R"], gb["R"][:, :m])
+    np.testing.assert_array_equal(gs["V"], gb["V"][:, :m])
+    np.testing.assert_array_equal(gs["h"], gb["h"][:, :m])
+    np.testing.assert_array_equal(gs["moments"], gb["moments"][:, :m])
