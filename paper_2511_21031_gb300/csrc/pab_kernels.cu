@@ -136,6 +136,25 @@ __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
     if (K.n_fixed > 0) {
         fixed_items<MIXED>(K, a, io, tc);
     } else {
+        // the cells' pressure terms, once per cell rather than once per (bin, cell) item
+        constexpr int kCellBytes = MIXED ? (int)sizeof(float) : 2 * (int)sizeof(double);
+        __shared__ __align__(8) unsigned char s_cell[kMaxWarps * kTile * kCellBytes];
+        double *cB0 = reinterpret_cast<double *>(s_cell);
+        double *cB0c = cB0 + kMaxWarps * kTile;
+        float *cA0 = reinterpret_cast<float *>(s_cell);
+        for (int cl = threadIdx.x; cl < io.nc; cl += blockDim.x) {
+            const double p = PAB_LD(a.p_inf, io.c0 + cl, K.C);
+            if (MIXED) {
+                cA0[cl] = d2f(K.p0 - p);
+            } else {
+                const double B0 = (K.pv - p) * K.inv_rho;
+                cB0[cl] = B0;
+                cB0c[cl] = B0 * K.inv_c;
+            }
+        }
+        io.cB0 = cB0;
+        io.cB0c = cB0c;
+        io.cA0 = cA0;
         if (threadIdx.x == 0)
             sh = PoolCounters{0, 0, 0};
         __syncthreads();

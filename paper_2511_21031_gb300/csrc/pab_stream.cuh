@@ -58,6 +58,10 @@ struct TileIO {
     int nc;               // cells of the CTA (1..32 x warps)
     int b0, b1;           // bins [b0, b1)
     double dt;            // flow step
+    // per cell of the CTA (index c - c0), formed once before the items: B0 = (pv - p_inf)/rho
+    // and B0/c (FP64 items), the FP32 image of p0 - p_inf (mixed items)
+    const double *cB0 = nullptr, *cB0c = nullptr;
+    const float *cA0 = nullptr;
 };
 
 // Status of the items a lane finished.
@@ -147,8 +151,8 @@ struct Item64 {
             tc.n_flag += 1;
             return false;
         }
-        B0 = (K.pv - p_inf) * K.inv_rho;
-        B0c = B0 * K.inv_c;
+        B0 = io.cB0[c - io.c0];
+        B0c = io.cB0c[c - io.c0];
         h = start_h(hc, io.dt);
         rem = io.dt;
         return true;
@@ -266,7 +270,7 @@ struct ItemMixed {
         bf.invR0f = bc.invR0f;
         bf.pg0f = bc.pg0f;
         const double p_inf = PAB_LD(io.p_inf, c, io.C);
-        A = bc.dpeqf + d2f(K.p0 - p_inf);
+        A = bc.dpeqf + io.cA0[c - io.c0];
         return p_inf;
     }
 
