@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(kOrderThreads)
 // Advance bin b of cell c over the slot's flow step, store the state and count.
 template <bool MIXED>
 __device__ __forceinline__ void advance_one(const StepConst &K, const BinConst &bc, const SlotDesc &d,
-                                            int b, long long c, double p_inf, bool p_ok, double &R,
-                                            double &V, GasBase &g, uint32_t &fl_or, uint32_t &n_flag,
-                                            uint32_t &n_att, uint32_t &n64)
+                                            int b, long long c, double p_inf, const CellTerms &ct,
+                                            bool p_ok, double &R, double &V, GasBase &g, uint32_t &fl_or,
+                                            uint32_t &n_flag, uint32_t &n_att, uint32_t &n64)
 {
     const size_t k = (size_t)b * (size_t)d.C + (size_t)c;
     const long long ns = (long long)d.B * d.C;
@@ -158,7 +158,7 @@ __device__ __forceinline__ void advance_one(const StepConst &K, const BinConst &
     float hc = PAB_LD(d.h, k, ns);
     int na = 0, nd = 0;
     g.reset();
-    const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
+    const uint32_t fl = advance_bin<MIXED>(K, bc, p_inf, ct, p_ok, d.dt, d.dt_sub, R, V, hc, na, nd, g);
     PAB_ST(d.R, k, ns, R);  // unchanged when the input was not finite
     PAB_ST(d.V, k, ns, V);
     PAB_ST(d.h, k, ns, hc);
@@ -258,6 +258,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
         const bool valid = c < d.C;
         const double p_inf = valid ? PAB_LD(d.p_inf, c, d.C) : K.p0;
         const bool p_ok = finite64(p_inf);
+        const CellTerms ct = cell_terms<MIXED>(K, p_inf);  // once per cell, not per bin
         uint32_t fl_or = 0, n_flag = 0, n_att = 0, n64 = 0;
         TermSums S;
 
@@ -273,7 +274,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
                 const BinConst &bc = K.bins[b];
                 double R, V;
                 GasBase g;
-                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, tc.fl_or, tc.n_flag, tc.n_att, tc.n64);
+                advance_one<MIXED>(K, bc, d, b, c, p_inf, ct, p_ok, R, V, g, tc.fl_or, tc.n_flag, tc.n_att, tc.n64);
                 if (d.out)
                     add_bin_terms<MIXED>(K, b, R, V, S);
             }
@@ -303,7 +304,7 @@ __global__ void __maxnreg__(PAB_BATCH_MAXNREG)
                 const BinConst &bc = K.bins[b];
                 double R, V;
                 GasBase g;
-                advance_one<MIXED>(K, bc, d, b, c, p_inf, p_ok, R, V, g, fl_or, n_flag, n_att, n64);
+                advance_one<MIXED>(K, bc, d, b, c, p_inf, ct, p_ok, R, V, g, fl_or, n_flag, n_att, n64);
                 if (d.out) {
                     if (MIXED) {
                         float tf[3];

@@ -418,12 +418,26 @@ __device__ __forceinline__ Decision decide64(const StepConst &K, const Trial &t)
 //   max_attempts trials.
 // FP64 trials throughout (the mixed mode has its own loop, advance_mixed).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
-                                                     double p_inf, double dt, double &R, double &V,
-                                                     float &hc, int &n_att, GasBase &g)
+// A cell's pressure terms, the same for all its bins: B0 = (pv - p_inf)/rho and B0/c (FP64
+// trials), the FP32 image of p0 - p_inf (mixed trials).
+struct CellTerms {
+    double B0, B0c;
+    float A0;
+};
+template <bool MIXED>
+__device__ __forceinline__ CellTerms cell_terms(const StepConst &K, double p_inf)
 {
-    const double B0 = (K.pv - p_inf) * K.inv_rho;
-    const double B0c = B0 * K.inv_c;
+    CellTerms t;
+    t.B0 = (K.pv - p_inf) * K.inv_rho;
+    t.B0c = t.B0 * K.inv_c;
+    t.A0 = MIXED ? d2f(K.p0 - p_inf) : 0.0f;
+    return t;
+}
+
+__device__ __forceinline__ uint32_t advance_adaptive(const StepConst &K, const BinConst &bc,
+                                                     double B0, double B0c, double dt, double &R,
+                                                     double &V, float &hc, int &n_att, GasBase &g)
+{
     double h = start_h(hc, dt);
     double rem = dt;  // time left of the flow step, counted down
     uint32_t flags = 0;
@@ -610,15 +624,16 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
 // ---------------------------------------------------------------------------
 template <bool MIXED>
 __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinConst &bc, double p_inf,
-                                                bool p_ok, double dt, double dt_sub, double &R, double &V,
-                                                float &hc, int &na, int &n64, GasBase &g)
+                                                const CellTerms &ct, bool p_ok, double dt, double dt_sub,
+                                                double &R, double &V, float &hc, int &na, int &n64,
+                                                GasBase &g)
 {
     na = 0;
     n64 = 0;
     if (!p_ok || !finite64(R) || !finite64(V))
         return PAB_FLAG_NONFINITE;
     uint32_t fl = 0;
-    const float A = MIXED ? bc.dpeqf + d2f(K.p0 - p_inf) : 0.0f;
+    const float A = MIXED ? bc.dpeqf + ct.A0 : 0.0f;
     if (K.n_fixed > 0) {
         advance_fixed<MIXED>(K, bc, p_inf, A, dt_sub, R, V, g);
         na = K.n_fixed;
@@ -626,7 +641,7 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
         float xi, v;
         fl = advance_mixed(K, bc, p_inf, A, dt, R, V, hc, na, n64, xi, v);
     } else {
-        fl = advance_adaptive(K, bc, p_inf, dt, R, V, hc, na, g);
+        fl = advance_adaptive(K, bc, ct.B0, ct.B0c, dt, R, V, hc, na, g);
     }
     if (!finite64(R) || !finite64(V))
         fl |= PAB_FLAG_NONFINITE;

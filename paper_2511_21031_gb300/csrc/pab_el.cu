@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256)
         int nd = 0;
         GasBase g;
         g.reset();
-        fl = advance_bin<false>(K, bc, p_inf, isfinite(p_inf), dt, 0.0, r, v, hc, na, nd, g);  // adaptive
+        fl = advance_bin<false>(K, bc, p_inf, cell_terms<false>(K, p_inf), isfinite(p_inf), dt, 0.0, r, v,
+                                hc, na, nd, g);  // adaptive
         PAB_ST(R, n, N, r);  // unchanged when the input was not finite
         PAB_ST(V, n, N, v);
         PAB_ST(h, n, N, hc);
