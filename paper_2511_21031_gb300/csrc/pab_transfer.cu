@@ -167,8 +167,9 @@ struct ItemT {
 
     // The start of the flow step from the stored state; false for a non-finite input (flagged,
     // counted, left as it is).
+    // (mRg_b: the bin's gas constant; pinf_c: the cell's p_inf / rho, both formed once per CTA)
     __device__ __forceinline__ bool start(const StepConst &K, const StepArgs &a, int b, long long c_,
-                                          TileCounts &tc)
+                                          double mRg_b, double pinf_c, TileCounts &tc)
     {
         c = c_;
         k = (size_t)b * (size_t)K.C + (size_t)c;
@@ -184,8 +185,8 @@ struct ItemT {
             tc.n_flag += 1;
             return false;
         }
-        mRg = gas_mRg(K, K.bins[b]);
-        pinf_rho = p_inf * K.inv_rho;
+        mRg = mRg_b;
+        pinf_rho = pinf_c;
         h = start_h(PAB_LD(a.h, k, ns), a.dt);
         rem = a.dt;
         return true;
@@ -320,6 +321,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     if (K.n_fixed > 0) {
         transfer_fixed(K, a, c0, nc, tc);
     } else {
+        // the bins' gas constants and the cells' p_inf / rho, once per CTA rather than per item
+        __shared__ double s_mRg[PAB_MAX_BINS];
+        __shared__ double s_pinf[kMaxWarps * kTile];
+        for (int b = threadIdx.x; b < K.B; b += blockDim.x)
+            s_mRg[b] = gas_mRg(K, K.bins[b]);
+        for (int cl = threadIdx.x; cl < nc; cl += blockDim.x)
+            s_pinf[cl] = PAB_LD(a.p_inf, c0 + cl, K.C) * K.inv_rho;
         if (threadIdx.x == 0)
             sh = PoolCounters{0, 0, 0};
         __syncthreads();
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                     int b, cl;
                     size_t k;
                     item_of(io, j, b, cl, k);
-                    have = it.start(K, a, b, c0 + cl, tc);
+                    have = it.start(K, a, b, c0 + cl, s_mRg[b], s_pinf[cl], tc);
                 }
             }
             if (!__any_sync(0xffffffffu, have)) {
