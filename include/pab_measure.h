@@ -90,6 +90,16 @@ pab_status pab_bits_check(int64_t n, const float *f_dev, const double *x_dev, co
                           double *seed_dev, uint16_t *cmp_dev, void *stream);
 
 /*
+ * The smear's FP64 exponential against the library's (no counterpart in the
+ * paper; a test hook): mine_dev[i] = the table-driven e^x the Gaussian kernel
+ * of the Euler-Lagrange smear uses, lib_dev[i] = the CUDA math library's exp,
+ * for x_dev[i].  All [n] double on the device.
+ * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.
+ */
+pab_status pab_exp_check(int64_t n, const double *x_dev, double *mine_dev, double *lib_dev,
+                         void *stream);
+
+/*
  * The trial accept tests against their exact forms (no counterpart in the
  * paper; a test hook for the controller of Sec. 3).  For each i:
  *   out[4i+0]  the FP64 trial's accept decision (an FP32 error estimate decides

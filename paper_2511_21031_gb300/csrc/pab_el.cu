@@ -26,6 +26,7 @@
 
 #include "pab.h"
 #include "pab_device.cuh"
+#include "pab_exp.cuh"
 #include "pab_el.h"
 #include "pab_check.cuh"
 #include "pab_internal.h"
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                 const double c2 = cc * cc;
                 sq[warp][a][o] = c2;
                 sqf[warp][a][o] = (float)c2;
-                const double f = exp(-c2 * inv2h2);
+                const double f = exp_tab(-c2 * inv2h2);
                 fac[warp][a][o] = a == 0 ? f * amp : f;
             }
             __syncwarp();
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                 const double d2 = cx * cx + cy * cy + cz * cz;
                 if (!(sqrt(d2) / h < 3.0))
                     continue;
-                const double a = amp * exp(-d2 * inv2h2);
+                const double a = amp * exp_tab(-d2 * inv2h2);
                 const long long c = ((long long)k * ny + j) * nx + i;
                 atomicAdd(PAB_AT(alpha, c, ng), a);
                 if (alpha_dot)

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "pab_device.cuh"
+#include "pab_exp.cuh"
 #include "pab_internal.h"
 #include "pab_measure.h"
 
@@ -165,6 +166,15 @@ __global__ void accept_check_kernel(const __grid_constant__ pab::StepConst K, lo
     }
 }
 
+__global__ void exp_check_kernel(long long n, const double *x, double *mine, double *lib)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        mine[i] = pab::exp_tab(x[i]);
+        lib[i] = exp(x[i]);
+    }
+}
+
 __global__ void gas32_check_kernel(long long n, const float *u, float a, float *out, float *lib)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -194,6 +204,21 @@ extern "C" pab_status pab_accept_check(int64_t n, const double *trial_dev, const
     pab::make_const(&c, &R0, &w, &K);
     cudaStream_t s = (cudaStream_t)stream;
     accept_check_kernel<<<152 * 4, 256, 0, s>>>(K, n, trial_dev, k_dev, out_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
+
+extern "C" pab_status pab_exp_check(int64_t n, const double *x_dev, double *mine_dev, double *lib_dev,
+                                    void *stream)
+{
+    if (n < 0 || (n > 0 && (!x_dev || !mine_dev || !lib_dev)))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    exp_check_kernel<<<152 * 4, 256, 0, s>>>(n, x_dev, mine_dev, lib_dev);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);

@@ -31,7 +31,8 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_last_error", "pab_status_string", "pab_peak_fma", "pab_bubble_step_noalloc",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
            "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check", "pab_gas_table",
-           "pab_get_contents", "pab_set_contents", "pab_check_report", "pab_accept_check")
+           "pab_get_contents", "pab_set_contents", "pab_check_report", "pab_accept_check",
+           "pab_exp_check")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -120,6 +121,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_bits_check": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
         "pab_accept_check": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
+        "pab_exp_check": (i32, [i64, vp, vp, vp, vp]),
         "pab_check_report": (i32, [ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
@@ -317,6 +319,18 @@ def pab_gas32_check(u, a: float, stream=None):
     if st != PAB_OK:
         raise PabError(st, "pab_gas32_check")
     return out, lib
+
+
+def pab_exp_check(x, stream=None):
+    """(the smear's table-driven e^x, the CUDA library's exp) of x (float64, on the device)."""
+    import torch
+    mine = torch.empty_like(x)
+    lib = torch.empty_like(x)
+    st = load().pab_exp_check(x.numel(), x.data_ptr(), mine.data_ptr(), lib.data_ptr(),
+                              _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_exp_check")
+    return mine, lib
 
 
 def pab_accept_check(trial, k, tol: float, v_floor: float, stream=None):
