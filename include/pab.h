@@ -23,7 +23,8 @@
  *   - Device pointers are caller-owned, contiguous, resident on the device
  *     that was current at pab_create, and must stay valid until the stream
  *     work that uses them has completed.  The handle owns only its state and
- *     its small scratch (status counters, staging for the host entry point).
+ *     its scratch (status counters, staging for the host entry point, and for
+ *     small grids the quadrature terms of pab_create below).
  *   - State layout is bin-major structure-of-arrays: element (bin i, cell c)
  *     is at index i * n_cells + c.  Moments are [7][n_cells], row k at k * n_cells.
  *   - Calls are stream-ordered and asynchronous unless stated.  `stream` is a
@@ -126,6 +127,10 @@ void pab_config_default(pab_config *cfg);
  * one), allocates the state R, Rdot (FP64 [Nb][C]) and the carried sub-step
  * h (FP32 [Nb][C]) on the current device, and initialises R = R0_i,
  * Rdot = Rdot0_ref R0_i/R0ref, h = 0 (first call uses dt) on `stream`.
+ * A grid of fewer 32-cell tiles than the device has SMs is stepped split by
+ * bins over more CTAs; its handle also holds 4 doubles per bin-state for the
+ * quadrature terms and one counter per tile (under 10 MB on 152 SMs), so that
+ * the step writes the moments in one launch.
  * Errors: PAB_EINVAL (bad cfg, even Nb, NULL out), PAB_ENOMEM, PAB_ECUDA.
  */
 pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out);
