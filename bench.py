@@ -68,10 +68,10 @@ MIXED_FP64_PIPE_ACTIVE_NCU = 0.602
 MIXED_FMA_PIPE_ACTIVE_NCU = 0.329
 # The batch kernel on 16 instances (ncu --set full, one-warp CTAs, 72 registers):
 # DRAM bytes per bin-state and utilisations.
-BATCH_DRAM_BYTES_PER_BINSTEP = 43.8
-BATCH_ISSUE_ACTIVE_NCU = 0.863
-BATCH_FP64_PIPE_ACTIVE_NCU = 0.553
-BATCH_FMA_PIPE_ACTIVE_NCU = 0.466
+BATCH_DRAM_BYTES_PER_BINSTEP = 43.9
+BATCH_ISSUE_ACTIVE_NCU = 0.872
+BATCH_FP64_PIPE_ACTIVE_NCU = 0.538
+BATCH_FMA_PIPE_ACTIVE_NCU = 0.474
 BATCH_COUNTERS_BUILD = "current (72 registers)"
 HBM_FALLBACK_GBS = 6800.0
 
