@@ -62,10 +62,10 @@ FP64_PIPE_ACTIVE_NCU = 0.915
 # The mixed step kernel on a 64^3 x 31 launch (ncu --set full, 4-warp CTAs): DRAM
 # bytes per bin-step (part of the 162 MB state stays in L2; 42 B algorithmic) and
 # the utilisations that bound it (issue slots first).
-MIXED_DRAM_BYTES_PER_BINSTEP = 36.3
-MIXED_ISSUE_ACTIVE_NCU = 0.745
-MIXED_FP64_PIPE_ACTIVE_NCU = 0.602
-MIXED_FMA_PIPE_ACTIVE_NCU = 0.329
+MIXED_DRAM_BYTES_PER_BINSTEP = 36.1
+MIXED_ISSUE_ACTIVE_NCU = 0.759
+MIXED_FP64_PIPE_ACTIVE_NCU = 0.575
+MIXED_FMA_PIPE_ACTIVE_NCU = 0.340
 # The batch kernel on 16 instances (ncu --set full, one-warp CTAs, 72 registers):
 # DRAM bytes per bin-state and utilisations.
 BATCH_DRAM_BYTES_PER_BINSTEP = 43.9
@@ -114,7 +114,7 @@ def _mixed_roofline(bin_steps_per_s, batched=False):
 # (profiles/step_kernel_mixed.md).  None until that capture exists for the current build.
 # An FP64 (collapse) trial is the FP64 kernel's trial arithmetic: FP64_FLOPS_PER_TRIAL.
 MIXED_FLOPS = {"fp32_per_trial": 342.36, "fp64_per_trial": 1.52, "fp64_per_fp64_trial": FP64_FLOPS_PER_TRIAL,
-               "fp32_per_binstep": 68.17, "fp64_per_binstep": 12.60,
+               "fp32_per_binstep": 68.17, "fp64_per_binstep": 11.63,
                "source": "profiles/step_kernel_mixed.md (fit over nine 64^3 launches)"}
 # The batch kernel runs the same trial arithmetic; its 16-instance capture agrees with this fit to
 # 3 % (FP32) and 11 % (FP64) (profiles/batch_kernel_mixed_16inst.md).
