@@ -28,6 +28,8 @@ struct pab_s {
     double *V = nullptr;
     float *h = nullptr;
     int32_t *attempts = nullptr;
+    double *G = nullptr;        // [Nb][C] gas factor at the stored radii (FP64 polytropic)
+    int G_valid = 0;            // G holds the factor at the current state
     double *terms = nullptr;    // [4][Nb][C] quadrature terms of a grid split by bins
     unsigned int *tickets = nullptr;  // [tiles] its per-tile counters (zero between steps)
     double *gas_tab = nullptr;  // gas-term nodes (K.gas_tab points here)
@@ -416,6 +418,10 @@ pab_status pab_create(const pab_config *cfg, void *stream, pab_t **out)
     // a small grid's step is split by bins over more CTAs, which store their items' quadrature
     // terms and count off each tile (at most 32 x SMs cells x 63 bins x 32 bytes, under 10 MB on
     // 152 SMs)
+    // FP64 polytropic steps carry each bin's gas factor from one flow step's moment pass to the
+    // next step's first right-hand side (8 bytes per bin-state)
+    if (e == cudaSuccess && cfg->precision == PAB_FP64 && cfg->gas_mode == PAB_GAS_POLYTROPIC)
+        e = cudaMallocAsync((void **)&h->G, n * sizeof(double), s);
     const bool split = cfg->gas_mode != PAB_GAS_TRANSFER && pab::step_splits_by_bins(h->K);
     const size_t n_tiles = (size_t)((cfg->n_cells + 31) / 32);
     if (e == cudaSuccess && split)
@@ -480,7 +486,7 @@ void pab_destroy(pab_t *h)
         if (h->ev_out[i])
             cudaEventSynchronize(h->ev_out[i]);
     }
-    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->terms, h->tickets, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
+    void *bufs[] = {h->R, h->V, h->h, h->attempts, h->G, h->terms, h->tickets, h->gas_tab, h->pb, h->mv, h->counters, h->stage_p,
                     h->stage_nb, h->stage_out, h->pipe_p[0], h->pipe_p[1], h->pipe_nb[0], h->pipe_nb[1],
                     h->pipe_out[0], h->pipe_out[1]};
     for (void *b : bufs)
@@ -524,6 +530,8 @@ pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_d
     a.attempts = h->attempts;
     a.terms = h->terms;
     a.tickets = h->tickets;
+    a.G = h->G;
+    a.G_valid = h->G_valid;
     a.out = moments_dev;
     a.counters = h->counters;
     a.pb = h->pb;
@@ -531,6 +539,8 @@ pab_status pab_bubble_step(pab_t *h, const double *p_inf_dev, const double *nb_d
     cudaError_t e = h->cfg.gas_mode == PAB_GAS_TRANSFER
                         ? pab::launch_transfer_step(h->K, a, h->block_warps, (cudaStream_t)stream)
                         : pab::launch_step(h->K, h->cfg.precision, a, h->block_warps, (cudaStream_t)stream);
+    // the moment pass wrote the factors at the new state; without moments they are stale
+    h->G_valid = (h->G && moments_dev && e == cudaSuccess) ? 1 : 0;
     if (e != cudaSuccess)
         return cuda_fail(h, e, "pab_bubble_step launch");
     return PAB_OK;
@@ -650,6 +660,7 @@ pab_status pab_set_state(pab_t *h, const double *R_dev, const double *Rdot_dev, 
         return fail(h, PAB_EINVAL, "pab_set_state: R_dev and Rdot_dev are required");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = n_state(h);
+    h->G_valid = 0;  // the carried gas factors belong to the old radii
     cudaError_t e = cudaMemcpyAsync(h->R, R_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->V, Rdot_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -782,6 +793,7 @@ pab_status pab_set_conservative(pab_t *h, const double *alpha_dev, const double 
         return PAB_EINVAL;
     if (!alpha_dev || !qR_dev || !qV_dev)
         return fail(h, PAB_EINVAL, "pab_set_conservative: NULL input");
+    h->G_valid = 0;  // new radii: the carried gas factors are stale
     cudaError_t e = pab::launch_prim_from_cons(h->K, alpha_dev, qR_dev, qV_dev, h->R, h->V, nb_out_dev,
                                                (cudaStream_t)stream);
     return e == cudaSuccess ? PAB_OK : cuda_fail(h, e, "pab_set_conservative");

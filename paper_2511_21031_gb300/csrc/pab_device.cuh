@@ -113,10 +113,16 @@ struct Trial {
 // A3 = (1 - 3 gamma) A1/c and the per-cell B0/c: one reciprocal and no other
 // division.  1/c = 0 gives Rayleigh-Plesset.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
-                                          double B0c, double R, double V, GasBase &g)
+// The gas factor (R0/R)^(3 gamma) of the polytropic contents (0 for an empty cavity).
+__device__ __forceinline__ double gas_G(const StepConst &K, const BinConst &bc, double R, GasBase &g)
 {
-    const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
+    return (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
+}
+
+// The acceleration for a given gas factor G at R.
+__device__ __forceinline__ double accel64_G(const StepConst &K, const BinConst &bc, double B0,
+                                            double B0c, double R, double V, double G)
+{
     const double den = fma(R, fma(V, -K.inv_c, 1.0), K.fmu_ic_rho);
     const double inv = rcp64(R * den);
     const double P = fma(bc.A1, G, B0);
@@ -126,13 +132,10 @@ __device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc
     return fma(N0, R, -s_rho) * inv;
 }
 
-// The bubble pressure over rho, p_b/rho = pv/rho + A1 G, FP64.  With it the
-// <R^3 p_bw> term needs no division: w R^3 p_bw/rho = w R^3 p_b/rho - w R^2 s/rho.
-__device__ __forceinline__ double bubble_pressure_rho64(const StepConst &K, const BinConst &bc,
-                                                        double R, GasBase &g)
+__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
+                                          double B0c, double R, double V, GasBase &g)
 {
-    const double G = (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
-    return fma(bc.A1, G, K.pv_rho);
+    return accel64_G(K, bc, B0, B0c, R, V, gas_G(K, bc, R, g));
 }
 
 // ---------------------------------------------------------------------------
@@ -237,10 +240,14 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BC &bc, float
 //   y1 = y + k1,  y2 = y + (k1 + k2)/4,  y3 = y + (k1 + k2)/6 + 2/3 k3,
 //   3 (y3 - z) = 2 k3 - (k1 + k2).
 // ---------------------------------------------------------------------------
+// (haveG: G0 is the gas factor at the trial's start R, known from before, and the first
+// right-hand side takes it instead of evaluating it; G0used returns the factor it used.)
 __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
-                                         double B0c, double R, double V, double h, GasBase &g)
+                                         double B0c, double R, double V, double h, GasBase &g,
+                                         bool haveG, double G0, double &G0used)
 {
-    const double a1 = accel64(K, bc, B0, B0c, R, V, g);
+    G0used = haveG ? G0 : gas_G(K, bc, R, g);
+    const double a1 = accel64_G(K, bc, B0, B0c, R, V, G0used);
     // y1 = y + h f(y) as one FMA (k1 itself is still formed for k1 + k2): every product-sum of
     // the trial is an explicit fma, so the compiler contracts nothing and the bits do not depend
     // on the kernel the trial is inlined into or on its register budget
@@ -260,6 +267,13 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
     t.V = fma(1.0 / 3.0, t.eV, fma(0.5, sV, V));
     t.ok = gt0(y1R) && gt0(y2R) && gt0(t.R) && finite64(t.V);
     return t;
+}
+
+__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
+                                         double B0c, double R, double V, double h, GasBase &g)
+{
+    double G0;
+    return trial64(K, bc, B0, B0c, R, V, h, g, false, 0.0, G0);
 }
 
 // The embedded difference 2 k3 - (k1 + k2) of FP32 increments, from exact
@@ -653,18 +667,27 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 }
 
 // Quadrature terms of one bin at (R, Rdot), FP64: w R^3, w R^2 Rdot,
-// w R^3 p_bw / rho (= w R^3 p_b/rho - w R^2 s/rho), w R^3 Rdot^2.  Every product
+// w R^3 p_bw / rho (= w R^3 p_b/rho - w R^2 s/rho with p_b/rho = pv/rho + A1 G: no division),
+// w R^3 Rdot^2.  Every product
 // is rounded explicitly, so a sum of the terms comes out the same whether the
 // caller stores them first or adds them as they come.
+// (G returns the gas factor at R the terms used, the value the next flow step starts from.)
 __device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
-                                             double t[4], GasBase &g)
+                                             double t[4], GasBase &g, double &G)
 {
     const double wr2 = __dmul_rn(__dmul_rn(bc.w, R), R);
     const double wr3 = __dmul_rn(wr2, R);
+    G = gas_G(K, bc, R, g);
     t[0] = wr3;
     t[1] = __dmul_rn(wr2, V);
-    t[2] = fma(wr3, bubble_pressure_rho64(K, bc, R, g), -__dmul_rn(wr2, fma(K.fmu_rho, V, K.tsig_rho)));
+    t[2] = fma(wr3, fma(bc.A1, G, K.pv_rho), -__dmul_rn(wr2, fma(K.fmu_rho, V, K.tsig_rho)));
     t[3] = __dmul_rn(__dmul_rn(wr3, V), V);
+}
+__device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
+                                             double t[4], GasBase &g)
+{
+    double G;
+    quad_terms64(K, bc, R, V, t, g, G);
 }
 
 // The same terms in mixed precision: w R^3 in FP64 (for the compensated alpha

@@ -134,6 +134,10 @@ struct StepArgs {
     // per 32-cell tile (left zeroed).  Without them its moments come from a second launch.
     double *terms = nullptr;
     unsigned int *tickets = nullptr;
+    // FP64: [B][C] the gas factor at the stored radii.  The moment pass writes it (when moments
+    // are requested); with G_valid the items start from it instead of evaluating it again.
+    double *G = nullptr;
+    int G_valid = 0;
 };
 
 // The first out-of-bounds index a checked build (PAB_CHECKED, pab_check.cuh) met in one

@@ -87,7 +87,8 @@ __device__ __forceinline__ void split_moments(const StepConst &K, const StepArgs
         int b, cl;
         size_t k;
         item_of(io, j, b, cl, k);
-        store_terms<MIXED>(K, a.terms, b, k, PAB_LDCG(a.R, k, ns), PAB_LDCG(a.V, k, ns));
+        store_terms<MIXED>(K, a.terms, b, k, PAB_LDCG(a.R, k, ns), PAB_LDCG(a.V, k, ns),
+                           MIXED ? nullptr : a.G);
     }
     __threadfence();
     __syncthreads();
@@ -155,6 +156,7 @@ __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
         io.cB0 = cB0;
         io.cB0c = cB0c;
         io.cA0 = cA0;
+        io.G = (!MIXED && a.G_valid) ? a.G : nullptr;
         if (threadIdx.x == 0)
             sh = PoolCounters{0, 0, 0};
         __syncthreads();
@@ -168,7 +170,8 @@ __device__ __forceinline__ void step_body(const StepConst &K, const StepArgs a)
     flush_counters(tc.fl_or, tc.n_flag, tc.n_att, tc.n64, a.counters);
     const long long c = io.c0 + (long long)kTile * warp + lane;
     if (a.out && gridDim.y == 1 && c < io.c0 + io.nc)
-        cell_moments<MIXED>(K, a.R, a.V, K.C, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out);
+        cell_moments<MIXED>(K, a.R, a.V, K.C, c, a.nb ? PAB_LD(a.nb, c, K.C) : K.nb_default, a.out,
+                            MIXED ? nullptr : a.G);
     if (TERMS)
         split_moments<MIXED>(K, a, io);
 }

@@ -62,6 +62,9 @@ struct TileIO {
     // and B0/c (FP64 items), the FP32 image of p0 - p_inf (mixed items)
     const double *cB0 = nullptr, *cB0c = nullptr;
     const float *cA0 = nullptr;
+    // [B][C] the gas factor at the stored radii, from the previous flow step's moment pass
+    // (FP64 items; nullptr: evaluated afresh)
+    const double *G = nullptr;
 };
 
 // Status of the items a lane finished.
@@ -123,6 +126,8 @@ struct Item64 {
     size_t k;
     BinConst bc;
     double B0, B0c, R, V, h, rem;
+    double Gy;  // the gas factor at the current state, when haveG
+    bool haveG;
     int n;
     uint32_t fl;
     GasBase g;
@@ -153,6 +158,8 @@ struct Item64 {
         }
         B0 = io.cB0[c - io.c0];
         B0c = io.cB0c[c - io.c0];
+        haveG = io.G != nullptr;
+        Gy = haveG ? PAB_LD(io.G, k, ns) : 0.0;
         h = start_h(hc, io.dt);
         rem = io.dt;
         return true;
@@ -168,10 +175,14 @@ struct Item64 {
         bool done = false;
         const bool last = le(rem, h);
         const double ht = last ? rem : h;
-        const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g);
+        double G0;
+        const Trial tr = trial64(K, bc, B0, B0c, R, V, ht, g, haveG, Gy, G0);
         ++n;
         const Decision vd = decide64(K, tr);
         const double fac = f2d_fin(vd.fac);
+        // a rejected trial leaves the state, and so its gas factor, as they were
+        haveG = !vd.accept;
+        Gy = G0;
         if (vd.accept) {
             R = tr.R;
             V = tr.V;
@@ -554,9 +565,11 @@ __device__ __forceinline__ void write_moments(const StepConst &K, double nb, lon
 // on one round trip per bin (4 in the step kernel's closing pass, whose reads hit L2 behind other
 // CTAs' trials; 8 in the reduce-only kernel, whose reads come from HBM).  The order of the sums
 // does not depend on it.
+// (Gout, FP64 only: where each bin's gas factor at its radius goes for the next flow step.)
 template <bool MIXED, int AHEAD = 4>
 __device__ __forceinline__ void cell_moments(const StepConst &K, const double *R, const double *V,
-                                             long long C, long long c, double nb, double *out)
+                                             long long C, long long c, double nb, double *out,
+                                             double *Gout = nullptr)
 {
     constexpr int kMomAhead = AHEAD;
     TermSums S;
@@ -586,11 +599,13 @@ __device__ __forceinline__ void cell_moments(const StepConst &K, const double *R
                 const double x = quad_terms_mixed(K, bc, r, v, tf);
                 add_terms<true>(S, x, tf, nullptr);
             } else {
-                double t[4];
+                double t[4], G;
                 GasBase g;
                 g.reset();
-                quad_terms64(K, bc, r, v, t, g);
+                quad_terms64(K, bc, r, v, t, g, G);
                 add_terms<false>(S, t[0], nullptr, t + 1);
+                if (Gout)
+                    PAB_ST(Gout, (size_t)b * (size_t)C + (size_t)c, (long long)K.B * C, G);
             }
         }
     }
@@ -621,7 +636,7 @@ __device__ __forceinline__ void add_bin_terms(const StepConst &K, int b, double 
 // gives its bits.
 template <bool MIXED>
 __device__ __forceinline__ void store_terms(const StepConst &K, double *terms, int b, size_t k,
-                                            double R, double V)
+                                            double R, double V, double *Gout = nullptr)
 {
     const long long ns = (long long)K.B * K.C;
     const BinConst &bc = K.bins[b];
@@ -633,13 +648,15 @@ __device__ __forceinline__ void store_terms(const StepConst &K, double *terms, i
         for (int m = 0; m < 3; ++m)
             PAB_ST(t32, (long long)m * ns + (long long)k, 3 * ns, tf[m]);
     } else {
-        double t[4];
+        double t[4], G;
         GasBase g;
         g.reset();
-        quad_terms64(K, bc, R, V, t, g);
+        quad_terms64(K, bc, R, V, t, g, G);
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             PAB_ST(terms, (long long)m * ns + (long long)k, 4 * ns, t[m]);
+        if (Gout)
+            PAB_ST(Gout, k, ns, G);
     }
 }
 
