@@ -127,6 +127,8 @@ void pab_config_default(pab_config *cfg);
  * one), allocates the state R, Rdot (FP64 [Nb][C]) and the carried sub-step
  * h (FP32 [Nb][C]) on the current device, and initialises R = R0_i,
  * Rdot = Rdot0_ref R0_i/R0ref, h = 0 (first call uses dt) on `stream`.
+ * An FP64 polytropic handle also holds each bin's gas factor at its radius
+ * (FP64 [Nb][C]), which a step that writes moments leaves for the next step.
  * A grid of fewer 32-cell tiles than the device has SMs is stepped split by
  * bins over more CTAs; its handle also holds 4 doubles per bin-state for the
  * quadrature terms and one counter per tile (under 10 MB on 152 SMs), so that
