@@ -48,17 +48,19 @@ SM_MAX_MHZ = 2070.0
 # error norm, controller) and per bin-step outside the trial loop (load, start of
 # the step, the closing pass's bubble pressure and quadrature sums): least-squares
 # fit of ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over nine
-# launches of the 64^3 x 31 grid with traced trial counts (residual 7e-4).  ncu counts
-# 129.51 per trial; two of those are the first stage's products h Rdot and h a, which its
+# launches of the 64^3 x 31 grid with traced trial counts (residual 1e-3).  ncu counts
+# 130.84 per trial; two of those are the first stage's products h Rdot and h a, which its
 # FMAs (y1 = fma(h, f, y)) form a second time beside k1 = h f, and are not counted here.
 # (The accept test's two FP64 products run only for errors within 2^-16 of tol; the FP32
-# estimate decides the rest, so they are not counted either.)
-FP64_FLOPS_PER_TRIAL = 127.51
-FP64_FLOPS_PER_BINSTEP = 25.33
-# DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum
-# on the 64^3 x 31 grid, 286.0 MB / 8.13M bin-steps); scaled by bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 35.1
-FP64_PIPE_ACTIVE_NCU = 0.915
+# estimate decides the rest, so they are not counted either.  The gas factor a flow step
+# starts from comes from the previous step's moment pass, so it is counted once.)
+FP64_FLOPS_PER_TRIAL = 128.84
+FP64_FLOPS_PER_BINSTEP = 15.50
+# DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum on the
+# 64^3 x 31 grid, 422.0 MB / 8.13M bin-steps, the carried gas factors included); scaled by
+# bin-steps.
+FP64_DRAM_BYTES_PER_BINSTEP = 51.9
+FP64_PIPE_ACTIVE_NCU = 0.913
 # The mixed step kernel on a 64^3 x 31 launch (ncu --set full, 4-warp CTAs): DRAM
 # bytes per bin-step (part of the 162 MB state stays in L2; 42 B algorithmic) and
 # the utilisations that bound it (issue slots first).
