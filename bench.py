@@ -754,13 +754,14 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
 
 
 # FP64-pipe instructions of the carrier-coupling kernels by their source, per cell and per
-# (bin, cell): GB300 retires 2 per clock and SM, and at these counts the pipe, not HBM, bounds
-# set_conservative (a multiply per rescaled value, two multiplies and an FMA per summed one, a
-# reciprocal and an inverse square root per cell).
+# (bin, cell): GB300 retires 2 per clock and SM.  set_conservative forms its products (the cube
+# of each summed value and the rescale of each value) on the integer pipe, leaving an FMA per
+# summed value and a reciprocal and an inverse square root per cell; with the five products in
+# FP64 the pipe, not HBM, bounded it (0.43 of HBM).
 CLOSURE_FP64_INSTR = {
     "mixture_pressure": (4.0, 0.0),
     "get_conservative": (0.0, 2.0),
-    "set_conservative": (13.0, 5.0),
+    "set_conservative": (13.0, 1.0),
 }
 FP64_PIPE_INSTR_PER_CLK_PER_SM = 2.0
 # Algorithmic HBM bytes of the carrier-coupling kernels (FP64): per cell and per (bin, cell).

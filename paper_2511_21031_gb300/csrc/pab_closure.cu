@@ -7,6 +7,7 @@
 #include "pab_bits.cuh"
 #include "pab_check.cuh"
 #include "pab_internal.h"
+#include "pab_intmul.cuh"
 
 PAB_CHECK_UNIT(closure)
 
@@ -31,13 +32,18 @@ __global__ void cons_from_prim_kernel(long long C, const double *__restrict__ nb
 // One thread per cell: the sum of w qR^3 over the bins, n_b = sqrt(4/3 pi S / alpha), then the
 // rescale of every bin.  Consecutive threads read consecutive cells of one bin row (coalesced),
 // and the bin loops are unrolled so that each thread keeps a chunk of loads in flight; the
-// second read of qR comes from L2 (a CTA's rows were just read).  The bound is GB300's FP64
-// pipe, not HBM: 3 FP64 operations per summed value, 1 per rescaled one and a few per cell,
-// against 2 per clock and SM, take longer than the 32 bytes per (bin, cell) take to stream.
-constexpr int kCellsPerCta = 256;
-constexpr int kUnroll = 8;     // rescale: qR and qV of 8 bins in flight per thread
-constexpr int kUnrollSum = 16;  // sum: qR of 16 bins in flight per thread
-__global__ void __launch_bounds__(kCellsPerCta)
+// second read of qR comes from L2 (a CTA's rows were just read).  Each (bin, cell) takes three
+// products (the cube of qR, and qR and qV times 1/n_b) and one FMA into the sum: in FP64, at
+// GB300's 2 FP64 operations per clock and SM, the five would take longer than the 32 bytes take
+// to stream, so the products are formed on the integer pipe (pab_intmul.cuh, within 1 ulp of
+// the FP64 ones) and the FMA alone runs in FP64.  Small CTAs at 32 registers keep 64 warps on
+// each SM, which matters more here than deeper unrolling (a few spilled registers cost less
+// than half the warps).  A layout with the bins spread over a CTA's warps, each value read once
+// and kept in registers, ran slower: a CTA then touches each of 62 rows for 256 bytes only.
+constexpr int kCellsPerCta = 128;
+constexpr int kUnroll = 4;     // rescale: qR and qV of 4 bins in flight per thread
+constexpr int kUnrollSum = 8;  // sum: qR of 8 bins in flight per thread
+__global__ void __launch_bounds__(kCellsPerCta, 16)
     prim_from_cons_kernel(const __grid_constant__ StepConst K, const double *__restrict__ alpha,
                           const double *__restrict__ qR, const double *__restrict__ qV,
                           double *__restrict__ R, double *__restrict__ V, double *__restrict__ nb_out)
@@ -56,6 +62,7 @@ __global__ void __launch_bounds__(kCellsPerCta)
     // the bins in whole chunks, every load of a chunk issued before its arithmetic, then the rest
     // in fours and ones (a predicated last chunk would run its FP64 operations for the missing
     // bins too)
+    bool ok = true;
     double s = 0.0;
     int b = 0;
     for (; b + kUnrollSum <= K.B; b += kUnrollSum) {
@@ -65,7 +72,7 @@ __global__ void __launch_bounds__(kCellsPerCta)
             q[i] = PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns);
 #pragma unroll
         for (int i = 0; i < kUnrollSum; ++i)
-            s = fma(sw[b + i] * q[i], q[i] * q[i], s);
+            s = fma(sw[b + i], cube_int(q[i], ok), s);
     }
     for (; b + 4 <= K.B; b += 4) {
         double q[4];
@@ -74,16 +81,20 @@ __global__ void __launch_bounds__(kCellsPerCta)
             q[i] = PAB_LD(qR, (size_t)(b + i) * C + (size_t)c, ns);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            s = fma(sw[b + i] * q[i], q[i] * q[i], s);
+            s = fma(sw[b + i], cube_int(q[i], ok), s);
     }
-    for (; b < K.B; ++b) {
-        const double q = PAB_LD(qR, (size_t)b * C + (size_t)c, ns);
-        s = fma(sw[b] * q, q * q, s);
+    for (; b < K.B; ++b)
+        s = fma(sw[b], cube_int(PAB_LD(qR, (size_t)b * C + (size_t)c, ns), ok), s);
+    if (!ok) {
+        // a subnormal, infinite or NaN value, or a cube outside the normal range: the sum in FP64
+        s = 0.0;
+        for (b = 0; b < K.B; ++b) {
+            const double q = PAB_LD(qR, (size_t)b * C + (size_t)c, ns);
+            s = fma(sw[b] * q, q * q, s);
+        }
     }
-    // n_b = sqrt(4/3 pi S / alpha) and 1/n_b from one reciprocal and one inverse square root:
-    // the kernel is bound by GB300's FP64 pipe (a multiply of each rescaled value and three
-    // operations of each summed one already match the HBM time), so an IEEE square root and two
-    // divisions per cell are worth avoiding
+    // n_b = sqrt(4/3 pi S / alpha) and 1/n_b from one reciprocal and one inverse square root,
+    // which leave the FP64 pipe less to do than an IEEE square root and two divisions
     double n = (double)NAN, in = (double)NAN;
     const double a = PAB_LD(alpha, c, K.C);
     if (a > 0.0 && a <= 1.0e300) {
@@ -93,27 +104,39 @@ __global__ void __launch_bounds__(kCellsPerCta)
     }
     if (nb_out)
         PAB_ST(nb_out, c, K.C, n);
-    b = 0;
-    for (; b + kUnroll <= K.B; b += kUnroll) {
-        double qr[kUnroll], qv[kUnroll];
+    const IntFactor f = int_factor(in);
+    ok = f.normal;
+    if (ok) {
+        b = 0;
+        for (; b + kUnroll <= K.B; b += kUnroll) {
+            double qr[kUnroll], qv[kUnroll];
 #pragma unroll
-        for (int i = 0; i < kUnroll; ++i) {
-            const size_t k = (size_t)(b + i) * C + (size_t)c;
-            qr[i] = PAB_LD(qR, k, ns);
-            qv[i] = PAB_LD(qV, k, ns);
+            for (int i = 0; i < kUnroll; ++i) {
+                const size_t k = (size_t)(b + i) * C + (size_t)c;
+                qr[i] = PAB_LD(qR, k, ns);
+                qv[i] = PAB_LD(qV, k, ns);
+            }
+#pragma unroll
+            for (int i = 0; i < kUnroll; ++i) {
+                const size_t k = (size_t)(b + i) * C + (size_t)c;
+                PAB_ST(R, k, ns, mul_int(qr[i], f, ok));
+                PAB_ST(V, k, ns, mul_int(qv[i], f, ok));
+            }
         }
-#pragma unroll
-        for (int i = 0; i < kUnroll; ++i) {
-            const size_t k = (size_t)(b + i) * C + (size_t)c;
-            PAB_ST(R, k, ns, qr[i] * in);
-            PAB_ST(V, k, ns, qv[i] * in);
+        for (; b < K.B; ++b) {
+            const size_t k = (size_t)b * C + (size_t)c;
+            PAB_ST(R, k, ns, mul_int(PAB_LD(qR, k, ns), f, ok));
+            PAB_ST(V, k, ns, mul_int(PAB_LD(qV, k, ns), f, ok));
         }
     }
-    for (; b < K.B; ++b) {
-        const size_t k = (size_t)b * C + (size_t)c;
-        const double qr = PAB_LD(qR, k, ns), qv = PAB_LD(qV, k, ns);
-        PAB_ST(R, k, ns, qr * in);
-        PAB_ST(V, k, ns, qv * in);
+    if (!ok) {
+        // 1/n_b or a value not normal, or a product outside the normal range: the cell's
+        // products again in FP64, over what the fast loop stored
+        for (b = 0; b < K.B; ++b) {
+            const size_t k = (size_t)b * C + (size_t)c;
+            PAB_ST(R, k, ns, PAB_LD(qR, k, ns) * in);
+            PAB_ST(V, k, ns, PAB_LD(qV, k, ns) * in);
+        }
     }
 }
 

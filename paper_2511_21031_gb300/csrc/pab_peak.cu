@@ -7,6 +7,7 @@
 
 #include "pab_device.cuh"
 #include "pab_exp.cuh"
+#include "pab_intmul.cuh"
 #include "pab_internal.h"
 #include "pab_measure.h"
 
@@ -175,6 +176,20 @@ __global__ void exp_check_kernel(long long n, const double *x, double *mine, dou
     }
 }
 
+__global__ void intmul_check_kernel(long long n, const double *x, const double *y, double *prod,
+                                    double *cube)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        bool ok = true;
+        const double p = pab::mul_int(x[i], pab::int_factor(y[i]), ok);
+        prod[i] = ok ? p : x[i] * y[i];
+        ok = true;
+        const double c = pab::cube_int(x[i], ok);
+        cube[i] = ok ? c : x[i] * x[i] * x[i];
+    }
+}
+
 __global__ void gas32_check_kernel(long long n, const float *u, float a, float *out, float *lib)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -219,6 +234,21 @@ extern "C" pab_status pab_exp_check(int64_t n, const double *x_dev, double *mine
         return PAB_OK;
     cudaStream_t s = (cudaStream_t)stream;
     exp_check_kernel<<<152 * 4, 256, 0, s>>>(n, x_dev, mine_dev, lib_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAB_OK : PAB_ECUDA;
+}
+
+extern "C" pab_status pab_intmul_check(int64_t n, const double *x_dev, const double *y_dev,
+                                       double *prod_dev, double *cube_dev, void *stream)
+{
+    if (n < 0 || (n > 0 && (!x_dev || !y_dev || !prod_dev || !cube_dev)))
+        return PAB_EINVAL;
+    if (n == 0)
+        return PAB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    intmul_check_kernel<<<152 * 4, 256, 0, s>>>(n, x_dev, y_dev, prod_dev, cube_dev);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);

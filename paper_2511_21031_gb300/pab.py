@@ -32,7 +32,7 @@ EXPORTS = ("pab_config_default", "pab_create", "pab_bubble_step", "pab_moments",
            "pab_strang_half", "pab_get_conservative", "pab_set_conservative", "pab_mixture_pressure",
            "pab_stiffened_gas", "pab_math_check", "pab_bits_check", "pab_gas32_check", "pab_gas_table",
            "pab_get_contents", "pab_set_contents", "pab_check_report", "pab_accept_check",
-           "pab_exp_check")
+           "pab_exp_check", "pab_intmul_check")
 NOALLOC_SCRATCH_BYTES = 256
 
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
         "pab_accept_check": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
         "pab_exp_check": (i32, [i64, vp, vp, vp, vp]),
+        "pab_intmul_check": (i32, [i64, vp, vp, vp, vp, vp]),
         "pab_check_report": (i32, [ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
@@ -331,6 +332,19 @@ def pab_exp_check(x, stream=None):
     if st != PAB_OK:
         raise PabError(st, "pab_exp_check")
     return mine, lib
+
+
+def pab_intmul_check(x, y, stream=None):
+    """(x y, x^3) formed on the integer pipe as the conservative-to-primitive pass forms them,
+    for x, y float64 on the device."""
+    import torch
+    prod = torch.empty_like(x)
+    cube = torch.empty_like(x)
+    st = load().pab_intmul_check(x.numel(), x.data_ptr(), y.data_ptr(), prod.data_ptr(),
+                                 cube.data_ptr(), _stream_handle(stream) or None)
+    if st != PAB_OK:
+        raise PabError(st, "pab_intmul_check")
+    return prod, cube
 
 
 def pab_accept_check(trial, k, tol: float, v_floor: float, stream=None):

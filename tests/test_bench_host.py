@@ -189,7 +189,7 @@ def test_closure_line_times_each_kernel_group(monkeypatch):
     assert k["set_conservative"]["algorithmic_gbs"] == pytest.approx((16.0 * C + 32.0 * C * B) / 3e-3 / 1e9)
     assert k["set_conservative"]["hbm_frac"] == pytest.approx(k["set_conservative"]["algorithmic_gbs"] / d["hbm_peak_gbs"])
     pipe = 2.0 * 152 * 2070e6
-    assert k["set_conservative"]["fp64_pipe_frac"] == pytest.approx((13.0 * C + 5.0 * C * B) / 3e-3 / pipe)
+    assert k["set_conservative"]["fp64_pipe_frac"] == pytest.approx((13.0 * C + 1.0 * C * B) / 3e-3 / pipe)
     assert k["get_conservative"]["fp64_pipe_frac"] == pytest.approx(2.0 * C * B / 2e-3 / pipe)
     assert d["status_flags"] == 0 and d["workload"].endswith("strang")
 
