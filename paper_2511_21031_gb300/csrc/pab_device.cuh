@@ -11,6 +11,7 @@
 #include "pab_bits.cuh"
 #include "pab_check.cuh"
 #include "pab_internal.h"
+#include "pab_intmul.cuh"
 
 namespace pab {
 
@@ -119,23 +120,35 @@ __device__ __forceinline__ double gas_G(const StepConst &K, const BinConst &bc, 
     return (K.gas_mode == PAB_GAS_POLYTROPIC) ? gas_factor(K, bc, R, g) : 0.0;
 }
 
-// The acceleration for a given gas factor G at R.
+// The acceleration for a given gas factor G at R.  INT: its two products (R den and the
+// numerator times 1/(R den)) formed on the integer pipe (pab_intmul.cuh), clearing ok where an
+// operand or a result is not a normal number or zero.
+template <bool INT>
 __device__ __forceinline__ double accel64_G(const StepConst &K, const BinConst &bc, double B0,
-                                            double B0c, double R, double V, double G)
+                                            double B0c, double R, double V, double G, bool &ok)
 {
     const double den = fma(R, fma(V, -K.inv_c, 1.0), K.fmu_ic_rho);
-    const double inv = rcp64(R * den);
+    const double inv = rcp64(INT ? mul_int(R, int_factor(den), ok) : R * den);
     const double P = fma(bc.A1, G, B0);
     const double t = fma(-V, fma(V, K.m05_inv_c, 1.5), fma(bc.A3, G, B0c));
     const double N0 = fma(V, t, P);
     const double s_rho = fma(K.fmu_rho, V, K.tsig_rho);
-    return fma(N0, R, -s_rho) * inv;
+    const double num = fma(N0, R, -s_rho);
+    return INT ? mul_int(num, int_factor(inv), ok) : num * inv;
 }
 
-__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
-                                          double B0c, double R, double V, GasBase &g)
+__device__ __forceinline__ double accel64_G(const StepConst &K, const BinConst &bc, double B0,
+                                            double B0c, double R, double V, double G)
 {
-    return accel64_G(K, bc, B0, B0c, R, V, gas_G(K, bc, R, g));
+    bool ok = true;
+    return accel64_G<false>(K, bc, B0, B0c, R, V, G, ok);
+}
+
+template <bool INT>
+__device__ __forceinline__ double accel64(const StepConst &K, const BinConst &bc, double B0,
+                                          double B0c, double R, double V, GasBase &g, bool &ok)
+{
+    return accel64_G<INT>(K, bc, B0, B0c, R, V, gas_G(K, bc, R, g), ok);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,21 +255,33 @@ __device__ __forceinline__ float accel32(const StepConst &K, const BC &bc, float
 // ---------------------------------------------------------------------------
 // (haveG: G0 is the gas factor at the trial's start R, known from before, and the first
 // right-hand side takes it instead of evaluating it; G0used returns the factor it used.)
-__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
-                                         double B0c, double R, double V, double h, GasBase &g,
-                                         bool haveG, double G0, double &G0used)
+// INT: the trial's plain products (k1 = h f(y) and the two of each right-hand side) formed on
+// the integer pipe, each within 1 ulp of the FP64 product, GB300's FP64 pipe being the bound of
+// the step; ok is cleared where one of them meets a value that is not a normal number or zero.
+template <bool INT>
+__device__ __forceinline__ Trial trial64_body(const StepConst &K, const BinConst &bc, double B0,
+                                              double B0c, double R, double V, double h, GasBase &g,
+                                              bool haveG, double G0, double &G0used, bool &ok)
 {
     G0used = haveG ? G0 : gas_G(K, bc, R, g);
-    const double a1 = accel64_G(K, bc, B0, B0c, R, V, G0used);
+    const double a1 = accel64_G<INT>(K, bc, B0, B0c, R, V, G0used, ok);
     // y1 = y + h f(y) as one FMA (k1 itself is still formed for k1 + k2): every product-sum of
     // the trial is an explicit fma, so the compiler contracts nothing and the bits do not depend
     // on the kernel the trial is inlined into or on its register budget
-    const double k1R = h * V, k1V = h * a1;
+    double k1R, k1V;
+    if (INT) {
+        const IntFactor fh = int_factor(h);
+        k1R = mul_int(V, fh, ok);
+        k1V = mul_int(a1, fh, ok);
+    } else {
+        k1R = h * V;
+        k1V = h * a1;
+    }
     const double y1R = fma(h, V, R), y1V = fma(h, a1, V);
-    const double a2 = accel64(K, bc, B0, B0c, y1R, y1V, g);
+    const double a2 = accel64<INT>(K, bc, B0, B0c, y1R, y1V, g, ok);
     const double sR = fma(h, y1V, k1R), sV = fma(h, a2, k1V);   // k1 + k2
     const double y2R = fma(0.25, sR, R), y2V = fma(0.25, sV, V);
-    const double a3 = accel64(K, bc, B0, B0c, y2R, y2V, g);
+    const double a3 = accel64<INT>(K, bc, B0, B0c, y2R, y2V, g, ok);
     // 2 k3 = (2h) f(y2) with 2h exact; y3 = y + (k1 + k2)/6 + 2/3 k3 written as
     // y + (k1 + k2)/2 + (2 k3 - (k1 + k2))/3
     const double h2 = twice_nn(h);
@@ -269,11 +294,34 @@ __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc,
     return t;
 }
 
+// The trial with its products on the integer pipe, and again with FP64 products where one of
+// them met a subnormal, infinite or NaN value or left the normal range.
+__device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
+                                         double B0c, double R, double V, double h, GasBase &g,
+                                         bool haveG, double G0, double &G0used)
+{
+    bool ok = true;
+    Trial t = trial64_body<true>(K, bc, B0, B0c, R, V, h, g, haveG, G0, G0used, ok);
+    if (!ok)
+        t = trial64_body<false>(K, bc, B0, B0c, R, V, h, g, haveG, G0, G0used, ok);
+    return t;
+}
+
 __device__ __forceinline__ Trial trial64(const StepConst &K, const BinConst &bc, double B0,
                                          double B0c, double R, double V, double h, GasBase &g)
 {
     double G0;
     return trial64(K, bc, B0, B0c, R, V, h, g, false, 0.0, G0);
+}
+
+// The trial with FP64 products: the mixed path's FP64 trials near collapse, too few to repay
+// the integer form's registers in kernels held to 64 of them.
+__device__ __forceinline__ Trial trial64_fp64(const StepConst &K, const BinConst &bc, double B0,
+                                              double B0c, double R, double V, double h, GasBase &g)
+{
+    double G0;
+    bool ok = true;
+    return trial64_body<false>(K, bc, B0, B0c, R, V, h, g, false, 0.0, G0, ok);
 }
 
 // The embedded difference 2 k3 - (k1 + k2) of FP32 increments, from exact
@@ -500,7 +548,7 @@ __device__ __forceinline__ Trial64Out collapse_trial64(const StepConst &K, const
     GasBase g;
     g.reset();
     const double B0 = (K.pv - p_inf) * K.inv_rho;
-    const Trial tr = trial64(K, bc, B0, B0 * K.inv_c, R, V, h, g);
+    const Trial tr = trial64_fp64(K, bc, B0, B0 * K.inv_c, R, V, h, g);
     const Decision vd = decide64(K, tr);
     return {tr.R, tr.V, tr.ok, vd.accept, vd.errf};
 }
@@ -626,7 +674,7 @@ __device__ __forceinline__ void advance_fixed(const StepConst &K, const BinConst
         if (MIXED && !((R < K.r_collapse * bc.R0) || (fabs(V) > K.v_collapse)))
             tr = trial32(K, bc, A, R, V, h);
         else
-            tr = trial64(K, bc, B0, B0c, R, V, h, g);
+            tr = MIXED ? trial64_fp64(K, bc, B0, B0c, R, V, h, g) : trial64(K, bc, B0, B0c, R, V, h, g);
         R = tr.R;
         V = tr.V;
     }
