@@ -100,17 +100,19 @@ pab_status pab_exp_check(int64_t n, const double *x_dev, double *mine_dev, doubl
                          void *stream);
 
 /*
- * The integer-pipe products of the conservative-to-primitive pass against
- * FP64 (no counterpart in the paper; a test hook for the n_b R_i, n_b Rdot_i
- * inversion of Listing 2 and Eq. e:ndf): prod_dev[i] = x_dev[i] y_dev[i] and
- * cube_dev[i] = x_dev[i]^3, each formed from the significands with integer
- * multiplies and rounded once (the FP64 instruction for zero, subnormal,
- * infinite or NaN operands and results outside the normal range).  Each is
- * within 1 ulp of the correctly rounded value.  All [n] double on the device.
+ * The integer-pipe arithmetic against FP64 (no counterpart in the paper; a
+ * test hook for the n_b R_i, n_b Rdot_i inversion of Listing 2 and Eq. e:ndf
+ * and for the FP64 trial's Keller-Miksis right-hand side, Eq. keller_miksis):
+ * prod_dev[i] = x_dev[i] y_dev[i], cube_dev[i] = x_dev[i]^3 and
+ * rcp_dev[i] = 1 / x_dev[i], each formed from the significands with integer
+ * multiplies (the reciprocal from an FP32 approximate one, refined as an
+ * integer) and rounded once; the FP64 operation for zero, subnormal, infinite
+ * or NaN operands and results outside the normal range.  Each is within 1 ulp
+ * of the correctly rounded value.  All [n] double on the device.
  * Errors: PAB_EINVAL (n < 0 or NULL pointers with n > 0), PAB_ECUDA.
  */
 pab_status pab_intmul_check(int64_t n, const double *x_dev, const double *y_dev, double *prod_dev,
-                            double *cube_dev, void *stream);
+                            double *cube_dev, double *rcp_dev, void *stream);
 
 /*
  * The trial accept tests against their exact forms (no counterpart in the

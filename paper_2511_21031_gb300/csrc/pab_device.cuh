@@ -121,14 +121,14 @@ __device__ __forceinline__ double gas_G(const StepConst &K, const BinConst &bc, 
 }
 
 // The acceleration for a given gas factor G at R.  INT: its two products (R den and the
-// numerator times 1/(R den)) formed on the integer pipe (pab_intmul.cuh), clearing ok where an
-// operand or a result is not a normal number or zero.
+// numerator times 1/(R den)) and the reciprocal formed on the integer pipe (pab_intmul.cuh),
+// clearing ok where an operand or a result is not a normal number or zero.
 template <bool INT>
 __device__ __forceinline__ double accel64_G(const StepConst &K, const BinConst &bc, double B0,
                                             double B0c, double R, double V, double G, bool &ok)
 {
     const double den = fma(R, fma(V, -K.inv_c, 1.0), K.fmu_ic_rho);
-    const double inv = rcp64(INT ? mul_int(R, int_factor(den), ok) : R * den);
+    const double inv = INT ? rcp_int(mul_int(R, int_factor(den), ok), ok) : rcp64(R * den);
     const double P = fma(bc.A1, G, B0);
     const double t = fma(-V, fma(V, K.m05_inv_c, 1.5), fma(bc.A3, G, B0c));
     const double N0 = fma(V, t, P);

@@ -117,5 +117,37 @@ __device__ __forceinline__ double cube_int(double x, bool &ok)
     return r;
 }
 
+// 1/x for a normal x, on the integer pipe but for one FP32 approximate reciprocal: y0, the
+// special-function unit's 1/f of the significand's top 24 bits f (within 2^-22 of 1/m, m the
+// significand), taken exactly as Y = y0 2^30; then e = 1 - m y0 exactly as an integer,
+// E = e 2^82 = 2^82 - X Y for the integer significand X, which fits in 64 bits while |e| < 2^-19;
+// and 1/m = y0 / (1 - e) = y0 (1 + e + e^2) to within e^3 (2^-66), the e^2 term from the top
+// half of E.  Rounded once: within 1 ulp of 1/x (the correct rounding but near ties); ok cleared
+// where x is zero, subnormal, infinite or NaN or 1/x is subnormal.
+__device__ __forceinline__ double rcp_int(double x, bool &ok)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const uint32_t mhi = (hi & 0xfffffu) | 0x100000u;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;"
+        : "=f"(y0)
+        : "f"(__uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29))));
+    const uint32_t yb = __float_as_uint(y0);  // y0 in (1/2, 1]: biased exponent 126 or 127
+    const uint32_t Y = ((yb & 0x7fffffu) | 0x800000u) << ((yb >> 23) - 120u);
+    // X Y mod 2^64 for X = mhi 2^32 + lo; 2^82 is 0 mod 2^64
+    const uint64_t xy = (uint64_t)lo * Y + ((uint64_t)(mhi * Y) << 32);
+    const int64_t E = (int64_t)(0ull - xy);
+    const int32_t Eh = (int32_t)(E >> 32);
+    const int64_t T = E + (((int64_t)Eh * Eh) >> 18);  // (e + e^2) 2^82
+    const int32_t Th = (int32_t)(T >> 32);
+    const int64_t corr = ((int64_t)Y * Th + (int64_t)__umulhi(Y, (uint32_t)T)) >> 18;
+    const uint64_t R62 = ((uint64_t)Y << 32) + (uint64_t)corr;  // (1/m) 2^62, in (2^61, 2^62]
+    double r;
+    const bool in_range = pack_sig(R62 << 1, 1024 - e, hi & 0x80000000u, r);
+    ok = ok && in_range && (unsigned)(e - 1) < 2046u;
+    return r;
+}
+
 }  // namespace
 }  // namespace pab

@@ -177,7 +177,7 @@ __global__ void exp_check_kernel(long long n, const double *x, double *mine, dou
 }
 
 __global__ void intmul_check_kernel(long long n, const double *x, const double *y, double *prod,
-                                    double *cube)
+                                    double *cube, double *rcp)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -187,6 +187,9 @@ __global__ void intmul_check_kernel(long long n, const double *x, const double *
         ok = true;
         const double c = pab::cube_int(x[i], ok);
         cube[i] = ok ? c : x[i] * x[i] * x[i];
+        ok = true;
+        const double r = pab::rcp_int(x[i], ok);
+        rcp[i] = ok ? r : 1.0 / x[i];
     }
 }
 
@@ -241,14 +244,15 @@ extern "C" pab_status pab_exp_check(int64_t n, const double *x_dev, double *mine
 }
 
 extern "C" pab_status pab_intmul_check(int64_t n, const double *x_dev, const double *y_dev,
-                                       double *prod_dev, double *cube_dev, void *stream)
+                                       double *prod_dev, double *cube_dev, double *rcp_dev,
+                                       void *stream)
 {
-    if (n < 0 || (n > 0 && (!x_dev || !y_dev || !prod_dev || !cube_dev)))
+    if (n < 0 || (n > 0 && (!x_dev || !y_dev || !prod_dev || !cube_dev || !rcp_dev)))
         return PAB_EINVAL;
     if (n == 0)
         return PAB_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    intmul_check_kernel<<<152 * 4, 256, 0, s>>>(n, x_dev, y_dev, prod_dev, cube_dev);
+    intmul_check_kernel<<<152 * 4, 256, 0, s>>>(n, x_dev, y_dev, prod_dev, cube_dev, rcp_dev);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);

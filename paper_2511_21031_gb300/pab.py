@@ -122,7 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "pab_gas32_check": (i32, [i64, vp, ctypes.c_float, vp, vp, vp]),
         "pab_accept_check": (i32, [i64, vp, vp, dbl, dbl, vp, vp]),
         "pab_exp_check": (i32, [i64, vp, vp, vp, vp]),
-        "pab_intmul_check": (i32, [i64, vp, vp, vp, vp, vp]),
+        "pab_intmul_check": (i32, [i64, vp, vp, vp, vp, vp, vp]),
         "pab_check_report": (i32, [ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     }
@@ -335,16 +335,17 @@ def pab_exp_check(x, stream=None):
 
 
 def pab_intmul_check(x, y, stream=None):
-    """(x y, x^3) formed on the integer pipe as the conservative-to-primitive pass forms them,
-    for x, y float64 on the device."""
+    """(x y, x^3, 1/x) formed on the integer pipe as the kernels form them, for x, y float64 on
+    the device."""
     import torch
     prod = torch.empty_like(x)
     cube = torch.empty_like(x)
+    rcp = torch.empty_like(x)
     st = load().pab_intmul_check(x.numel(), x.data_ptr(), y.data_ptr(), prod.data_ptr(),
-                                 cube.data_ptr(), _stream_handle(stream) or None)
+                                 cube.data_ptr(), rcp.data_ptr(), _stream_handle(stream) or None)
     if st != PAB_OK:
         raise PabError(st, "pab_intmul_check")
-    return prod, cube
+    return prod, cube, rcp
 
 
 def pab_accept_check(trial, k, tol: float, v_floor: float, stream=None):

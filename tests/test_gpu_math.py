@@ -100,11 +100,12 @@ def _ordered(v):
 
 @pytest.mark.gpu
 def test_integer_pipe_products_within_one_ulp():
-    """The conservative-to-primitive pass's products formed from the significands with integer
-    multiplies: x y against the IEEE product and x^3 against the correctly rounded exact cube
-    (exact rational arithmetic) are within 1 ulp everywhere and equal to them in all but a few
-    per mille of draws (those within 2^-8 ulp of a tie); zero, signed, subnormal, infinite and
-    NaN operands and products that overflow or underflow give the FP64 result."""
+    """Products and reciprocals formed from the significands with integer multiplies (the
+    conservative-to-primitive pass, the FP64 trial's right-hand side): x y against the IEEE
+    product, x^3 and 1/x against the correctly rounded exact values (exact rational arithmetic)
+    are within 1 ulp everywhere and equal to them in all but a few per mille of draws (those
+    within 2^-8 ulp of a tie); zero, signed, subnormal, infinite and NaN operands and results
+    that overflow or underflow give the FP64 result."""
     import torch
     from fractions import Fraction
     g = np.random.default_rng(67)
@@ -119,9 +120,9 @@ def test_integer_pipe_products_within_one_ulp():
     xs, ys = np.meshgrid(special, special)
     x = np.concatenate([x, xs.ravel(), [top] * 4])
     y = np.concatenate([y, ys.ravel(), [top, np.nextafter(1.0, 2.0), 1.5, 2.0 ** -1000]])
-    prod, cube = pab.pab_intmul_check(torch.as_tensor(x, device="cuda"),
-                                      torch.as_tensor(y, device="cuda"))
-    prod, cube = prod.cpu().numpy(), cube.cpu().numpy()
+    prod, cube, rcp = pab.pab_intmul_check(torch.as_tensor(x, device="cuda"),
+                                           torch.as_tensor(y, device="cuda"))
+    prod, cube, rcp = prod.cpu().numpy(), cube.cpu().numpy(), rcp.cpu().numpy()
 
     with np.errstate(all="ignore"):
         ref = x * y
@@ -146,3 +147,17 @@ def test_integer_pipe_products_within_one_ulp():
     nan3 = np.isnan(ref3)
     assert np.array_equal(np.isnan(cube[rest]), nan3)
     assert np.abs(_ordered(cube[rest][~nan3]) - _ordered(ref3[~nan3])).max() <= 2
+
+    # 1/x against the correctly rounded exact reciprocal where x and 1/x are normal, against the
+    # IEEE division elsewhere (zero, subnormal, infinite, NaN, and 1/x subnormal)
+    normal = finite & (np.abs(x) >= 2.0 ** -1022) & (np.abs(x) < 2.0 ** 1022)
+    idx = np.flatnonzero(normal)[:40_000]
+    exact = np.array([float(1 / Fraction(float(v))) for v in x[idx]])
+    dr = np.abs(_ordered(rcp[idx]) - _ordered(exact))
+    assert dr.max() <= 1, (dr.max(), x[idx][np.argmax(dr)])
+    assert np.mean(dr == 0) >= 0.99
+    with np.errstate(all="ignore"):
+        refr = 1.0 / x[~normal]
+    nanr = np.isnan(refr)
+    assert np.array_equal(np.isnan(rcp[~normal]), nanr)
+    assert np.abs(_ordered(rcp[~normal][~nanr]) - _ordered(refr[~nanr])).max() <= 1
