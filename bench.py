@@ -43,30 +43,31 @@ NOMINAL_FP64_FLOPS_PER_CLK_PER_SM = 4.0   # nominal 1.25 TFLOP/s / (152 SMs x 2.
 NOMINAL_FP32_FLOPS_PER_CLK_PER_SM = 256.0  # 128 FP32 lanes x 2 (FMA)
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-# FP64 flops (DFMA = 2, DADD/DMUL = 1) of the FP64 step kernel per trial (one sub-step
-# attempt: 3 Keller-Miksis right-hand sides, stage combination, error norm, controller) and per
-# bin-step outside the trial loop (load, start of the step, the closing pass's bubble pressure
-# and quadrature sums): least-squares fit of ncu's
+# FP64 flops (DFMA = 2, DADD/DMUL = 1) the FP64 step kernel's FP64 pipe executes per trial (one
+# sub-step attempt: 3 Keller-Miksis right-hand sides, stage combination, error norm, controller)
+# and per bin-step outside the trial loop (load, start of the step, the closing pass's bubble
+# pressure and quadrature sums): least-squares fit of ncu's
 # smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on over nine launches of the 64^3 x 31
-# grid with traced trial counts (residual 1e-3) gives 122.84 per trial on the FP64 pipe.  The
-# two products of each right-hand side are formed on the integer pipe (pab_intmul.cuh) and are
-# added here: 6 per trial.  The first stage's k1 = h f products also run there; its FMAs
-# (y1 = fma(h, f, y)) form them a second time, so they are not counted.  (The accept test's two
-# FP64 products run only for errors within 2^-16 of tol; the FP32 estimate decides the rest, so
-# they are not counted either.  The gas factor a flow step starts from comes from the previous
-# step's moment pass, so it is counted once.)
-FP64_FLOPS_PER_TRIAL = 128.84
+# grid with traced trial counts (residual 1e-3).  These are the DP operations the FP64 roofline
+# counts.  (The accept test's two FP64 products run only for errors within 2^-16 of tol; the
+# FP32 estimate decides the rest.  The gas factor a flow step starts from comes from the
+# previous step's moment pass.)
+FP64_FLOPS_PER_TRIAL = 104.84
 FP64_FLOPS_PER_BINSTEP = 15.50
-# Of those, the products each right-hand side forms on the integer pipe (R den and the numerator
-# times 1/(R den), pab_intmul.cuh): FP64-precision operations of the method that the FP64 pipe
-# does not execute.  (The trial's k1 = h f products run there too; they are among the two
-# recomputed products not counted above.)
-FP64_INT_PIPE_PRODUCTS_PER_TRIAL = 6.0
+# Operations of the trial that the integer pipe forms instead (pab_intmul.cuh), in the flops the
+# FP64 instructions they replace would count: each right-hand side's two products (2) and its
+# reciprocal's refinement (3 FMAs, 6), three right-hand sides a trial.  Reported beside the
+# roofline (achieved_with_int_pipe), not in it.  (The first stage's k1 = h f products also run
+# there; the first stage's FMAs form them a second time, so they were never counted.)
+FP64_INT_PIPE_FLOPS_PER_TRIAL = 24.0
+# A trial with FP64 products and reciprocal, as the mixed kernels run their FP64 trials near
+# collapse: the FP64-pipe fit of that build (130.84 per trial, less the two recomputed products).
+FP64_PRODUCT_TRIAL_FLOPS = 128.84
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum on the
-# 64^3 x 31 grid, 421.1 MB / 8.13M bin-steps, the carried gas factors included); scaled by
+# 64^3 x 31 grid, 421.6 MB / 8.13M bin-steps, the carried gas factors included); scaled by
 # bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 51.8
-FP64_PIPE_ACTIVE_NCU = 0.924
+FP64_DRAM_BYTES_PER_BINSTEP = 51.9
+FP64_PIPE_ACTIVE_NCU = 0.918
 # The mixed step kernel on a 64^3 x 31 launch (ncu --set full, 4-warp CTAs): DRAM
 # bytes per bin-step (part of the 162 MB state stays in L2; 42 B algorithmic) and
 # the utilisations that bound it (issue slots first).
@@ -120,8 +121,8 @@ def _mixed_roofline(bin_steps_per_s, batched=False):
 # trial, per FP64 (collapse) trial and per bin-step outside the trial loop: least-squares fit of
 # ncu's smsp__sass_thread_inst_executed_op_{f,d}{fma,add,mul}_pred_on over traced launches
 # (profiles/step_kernel_mixed.md).  None until that capture exists for the current build.
-# An FP64 (collapse) trial is the FP64 kernel's trial arithmetic: FP64_FLOPS_PER_TRIAL.
-MIXED_FLOPS = {"fp32_per_trial": 342.36, "fp64_per_trial": 1.52, "fp64_per_fp64_trial": FP64_FLOPS_PER_TRIAL,
+# An FP64 (collapse) trial is the trial with FP64 products: FP64_PRODUCT_TRIAL_FLOPS.
+MIXED_FLOPS = {"fp32_per_trial": 342.36, "fp64_per_trial": 1.52, "fp64_per_fp64_trial": FP64_PRODUCT_TRIAL_FLOPS,
                "fp32_per_binstep": 68.17, "fp64_per_binstep": 11.63,
                "source": "profiles/step_kernel_mixed.md (fit over nine 64^3 launches)"}
 # The batch kernel runs the same trial arithmetic; its 16-instance capture agrees with this fit to
@@ -727,12 +728,12 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
            "status_flags": flags}
     if precision == "fp64":
         flops = bs * (out["trials_per_bin_step"] * FP64_FLOPS_PER_TRIAL + FP64_FLOPS_PER_BINSTEP)
-        on_pipe = flops - bs * out["trials_per_bin_step"] * FP64_INT_PIPE_PRODUCTS_PER_TRIAL
+        with_int = flops + bs * out["trials_per_bin_step"] * FP64_INT_PIPE_FLOPS_PER_TRIAL
         out["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": flops / (total_ms * 1e-3) / 1e12,
                            "peak": _fp64_peak_derived() / 1e12, "unit": "TFLOP/s",
                            "frac": flops / (total_ms * 1e-3) / _fp64_peak_derived(),
-                           "fp64_pipe_achieved": on_pipe / (total_ms * 1e-3) / 1e12,
-                           "int_pipe_products_per_trial": FP64_INT_PIPE_PRODUCTS_PER_TRIAL}
+                           "achieved_with_int_pipe": with_int / (total_ms * 1e-3) / 1e12,
+                           "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL}
     else:
         out["roofline"] = _mixed_compute_roofline(out["value"], out["trials_per_bin_step"],
                                                   out["fp64_trial_fraction"])
@@ -1034,11 +1035,11 @@ def run_ours(args):
                 "pipe": "fp64", "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz",
                 "frac_at_measured_clock": flops_per_launch / avg_launch_s
                 / (NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * sm_mhz * 1e6),
-                # the flops the FP64 pipe itself executed: the products formed on the integer
-                # pipe left out (achieved counts them, as operations of the method)
-                "fp64_pipe_achieved": (flops_per_launch - wl.n_cells * wl.n_bins * trials_per_binstep
-                                       * FP64_INT_PIPE_PRODUCTS_PER_TRIAL) / avg_launch_s / 1e12,
-                "int_pipe_products_per_trial": FP64_INT_PIPE_PRODUCTS_PER_TRIAL}
+                # with the operations the integer pipe forms in place of FP64 instructions,
+                # counted as those instructions would be (context: no FP64 pipe executes them)
+                "achieved_with_int_pipe": (flops_per_launch + wl.n_cells * wl.n_bins * trials_per_binstep
+                                           * FP64_INT_PIPE_FLOPS_PER_TRIAL) / avg_launch_s / 1e12,
+                "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "pipe": "fp64+fp32"}
@@ -1146,16 +1147,12 @@ def run_ours(args):
         roof["peak_measured"] = fma["fp64_tflops"]
         roof["frac_of_measured"] = roof["achieved"] / fma["fp64_tflops"]
         roof["peak_measured_source"] = "pab_peak_fma in this run (fma_probe)"
-        if roof.get("fp64_pipe_achieved"):
-            roof["fp64_pipe_frac_of_measured"] = roof["fp64_pipe_achieved"] / fma["fp64_tflops"]
     for v in variants:
         r = v.get("roofline") if isinstance(v, dict) else None
         if not (r and fma and "fp64_tflops" in fma):
             continue
         if r.get("pipe") == "fp64" and r.get("achieved"):
             r["frac_of_measured"] = r["achieved"] / fma["fp64_tflops"]
-            if r.get("fp64_pipe_achieved"):
-                r["fp64_pipe_frac_of_measured"] = r["fp64_pipe_achieved"] / fma["fp64_tflops"]
         if r.get("fp64_tflops") is not None:
             r["fp64_frac_of_measured"] = r["fp64_tflops"] / fma["fp64_tflops"]
             r["fp32_frac_of_measured"] = r["fp32_tflops"] / fma["fp32_tflops"]
