@@ -98,6 +98,26 @@ __device__ __forceinline__ double mul_int(double x, const IntFactor &f, bool &ok
     return r;
 }
 
+// x y with both operands split here; a zero operand (the other a normal number or zero) gives a
+// signed zero; ok cleared where an operand is subnormal, infinite or NaN or the product leaves
+// the normal range.
+__device__ __forceinline__ double mul2_int(double x, double y, bool &ok)
+{
+    const Sig a = split_sig(x), b = split_sig(y);
+    double r;
+    const bool in_range = pack_sig(mulhi_sig(a.a1, a.a0, b.a1, b.a0), a.e + b.e - 2044,
+                                   a.sign ^ b.sign, r);
+    const bool na = (unsigned)(a.e - 1) < 2046u, nb = (unsigned)(b.e - 1) < 2046u;
+    const bool za = is_zero_sig(x), zb = is_zero_sig(y);
+    if (za || zb) {
+        r = __longlong_as_double((long long)((uint64_t)(a.sign ^ b.sign) << 32));
+        ok = ok && (za || na) && (zb || nb);
+    } else {
+        ok = ok && in_range && na && nb;
+    }
+    return r;
+}
+
 // x^3 from the significand's square kept to 64 bits and then times the significand once more,
 // rounded once: within 1 ulp of the exact cube (and equal to its rounding but near ties); ok
 // cleared where x is subnormal, infinite or NaN or the cube leaves the normal range.

@@ -37,6 +37,22 @@ __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc
     return (K.p0 + K.two_sigma * bc.invR0 - K.pv) * V0 * (K.tr_Rg * K.tr_inv_RgTw);  // ... / T_w
 }
 
+// INT: the products and reciprocals formed from the significands on the integer pipe
+// (pab_intmul.cuh, each within 1 ulp of the FP64 operation), GB300's FP64 pipe being the bound of
+// the step; ok is cleared where one of them meets a subnormal, infinite or NaN value or leaves the
+// normal range, and the trial is then formed again in FP64.
+template <bool INT>
+__device__ __forceinline__ double mul_t(double x, double y, bool &ok)
+{
+    return INT ? mul2_int(x, y, ok) : x * y;
+}
+
+template <bool INT>
+__device__ __forceinline__ double rcp_t(double x, bool &ok)
+{
+    return INT ? rcp_int(x, ok) : rcp64(x);
+}
+
 // dp_b/dt and dm_v/dt (Ando's pressure equation and Eq. massVaporRate with
 // constant-coefficient wall gradients), iR = 1/R.  With chi_vw = rho_vw/rho_bw
 // and 1 - chi_vw = rho_gw/rho_bw the vapour flux is
@@ -48,18 +64,25 @@ __device__ __forceinline__ double gas_mRg(const StepConst &K, const BinConst &bc
 //   dp_b/dt = 3 gamma/R ((R_v T_w X + kT (T_w - T_mean))/R - Rdot p_b),
 //   dm_v/dt = 4 pi R^2 mdot = 4 pi R X,
 // with the constants folded in: X4 = 4 pi X, and kT T_mean = (4 pi/3) kT p_b R^3/(m_v R_v + m_g R_g).
+template <bool INT>
 __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, const State4 &s,
-                                               double iR, double &dpb, double &dmv)
+                                               double iR, double &dpb, double &dmv, bool &ok)
 {
-    const double T3 = s.pb * s.R * s.R * s.R * rcp64(fma(s.mv, K.tr_Rv, mRg));  // T_mean 3/(4 pi)
-    const double mvRg = s.mv * K.tr_Rg;
-    const double D2 = mvRg + mRg;                          // (m_v + m_g) R_g
-    const double rho_gw = (s.pb - K.pv) * K.tr_inv_RgTw;   // gas density at the wall
+    // T_mean 3/(4 pi)
+    const double T3 = mul_t<INT>(
+        mul_t<INT>(mul_t<INT>(mul_t<INT>(s.pb, s.R, ok), s.R, ok), s.R, ok),
+        rcp_t<INT>(fma(s.mv, K.tr_Rv, mRg), ok), ok);
+    const double mvRg = mul_t<INT>(s.mv, K.tr_Rg, ok);
+    const double D2 = mvRg + mRg;                                    // (m_v + m_g) R_g
+    const double rho_gw = mul_t<INT>(s.pb - K.pv, K.tr_inv_RgTw, ok);  // gas density at the wall
     const double rho_bw = K.tr_rho_vw + rho_gw;
-    const double X4 = K.tr_Dc_4pi * rho_bw * fma(K.tr_rho_vw, D2, -mvRg * rho_bw) * rcp64(D2 * rho_gw);
+    const double X4 = mul_t<INT>(
+        mul_t<INT>(mul_t<INT>(K.tr_Dc_4pi, rho_bw, ok),
+                   fma(K.tr_rho_vw, D2, -mul_t<INT>(mvRg, rho_bw, ok)), ok),
+        rcp_t<INT>(mul_t<INT>(D2, rho_gw, ok), ok), ok);
     const double q = fma(K.tr_RvTw_4pi, X4, fma(-K.tr_kT_43pi, T3, K.tr_kT_Tw));
-    dpb = K.three_gamma * iR * fma(q, iR, -s.V * s.pb);
-    dmv = s.R * X4;
+    dpb = mul_t<INT>(mul_t<INT>(K.three_gamma, iR, ok), fma(q, iR, -mul_t<INT>(s.V, s.pb, ok)), ok);
+    dmv = mul_t<INT>(s.R, X4, ok);
 }
 
 // Keller-Miksis, Eq. (keller_miksis), with the state p_b, regrouped as in
@@ -68,37 +91,42 @@ __device__ __forceinline__ void transfer_rates(const StepConst &K, double mRg, c
 //   Rddot = (N0 R - s/rho) / (R den),
 //   N0 = P (1 + Rdot/c) + R dp_b/dt /(rho c) - Rdot^2 (3/2 - Rdot/(2c)),  P = (p_b - p_inf)/rho,
 // taken as N0 = P + R dp_b/dt /(rho c) + Rdot (P/c - Rdot (3/2 - Rdot/(2c))).
-__device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double pinf_rho, const State4 &s)
+template <bool INT>
+__device__ __forceinline__ State4 rhs4(const StepConst &K, double mRg, double pinf_rho, const State4 &s,
+                                       bool &ok)
 {
     const double den = fma(s.R, fma(s.V, -K.inv_c, 1.0), K.fmu_ic_rho);
-    const double inv = rcp64(s.R * den);
-    const double iR = den * inv;
+    const double inv = rcp_t<INT>(mul_t<INT>(s.R, den, ok), ok);
+    const double iR = mul_t<INT>(den, inv, ok);
     double dpb, dmv;
-    transfer_rates(K, mRg, s, iR, dpb, dmv);
+    transfer_rates<INT>(K, mRg, s, iR, dpb, dmv, ok);
     const double P = fma(s.pb, K.inv_rho, -pinf_rho);
-    const double t = fma(-s.V, fma(s.V, K.m05_inv_c, 1.5), P * K.inv_c);
-    const double N0 = fma(s.V, t, fma(s.R * K.ic_rho, dpb, P));
+    const double t = fma(-s.V, fma(s.V, K.m05_inv_c, 1.5), mul_t<INT>(P, K.inv_c, ok));
+    const double N0 = fma(s.V, t, fma(mul_t<INT>(s.R, K.ic_rho, ok), dpb, P));
     const double s_rho = fma(K.fmu_rho, s.V, K.tsig_rho);
-    return State4{s.V, fma(N0, s.R, -s_rho) * inv, dpb, dmv};
+    return State4{s.V, mul_t<INT>(fma(N0, s.R, -s_rho), inv, ok), dpb, dmv};
 }
 
-__device__ __forceinline__ State4 scale(double h, const State4 &f)
+template <bool INT>
+__device__ __forceinline__ State4 scale(double h, const State4 &f, bool &ok)
 {
-    return State4{h * f.R, h * f.V, h * f.pb, h * f.mv};
+    return State4{mul_t<INT>(h, f.R, ok), mul_t<INT>(h, f.V, ok), mul_t<INT>(h, f.pb, ok),
+                  mul_t<INT>(h, f.mv, ok)};
 }
 
 // Shu-Osher SSP-RK3 with the embedded Heun member in increment form (as trial64),
 // on four components: k1 = h f(y), y1 = y + k1, s = k1 + k2, y2 = y + s/4,
 // e = 2 k3 - s = (2h) f(y2) - s = 3 (y3 - z) with 2h exact, y3 = y + s/2 + e/3.
-__device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double pinf_rho, const State4 &y,
-                                         double h)
+template <bool INT>
+__device__ __forceinline__ Trial4 trial4_body(const StepConst &K, double mRg, double pinf_rho,
+                                              const State4 &y, double h, bool &ok)
 {
-    const State4 k1 = scale(h, rhs4(K, mRg, pinf_rho, y));
+    const State4 k1 = scale<INT>(h, rhs4<INT>(K, mRg, pinf_rho, y, ok), ok);
     const State4 y1{y.R + k1.R, y.V + k1.V, y.pb + k1.pb, y.mv + k1.mv};
-    const State4 f2 = rhs4(K, mRg, pinf_rho, y1);
+    const State4 f2 = rhs4<INT>(K, mRg, pinf_rho, y1, ok);
     const State4 s{fma(h, f2.R, k1.R), fma(h, f2.V, k1.V), fma(h, f2.pb, k1.pb), fma(h, f2.mv, k1.mv)};
     const State4 y2{fma(0.25, s.R, y.R), fma(0.25, s.V, y.V), fma(0.25, s.pb, y.pb), fma(0.25, s.mv, y.mv)};
-    const State4 f3 = rhs4(K, mRg, pinf_rho, y2);
+    const State4 f3 = rhs4<INT>(K, mRg, pinf_rho, y2, ok);
     const double h2 = twice_nn(h);
     const State4 e{fma(h2, f3.R, -s.R), fma(h2, f3.V, -s.V), fma(h2, f3.pb, -s.pb), fma(h2, f3.mv, -s.mv)};
     Trial4 t;
@@ -107,6 +135,18 @@ __device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double 
     t.eR = e.R;
     t.eV = e.V;
     t.ok = gt0(y1.R) && gt0(y2.R) && gt0(t.y.R) && finite64(t.y.V);
+    return t;
+}
+
+// The trial with its products and reciprocals on the integer pipe, and again in FP64 where one
+// of them met a subnormal, infinite or NaN value or left the normal range.
+__device__ __forceinline__ Trial4 trial4(const StepConst &K, double mRg, double pinf_rho, const State4 &y,
+                                         double h)
+{
+    bool ok = true;
+    Trial4 t = trial4_body<true>(K, mRg, pinf_rho, y, h, ok);
+    if (!ok)
+        t = trial4_body<false>(K, mRg, pinf_rho, y, h, ok);
     return t;
 }
 
@@ -308,7 +348,10 @@ __device__ __forceinline__ void transfer_cell_moments(const StepConst &K, const 
 }
 
 // One CTA of nw warps owns nw tiles (32 nw cells) and streams their items lane by lane.
-__global__ void __launch_bounds__(kMaxWarps * 32)
+// 96 registers (up to 16 warps a CTA fit): with the trial's arithmetic on the integer pipe the
+// kernel takes 128 uncapped, and 96 (a few bytes spilled, 5 CTAs of 4 warps per SM) ran 3.5 %
+// faster than 128 and 104, 7 % faster than 112.
+__global__ void __maxnreg__(96)
     transfer_step_kernel(const __grid_constant__ StepConst K, const StepArgs a)
 {
     __shared__ PoolCounters sh;
