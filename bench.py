@@ -53,13 +53,16 @@ SM_MAX_MHZ = 2070.0
 # FP32 estimate decides the rest.  The gas factor a flow step starts from comes from the
 # previous step's moment pass.)
 FP64_FLOPS_PER_TRIAL = 104.84
-FP64_FLOPS_PER_BINSTEP = 15.50
+FP64_FLOPS_PER_BINSTEP = 8.50
 # Operations of the trial that the integer pipe forms instead (pab_intmul.cuh), in the flops the
 # FP64 instructions they replace would count: each right-hand side's two products (2) and its
 # reciprocal's refinement (3 FMAs, 6), three right-hand sides a trial.  Reported beside the
 # roofline (achieved_with_int_pipe), not in it.  (The first stage's k1 = h f products also run
 # there; the first stage's FMAs form them a second time, so they were never counted.)
 FP64_INT_PIPE_FLOPS_PER_TRIAL = 24.0
+# and per bin-step the seven products of the closing pass's quadrature terms (w R^2, w R^3,
+# w R^2 Rdot, w R^3 Rdot^2, the viscous and surface-tension term).
+FP64_INT_PIPE_FLOPS_PER_BINSTEP = 7.0
 # A trial with FP64 products and reciprocal, as the mixed kernels run their FP64 trials near
 # collapse: the FP64-pipe fit of that build (130.84 per trial, less the two recomputed products).
 FP64_PRODUCT_TRIAL_FLOPS = 128.84
@@ -728,12 +731,14 @@ def _bench_collapse(args, stream, dev, precision, sample_cells=64):
            "status_flags": flags}
     if precision == "fp64":
         flops = bs * (out["trials_per_bin_step"] * FP64_FLOPS_PER_TRIAL + FP64_FLOPS_PER_BINSTEP)
-        with_int = flops + bs * out["trials_per_bin_step"] * FP64_INT_PIPE_FLOPS_PER_TRIAL
+        with_int = flops + bs * (out["trials_per_bin_step"] * FP64_INT_PIPE_FLOPS_PER_TRIAL
+                                 + FP64_INT_PIPE_FLOPS_PER_BINSTEP)
         out["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": flops / (total_ms * 1e-3) / 1e12,
                            "peak": _fp64_peak_derived() / 1e12, "unit": "TFLOP/s",
                            "frac": flops / (total_ms * 1e-3) / _fp64_peak_derived(),
                            "achieved_with_int_pipe": with_int / (total_ms * 1e-3) / 1e12,
-                           "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL}
+                           "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL,
+                           "int_pipe_flops_per_binstep": FP64_INT_PIPE_FLOPS_PER_BINSTEP}
     else:
         out["roofline"] = _mixed_compute_roofline(out["value"], out["trials_per_bin_step"],
                                                   out["fp64_trial_fraction"])
@@ -1037,9 +1042,11 @@ def run_ours(args):
                 / (NOMINAL_FP64_FLOPS_PER_CLK_PER_SM * N_SM * sm_mhz * 1e6),
                 # with the operations the integer pipe forms in place of FP64 instructions,
                 # counted as those instructions would be (context: no FP64 pipe executes them)
-                "achieved_with_int_pipe": (flops_per_launch + wl.n_cells * wl.n_bins * trials_per_binstep
-                                           * FP64_INT_PIPE_FLOPS_PER_TRIAL) / avg_launch_s / 1e12,
-                "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL}
+                "achieved_with_int_pipe": (flops_per_launch + wl.n_cells * wl.n_bins
+                                           * (trials_per_binstep * FP64_INT_PIPE_FLOPS_PER_TRIAL
+                                              + FP64_INT_PIPE_FLOPS_PER_BINSTEP)) / avg_launch_s / 1e12,
+                "int_pipe_flops_per_trial": FP64_INT_PIPE_FLOPS_PER_TRIAL,
+                "int_pipe_flops_per_binstep": FP64_INT_PIPE_FLOPS_PER_BINSTEP}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "pipe": "fp64+fp32"}

@@ -720,16 +720,44 @@ __device__ __forceinline__ uint32_t advance_bin(const StepConst &K, const BinCon
 // is rounded explicitly, so a sum of the terms comes out the same whether the
 // caller stores them first or adds them as they come.
 // (G returns the gas factor at R the terms used, the value the next flow step starts from.)
-__device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
-                                             double t[4], GasBase &g, double &G)
+// (The terms with FP64 products: out of line, for the states whose products the integer form
+// below does not take; returned by value, so that the caller's terms stay in registers.)
+struct Terms4 {
+    double t0, t1, t2, t3;
+};
+static __device__ __noinline__ Terms4 quad_terms64_fp64(const BinConst &bc, double R, double V,
+                                                        double G, double pv_rho, double fmu_rho,
+                                                        double tsig_rho)
 {
     const double wr2 = __dmul_rn(__dmul_rn(bc.w, R), R);
     const double wr3 = __dmul_rn(wr2, R);
+    return Terms4{wr3, __dmul_rn(wr2, V),
+                  fma(wr3, fma(bc.A1, G, pv_rho), -__dmul_rn(wr2, fma(fmu_rho, V, tsig_rho))),
+                  __dmul_rn(__dmul_rn(wr3, V), V)};
+}
+
+// The products formed from the significands on the integer pipe (pab_intmul.cuh, each within
+// 1 ulp of the FP64 product), GB300's FP64 pipe being the bound of the FP64 step; where one of
+// them meets a subnormal, infinite or NaN value the terms are formed again with FP64 products.
+__device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
+                                             double t[4], GasBase &g, double &G)
+{
     G = gas_G(K, bc, R, g);
+    bool ok = true;
+    const IntFactor fR = int_factor(R);
+    const double wr2 = mul_int(mul_int(bc.w, fR, ok), fR, ok);
+    const double wr3 = mul_int(wr2, fR, ok);
     t[0] = wr3;
-    t[1] = __dmul_rn(wr2, V);
-    t[2] = fma(wr3, fma(bc.A1, G, K.pv_rho), -__dmul_rn(wr2, fma(K.fmu_rho, V, K.tsig_rho)));
-    t[3] = __dmul_rn(__dmul_rn(wr3, V), V);
+    t[1] = mul2_int(wr2, V, ok);
+    t[2] = fma(wr3, fma(bc.A1, G, K.pv_rho), -mul2_int(wr2, fma(K.fmu_rho, V, K.tsig_rho), ok));
+    t[3] = mul2_int(mul2_int(wr3, V, ok), V, ok);
+    if (!ok) {
+        const Terms4 f = quad_terms64_fp64(bc, R, V, G, K.pv_rho, K.fmu_rho, K.tsig_rho);
+        t[0] = f.t0;
+        t[1] = f.t1;
+        t[2] = f.t2;
+        t[3] = f.t3;
+    }
 }
 __device__ __forceinline__ void quad_terms64(const StepConst &K, const BinConst &bc, double R, double V,
                                              double t[4], GasBase &g)
