@@ -67,10 +67,10 @@ FP64_INT_PIPE_FLOPS_PER_BINSTEP = 7.0
 # collapse: the FP64-pipe fit of that build (130.84 per trial, less the two recomputed products).
 FP64_PRODUCT_TRIAL_FLOPS = 128.84
 # DRAM bytes per bin-step of the step kernel (ncu dram__bytes_{read,write}.sum on the
-# 64^3 x 31 grid, 421.6 MB / 8.13M bin-steps, the carried gas factors included); scaled by
+# 64^3 x 31 grid, 421.0 MB / 8.13M bin-steps, the carried gas factors included); scaled by
 # bin-steps.
-FP64_DRAM_BYTES_PER_BINSTEP = 51.9
-FP64_PIPE_ACTIVE_NCU = 0.918
+FP64_DRAM_BYTES_PER_BINSTEP = 51.8
+FP64_PIPE_ACTIVE_NCU = 0.904
 # The mixed step kernel on a 64^3 x 31 launch (ncu --set full, 4-warp CTAs): DRAM
 # bytes per bin-step (part of the 162 MB state stays in L2; 42 B algorithmic) and
 # the utilisations that bound it (issue slots first).
