@@ -56,7 +56,12 @@ typedef enum {
     PAB_ESTATE = 6         /* call not valid in the handle's state */
 } pab_status;
 
-/* precision: PAB_FP64 computes every step in FP64.  PAB_MIXED evaluates the
+/* precision: PAB_FP64 computes every step in FP64: FP64 state and FP64
+ * operations, where the plain products and reciprocals of the trial and of the
+ * moment terms are formed from the 53-bit significands on the integer pipe and
+ * rounded once, each within 1 ulp of the IEEE FP64 result (a trial meeting a
+ * subnormal, infinite or NaN value is formed again with FP64 instructions).
+ * PAB_MIXED evaluates the
  * Keller-Miksis right-hand sides in FP32, written in deviations from
  * equilibrium, and keeps in FP64 the state, the embedded error estimate and the
  * accept decision, the time bookkeeping and a compensated alpha sum; bins near

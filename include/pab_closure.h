@@ -45,8 +45,11 @@ pab_status pab_get_conservative(pab_t *h, const double *nb_dev, double *qR_dev, 
 /*
  * Set the state from conservative variables and the void fraction alpha_dev
  * [C]: n_b = sqrt(4/3 pi sum_i w_i qR_i^3 / alpha) (Eq. e:ndf with R = qR/n_b),
- * then R = qR / n_b, Rdot = qV / n_b.  nb_out_dev [C] receives n_b (may be
- * NULL).  A cell with alpha <= 0 or non-finite gets n_b = NaN and is flagged
+ * then R = qR / n_b, Rdot = qV / n_b.  The cubes and the products by 1/n_b are
+ * formed from the significands on the integer pipe, each within 1 ulp of the
+ * FP64 result (FP64 instructions for a cell with a subnormal, infinite or NaN
+ * value).  nb_out_dev [C] receives n_b (may be NULL).  A cell with alpha <= 0
+ * or non-finite gets n_b = NaN and is flagged
  * PAB_FLAG_NONFINITE on its next step; the carried sub-step h is kept.
  * Errors: PAB_EINVAL (NULL inputs), PAB_ECUDA.
  */

@@ -19,8 +19,9 @@
  * Requirements checked by pab_create: precision PAB_FP64, 0 <= pv < p0,
  * R_g, R_v, T_w positive, k_bw, D_vg, beta_T, beta_c >= 0.  The batched,
  * allocation-free and volume-averaged entry points do not take this mode.
- * Moments (pab.h) use the state p_b in <R^3 p_bw>.  Conventions are those of
- * pab.h.
+ * Moments (pab.h) use the state p_b in <R^3 p_bw>.  Conventions, and the
+ * integer-pipe forms of the trial's products and reciprocals (within 1 ulp of
+ * FP64; see precision), are those of pab.h.
  */
 #ifndef PAB_TRANSFER_H
 #define PAB_TRANSFER_H
