@@ -36,6 +36,17 @@ PAB_CHECK_UNIT(el)
 namespace pab {
 namespace {
 
+// A stencil point's weight fx fy fz and its rate term with FP64 products: out of line, for the
+// points whose products the integer form (pab_intmul.cuh) does not take; returned by value.
+struct Weight2 {
+    double a, ad;
+};
+static __device__ __noinline__ Weight2 smear_weight_fp64(double f0, double f1, double f2, double rate)
+{
+    const double a = f0 * f1 * f2;
+    return Weight2{a, a * rate};
+}
+
 constexpr int kSmearWarps = 4;
 constexpr int kCacheHalf = 24;  // stencil half-widths up to this use the separable cache
 constexpr int kSide = 2 * kCacheHalf + 1;
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
 {
     // per warp and axis offset: the squared distance (FP64 and FP32) and the 1-D
     // Gaussian factor; the x factor carries V/(h^3 (2 pi)^{3/2}) so that a stencil
-    // point costs two FP64 multiplies (three with the rate)
+    // point costs two multiplies (three with the rate), formed on the integer pipe
     __shared__ double fac[kSmearWarps][3][kSide];
     __shared__ double sq[kSmearWarps][3][kSide];
     __shared__ float sqf[kSmearWarps][3][kSide];
@@ -203,11 +214,22 @@ __global__ void __launch_bounds__(kSmearWarps * 32)
                     if (lane < queued) {
                         const int tq = ring[warp][(tail + lane) & 63];
                         const int qi = tq & 255, qj = (tq >> 8) & 255, qk = tq >> 16;
-                        const double a = fac[warp][0][qi] * fac[warp][1][qj] * fac[warp][2][qk];
+                        // the weight and its rate term from the significands on the integer
+                        // pipe (each product within 1 ulp of FP64), GB300's FP64 pipe being the
+                        // bound of the smear
+                        const double f0 = fac[warp][0][qi], f1 = fac[warp][1][qj], f2 = fac[warp][2][qk];
+                        bool okw = true;
+                        double a = mul2_int(mul2_int(f0, f1, okw), f2, okw);
+                        double ad = mul2_int(a, rate, okw);
+                        if (!okw) {
+                            const Weight2 w = smear_weight_fp64(f0, f1, f2, rate);
+                            a = w.a;
+                            ad = w.ad;
+                        }
                         const long long c = ((long long)(bz + qk) * ny + (by + qj)) * nx + (bx + qi);
                         atomicAdd(PAB_AT(alpha, c, ng), a);
                         if (alpha_dot)
-                            atomicAdd(PAB_AT(alpha_dot, c, ng), a * rate);
+                            atomicAdd(PAB_AT(alpha_dot, c, ng), ad);
                     }
                     const int done = queued < 32 ? queued : 32;
                     tail = (tail + done) & 63;
